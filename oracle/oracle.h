@@ -1,0 +1,77 @@
+/*
+ * CPU oracle for the block-sparse quadtree product C = A*B.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the GPU library: only
+ * the test suite, the smoke check and the benchmark's CPU-baseline leg may
+ * build, load or call it.  It shares no code with the GPU path.
+ *
+ * Representation (paper, Section 2): a matrix is a sparse quadtree; a node is
+ * either nil (the identically zero submatrix, a NULL pointer here), a dense
+ * leaf of b x b doubles (row-major), or four quadrants [[11, 12], [21, 22]],
+ * each again a sparse quadtree.  A grid of G x G leaves is padded virtually to
+ * 2^D x 2^D with nil leaves (D = ceil(log2 G)).
+ *
+ * Every function returns 0 on success and a negative code on error:
+ *   -1 invalid argument / out-of-range leaf coordinate,
+ *   -2 shape mismatch, -3 duplicate leaf coordinate, -4 out of memory.
+ */
+#ifndef CHT_ORACLE_H
+#define CHT_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_mat orc_mat;
+
+/* Build a quadtree from a list of leaves (any order).  Leaf i sits at leaf
+ * coordinates (brow[i], bcol[i]) and holds vals[i*b*b .. (i+1)*b*b) in
+ * row-major order.  Leaves whose values are all zero are identically zero
+ * and are not stored (nil).  n must be a positive multiple of b. */
+int orc_build(int64_t n, int32_t b, int64_t nblk, const int32_t *brow,
+              const int32_t *bcol, const double *vals, orc_mat **out);
+
+/* C = A*B by the recursive quadtree algorithm; *npairs (may be NULL) gets the
+ * number of leaf-times-leaf products performed. */
+int orc_multiply(const orc_mat *A, const orc_mat *B, orc_mat **C,
+                 int64_t *npairs);
+
+/* Transpose (a new matrix). */
+int orc_transpose(const orc_mat *A, orc_mat **out);
+
+/* The matrix with exactly M's pattern whose leaves are X's leaves where X has
+ * one and zero leaves elsewhere. */
+int orc_restrict(const orc_mat *X, const orc_mat *M, orc_mat **out);
+
+/* Gradients of L = f(C), C = A*B, given dC = dL/dC:
+ * dA = (dC * B^T) on A's pattern, dB = (A^T * dC) on B's pattern. */
+int orc_backward(const orc_mat *A, const orc_mat *B, const orc_mat *dC,
+                 orc_mat **dA, orc_mat **dB);
+
+/* One leaf of C = A*B straight from the definition
+ * C(I,J) = sum_K A(I,K) B(K,J), K ascending.  out: b*b doubles.
+ * *present (may be NULL) is 1 when at least one K contributes. */
+int orc_leaf_product(const orc_mat *A, const orc_mat *B, int64_t I, int64_t J,
+                     double *out, int *present);
+
+/* Number of stored leaves. */
+int64_t orc_nleaves(const orc_mat *M);
+
+/* Stored leaves in quadtree depth-first order (quadrants 11, 12, 21, 22),
+ * which is the Morton (Z) order of the leaf coordinates.  Arrays sized by
+ * orc_nleaves(); vals may be NULL to get the pattern only. */
+int orc_extract(const orc_mat *M, int32_t *brow, int32_t *bcol, double *vals);
+
+int64_t orc_dim(const orc_mat *M);
+int32_t orc_leafsize(const orc_mat *M);
+void orc_free(orc_mat *M);
+
+/* Threads used by the parallel top levels of the recursion. */
+int orc_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
