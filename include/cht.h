@@ -1,0 +1,242 @@
+/*
+ * libcht -- block-sparse quadtree matrix product C = A*B on one GB300 GPU.
+ *
+ * The paper (Chunks and Tasks Matrix Library 2.0, Section 2) represents a
+ * matrix as a sparse quadtree: a node is identically zero (nil), a small dense
+ * leaf matrix, or four quadrants that are again sparse quadtrees.  Its
+ * functionality list (Section 2.2) starts with construction from index and
+ * value vectors, extraction, and matrix-matrix multiplication; Section 3
+ * demonstrates the multiplication on block-sparse matrices.
+ *
+ * This library keeps that contract on one GPU.  The quadtree is flattened:
+ * the stored (non-nil) leaves of a matrix are kept in Morton (Z) order of
+ * their leaf coordinates -- the order of a depth-first walk over quadrants
+ * 11, 12, 21, 22 -- as one array of dense b x b FP64 leaves, row-major inside
+ * each leaf.  The product runs in two phases:
+ *   symbolic: the (A-leaf, B-leaf) pairs that meet on a shared inner index K
+ *             and the product's leaf pattern (the boolean product of the two
+ *             patterns), exact integer work;
+ *   numeric:  one persistent kernel that sums, for every leaf (I, J) of C,
+ *             the leaf products A(I,K) B(K,J) in ascending K.
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are device pointers; all others are host pointers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; calls return without waiting for the
+ *    GPU unless stated otherwise.
+ *  - Inputs are copied: the caller keeps ownership of its buffers and may
+ *    reuse them once the call's work on `stream` has completed.
+ *  - Handles returned through out-parameters are owned by the caller and are
+ *    released with cht_mat_free / cht_plan_free / cht_batch_free, in any
+ *    order.  A handle's device memory is returned in the order of the stream
+ *    that created it, which must outlive the handle; work on other streams
+ *    that uses the handle must be complete (or ordered before) the free.
+ *  - Every call returns a cht_status; on error no output handle is created
+ *    and *out is left unchanged.  cht_last_error() gives a one-line reason.
+ *  - Kernels never trap.  A device-side failure (a bounded wait that ran
+ *    out) is recorded in a library-wide status word; calls that synchronise
+ *    report it, and cht_sync_status() reads and clears it.
+ */
+#ifndef CHT_H
+#define CHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cht_mat *cht_mat_t;     /* a block-sparse matrix on the GPU  */
+typedef struct cht_plan *cht_plan_t;   /* symbolic result of A*B            */
+typedef struct cht_batch *cht_batch_t; /* many products in one launch       */
+
+typedef enum {
+  CHT_OK = 0,
+  CHT_ERR_INVALID = -1,     /* bad argument, leaf coordinate out of range */
+  CHT_ERR_SHAPE = -2,       /* dimensions or leaf sizes do not match      */
+  CHT_ERR_DUPLICATE = -3,   /* the same leaf coordinate given twice       */
+  CHT_ERR_OOM = -4,         /* an allocation failed                       */
+  CHT_ERR_CUDA = -5,        /* a CUDA runtime call failed                 */
+  CHT_ERR_TIMEOUT = -6,     /* a bounded device-side wait ran out         */
+  CHT_ERR_UNSUPPORTED = -7  /* valid request this build does not handle   */
+} cht_status;
+
+typedef enum {
+  CHT_FP64 = 0,       /* FP64 leaf products, FP64 accumulation             */
+  CHT_SPLIT_BF16 = 1  /* FP64 operands split into BF16 slices, tcgen05 MMA  */
+} cht_mode;
+
+/* Leaf sizes the numeric kernels support. */
+#define CHT_MIN_LEAF 32
+#define CHT_MAX_LEAF 64
+
+/* ------------------------------------------------------------------------
+ * Memory.  By default the library allocates device memory with
+ * cudaMallocAsync / cudaFreeAsync on the stream of the call.  A caller may
+ * install its own allocator instead (e.g. a framework's caching allocator).
+ * alloc returns NULL on failure (reported as CHT_ERR_OOM).  Passing NULL
+ * for both restores the default.  Not thread-safe; call before other calls.
+ * ---------------------------------------------------------------------- */
+typedef void *(*cht_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*cht_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int cht_set_allocator(cht_alloc_fn alloc, cht_free_fn free_fn, void *ctx);
+
+/* ------------------------------------------------------------------------
+ * Construction (paper, Section 2.2, "Assignment from ... matrix elements":
+ * construct a matrix from index vectors and values), at leaf granularity.
+ *
+ * n        matrix dimension; a positive multiple of b.
+ * b        leaf size; CHT_MIN_LEAF <= b <= CHT_MAX_LEAF, a multiple of 8
+ *          (the numeric kernels take b = 32 or b = 64).
+ * nblocks  number of leaves given (0 is a valid, empty matrix).
+ * d_brow, d_bcol  int32 leaf coordinates, 0 <= coordinate < n / b.
+ * d_vals   nblocks * b * b doubles; leaf i is d_vals[i*b*b ...], row-major.
+ * Leaves may come in any order.  A leaf whose values are all zero is
+ * identically zero (nil, Section 2) and is not stored.
+ * Errors: CHT_ERR_INVALID (range, sizes), CHT_ERR_DUPLICATE (a coordinate
+ * given twice, zero leaves included), CHT_ERR_OOM, CHT_ERR_CUDA.
+ * Synchronises `stream` once, to validate the input and size the handle.
+ * ---------------------------------------------------------------------- */
+int cht_mat_from_blocks(int64_t n, int32_t b, int64_t nblocks,
+                        const int32_t *d_brow, const int32_t *d_bcol,
+                        const double *d_vals, void *stream, cht_mat_t *out);
+
+/* Shape of a matrix: dimension, leaf size, number of stored leaves. */
+int cht_mat_info(cht_mat_t M, int64_t *n, int32_t *b, int64_t *nblocks);
+
+/* Device arrays of a matrix (owned by the handle, valid until it is freed):
+ * leaf values [nblocks][b][b] in Morton order, and each leaf's (row, col).
+ * Any out-pointer may be NULL.  The values may be written in place. */
+int cht_mat_leaves(cht_mat_t M, double **d_vals, const int32_t **d_brow,
+                   const int32_t **d_bcol);
+
+/* Extraction (paper, Section 2.2): write M densely into the caller's
+ * n x n row-major buffer d_out with leading dimension ld >= n (doubles).
+ * The whole n x n region is overwritten (zeros outside stored leaves). */
+int cht_to_dense(cht_mat_t M, double *d_out, int64_t ld, void *stream);
+
+/* A new matrix with M's pattern (shared, not copied) and uninitialised
+ * values, e.g. to hold a gradient dL/dM or a target on M's pattern. */
+int cht_mat_like(cht_mat_t M, void *stream, cht_mat_t *out);
+
+int cht_mat_free(cht_mat_t M);
+
+/* ------------------------------------------------------------------------
+ * Symbolic multiply (paper, Section 2: the multiply recursion visits only
+ * non-nil quadrant pairs, and a nil operand gives a nil product).  Flattened:
+ * every triple (I, K, J) with A(I,K) and B(K,J) stored is a pair; C's
+ * pattern is the set of (I, J) with at least one pair (the boolean product of
+ * the patterns; a leaf whose values later cancel to zero stays stored).
+ * The plan holds C's pattern (Morton order), each C leaf's pair segment in
+ * ascending K, and a longest-first work schedule.
+ * A and B must have equal n and b (else CHT_ERR_SHAPE).
+ * *nnzb_C and *npairs (either may be NULL) get the number of C leaves and of
+ * pairs; the useful work of the numeric phase is 2 * b^3 * npairs flops.
+ * Synchronises `stream` twice (to size the pair list and C's pattern).
+ * ---------------------------------------------------------------------- */
+int cht_symbolic_multiply(cht_mat_t A, cht_mat_t B, void *stream,
+                          cht_plan_t *out, int64_t *nnzb_C, int64_t *npairs);
+
+/* Plan counts; any out-pointer may be NULL. */
+int cht_plan_info(cht_plan_t P, int64_t *nnzb_C, int64_t *npairs);
+
+/* Plan arrays (device, owned by the plan): pair segments cseg[nnzb_C + 1]
+ * (int64), for each pair the A leaf and B leaf (Morton indices, int32),
+ * each C leaf's (row, col), and the schedule order[nnzb_C].  Any
+ * out-pointer may be NULL. */
+int cht_plan_arrays(cht_plan_t P, const int64_t **d_cseg,
+                    const int32_t **d_pair_a, const int32_t **d_pair_b,
+                    const int32_t **d_crow, const int32_t **d_ccol,
+                    const int32_t **d_order);
+
+int cht_plan_free(cht_plan_t P);
+
+/* ------------------------------------------------------------------------
+ * Numeric multiply C = A*B on a plan from cht_symbolic_multiply(A, B).
+ * mode     CHT_FP64, or CHT_SPLIT_BF16 with `nslices` BF16 slices per
+ *          operand (ignored for CHT_FP64).
+ * *C       in/out.  If *C is NULL a new matrix on the plan's pattern is
+ *          created.  If *C is a matrix previously produced from this plan,
+ *          its values are overwritten in place (no allocation).
+ * max_rel_err_est  may be NULL.  If given, the call synchronises `stream`,
+ *          returns any device-side failure (e.g. CHT_ERR_TIMEOUT), and
+ *          stores an a-priori bound on |C - A*B| / (|A| |B|) elementwise.
+ * Each C leaf is summed in ascending K by one CTA: results are bitwise
+ * reproducible run to run.  No atomics touch C.
+ * ---------------------------------------------------------------------- */
+int cht_multiply(cht_plan_t plan, cht_mat_t A, cht_mat_t B, int mode,
+                 int32_t nslices, void *stream, cht_mat_t *C,
+                 double *max_rel_err_est);
+
+/* ------------------------------------------------------------------------
+ * Backward of C = A*B for a loss L(C), given dC = dL/dC:
+ *   dA = (dC * B^T) restricted to A's pattern,
+ *   dB = (A^T * dC) restricted to B's pattern
+ * (sampled block products: only the stored leaves of A and B are outputs;
+ * a stored leaf that no triple reaches gets zeros).
+ * plan             the forward plan, or NULL.
+ * recompute_pairs  nonzero (or plan == NULL): rebuild the triples from the
+ *                  patterns of A, B and dC instead of reading the plan's
+ *                  pair list (for when the plan's lists were not kept).
+ *                  With a plan and dC produced from that plan, the plan's
+ *                  pairs are regrouped (cached in the plan).
+ * *dA, *dB         in/out as for cht_multiply (NULL = create; a matrix with
+ *                  A's / B's pattern from an earlier call = overwrite).
+ *                  Either pointer may be NULL to skip that gradient.
+ * ---------------------------------------------------------------------- */
+int cht_multiply_backward(cht_plan_t plan, cht_mat_t A, cht_mat_t B,
+                          cht_mat_t dC, int recompute_pairs, void *stream,
+                          cht_mat_t *dA, cht_mat_t *dB);
+
+/* ------------------------------------------------------------------------
+ * Batched products: `count` independent products C_i = A_i * B_i, each with
+ * its own plan (own n and leaf size), computed by ONE persistent kernel
+ * launch whose work list concatenates all products' C leaves in
+ * longest-first order.  cht_batch_create allocates every output and all
+ * launch tables (and may synchronise); cht_batch_run only launches (no
+ * allocation, no synchronisation), so it may be captured in a CUDA graph.
+ * cht_batch_output gives a non-owning view of C_i (valid while the batch
+ * lives; do not free it).
+ * ---------------------------------------------------------------------- */
+int cht_batch_create(int32_t count, const cht_plan_t *plans,
+                     const cht_mat_t *As, const cht_mat_t *Bs, int mode,
+                     int32_t nslices, void *stream, cht_batch_t *out);
+int cht_batch_run(cht_batch_t batch, void *stream);
+int cht_batch_output(cht_batch_t batch, int32_t i, cht_mat_t *C);
+int cht_batch_free(cht_batch_t batch);
+
+/* ------------------------------------------------------------------------
+ * Options (library-wide, not thread-safe).
+ * ---------------------------------------------------------------------- */
+typedef enum {
+  CHT_OPT_SCHEDULE = 0,       /* 0 = longest-first (default), 1 = Morton   */
+  CHT_OPT_WAIT_BUDGET_NS = 1, /* bound of each device-side wait, ns
+                                 (default 2e9; 0 makes every wait expire:
+                                 a test hook for the timeout path)         */
+  CHT_OPT_CTAS_PER_SM = 2,    /* persistent grid = SMs * this (0 = auto)   */
+  CHT_OPT_FP64_ENGINE = 3     /* 0 = DMMA (mma.sync f64), 1 = DFMA          */
+} cht_option;
+int cht_set_option(int option, int64_t value);
+int cht_get_option(int option, int64_t *value);
+
+/* Synchronise `stream`, then read and clear the device status word:
+ * CHT_OK or the first recorded device-side failure (CHT_ERR_TIMEOUT). */
+int cht_sync_status(void *stream);
+
+/* Kernels launched by this library since load (counted on the host). */
+int64_t cht_launch_count(void);
+
+/* Human-readable name of a status code, and the last error's detail. */
+const char *cht_status_str(int status);
+const char *cht_last_error(void);
+
+/* Measure the FP64 arithmetic peak of this GPU: a register-resident kernel
+ * of independent FP64 FMAs (engine 1) or mma.sync f64 (engine 0) on every
+ * SM, timed with CUDA events.  *tflops gets useful TFLOP/s. Synchronises. */
+int cht_measure_fp64_peak(int engine, void *stream, double *tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHT_H */

@@ -1,0 +1,173 @@
+// Shared host-side declarations of libcht (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <memory>
+#include <vector>
+
+#include "cht.h"
+
+namespace cht {
+
+// ----------------------------------------------------------------- errors --
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);  // records, returns CHT_ERR_CUDA
+
+#define CHT_TRY(expr)                \
+  do {                               \
+    int _rc = (expr);                \
+    if (_rc != CHT_OK) return _rc;   \
+  } while (0)
+
+#define CHT_CUDA_TRY(call)                                       \
+  do {                                                           \
+    cudaError_t _e = (call);                                     \
+    if (_e != cudaSuccess) return ::cht::cuda_fail(_e, #call);   \
+  } while (0)
+
+// Checks the launch that was just enqueued and counts it.
+int launched(const char *name);
+
+extern std::atomic<int64_t> g_launches;
+
+// ---------------------------------------------------------------- options --
+struct Options {
+  int schedule = 0;               // 0 longest-first, 1 Morton
+  int64_t wait_budget_ns = 2000000000LL;
+  int ctas_per_sm = 0;            // 0 = auto
+  int fp64_engine = 0;            // 0 DMMA, 1 DFMA
+};
+extern Options g_opt;
+
+// Device status word (one per device, zero = OK); kernels OR flags into it.
+enum : int { DEV_STATUS_TIMEOUT = 1, DEV_STATUS_BAD_INDEX = 2 };
+int device_status_ptr(int **ptr);
+int num_sms(int *sms);
+
+// ------------------------------------------------------------- allocation --
+void *dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void *p, size_t bytes, cudaStream_t s);
+
+// A device array released (in stream order) when the owner goes away.
+template <class T>
+struct DevArray {
+  T *p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  DevArray() = default;
+  DevArray(const DevArray &) = delete;
+  DevArray &operator=(const DevArray &) = delete;
+  DevArray(DevArray &&o) noexcept { swap(o); }
+  DevArray &operator=(DevArray &&o) noexcept {
+    reset();
+    swap(o);
+    return *this;
+  }
+  ~DevArray() { reset(); }
+  void swap(DevArray &o) {
+    std::swap(p, o.p);
+    std::swap(n, o.n);
+    std::swap(s, o.s);
+  }
+  void reset() {
+    if (p) dev_free(p, n * sizeof(T), s);
+    p = nullptr;
+    n = 0;
+  }
+  // Allocates max(count, 1) elements; returns CHT_ERR_OOM on failure.
+  int alloc(size_t count, cudaStream_t stream) {
+    reset();
+    size_t c = count ? count : 1;
+    p = static_cast<T *>(dev_alloc(c * sizeof(T), stream));
+    if (!p) {
+      set_error("device allocation of %zu bytes failed", c * sizeof(T));
+      return CHT_ERR_OOM;
+    }
+    n = c;
+    s = stream;
+    return CHT_OK;
+  }
+};
+
+// ---------------------------------------------------------------- pattern --
+// The stored leaves of a matrix in Morton order, with row and column indexes.
+struct Pattern {
+  int64_t n = 0;
+  int32_t b = 0;
+  int64_t G = 0;   // leaves per side
+  int L = 1;       // bits per leaf coordinate, 2^L >= G
+  int64_t nnz = 0; // stored leaves
+  uint64_t id = 0; // unique per pattern object
+  DevArray<uint64_t> mkey;                   // Morton keys, ascending
+  DevArray<int32_t> brow, bcol;              // per leaf
+  DevArray<int64_t> rowptr, colptr;          // [G + 1]
+  DevArray<int32_t> rowcol, rowleaf;         // CSR by leaf row (cols ascending)
+  DevArray<int32_t> colrow, colleaf;         // CSC by leaf col (rows ascending)
+};
+uint64_t next_id();
+int bits_for(int64_t G);
+// Fills brow/bcol and the row and column indexes from the sorted mkey.
+int build_pattern_index(Pattern &p, cudaStream_t s);
+
+// ------------------------------------------------------------ scan / sort --
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
+int scan_exclusive(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+int scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+// Stable LSD radix sort of (key, value) by the low `nbits` bits of key.
+int radix_sort_pairs(const uint64_t *kin, const int32_t *vin, uint64_t *kout,
+                     int32_t *vout, int64_t n, int nbits, cudaStream_t s);
+// Copy of a device int64 to the host (synchronises s).
+int read_i64(const int64_t *d, int64_t *h, cudaStream_t s);
+
+// ---------------------------------------------------------------- kernels --
+// The grouped leaf-GEMM work description (one output leaf per unit).
+struct GemmWork {
+  const double *X;        // left operand leaves
+  const double *Y;        // right operand leaves
+  double *Z;              // output leaves (Z[unit_out[u]] gets the sum)
+  const int32_t *px;      // per pair: index into X
+  const int32_t *py;      // per pair: index into Y
+  const int64_t *seg;     // per output leaf: pair segment [seg[o], seg[o+1])
+  const int32_t *order;   // schedule: output leaf of each unit
+  int64_t nunits;
+  int32_t b;
+  int trans_x, trans_y;   // use X^T / Y^T in the product
+};
+// Z[o] = sum_p op(X[px[p]]) op(Y[py[p]]) for every unit; FP64.
+int launch_leafgemm_f64(const GemmWork &w, cudaStream_t s);
+
+int launch_fp64_peak(int engine, cudaStream_t s, double *tflops);
+
+}  // namespace cht
+
+// ------------------------------------------------------------ opaque types --
+struct cht_mat {
+  std::shared_ptr<cht::Pattern> pat;
+  cht::DevArray<double> vals;  // [nnz][b][b]
+  uint64_t plan_id = 0;        // plan that produced it (0 = built from blocks)
+  bool view = false;           // non-owning view (batched outputs)
+  double *view_vals = nullptr;
+  double *values() { return view ? view_vals : vals.p; }
+};
+
+struct cht_plan {
+  uint64_t id = 0;
+  int64_t n = 0;
+  int32_t b = 0;
+  int64_t nA = 0, nB = 0;
+  uint64_t patA = 0, patB = 0;       // pattern ids of A and B
+  std::shared_ptr<cht::Pattern> C;   // product pattern
+  int64_t npairs = 0;
+  cht::DevArray<int64_t> cseg;       // [nC + 1]
+  cht::DevArray<int32_t> pa, pb, pc; // per pair (sorted by C leaf, then K)
+  cht::DevArray<int32_t> order;      // schedule [nC]
+  // backward regroupings (built on first use)
+  bool have_bwd = false;
+  cht::DevArray<int64_t> segA, segB;      // [nA + 1], [nB + 1]
+  cht::DevArray<int32_t> dA_c, dA_b;      // pairs grouped by A leaf
+  cht::DevArray<int32_t> dB_a, dB_c;      // pairs grouped by B leaf
+  cht::DevArray<int32_t> idA, idB;        // identity schedules
+};

@@ -1,0 +1,304 @@
+// Numeric phase, FP64 (step S6; also the two sampled products of the
+// backward, S8): a persistent grouped leaf-GEMM.
+//
+// Paper, Section 3: leaf products are dense double-precision matrix products
+// (BLAS dgemm on the leaf's blocks); the multiply task adds the products of
+// the quadrant pairs.  Here each unit of work is one output leaf o:
+//     Z[o] = sum_{p in seg(o)} op(X[px[p]]) * op(Y[py[p]])
+// summed in the segment's order (ascending K for the forward product) in
+// registers, and stored once -- no atomics.  Units are taken from an atomic
+// counter in schedule order (longest segment first by default).
+//
+// Data movement: each CTA streams its pairs' two leaves (b*b doubles each,
+// contiguous) into a ring of shared-memory stages with one-dimensional TMA
+// bulk copies completing on an mbarrier per stage.  Every wait is bounded;
+// on expiry the CTA records DEV_STATUS_TIMEOUT, drains its copies in flight
+// and returns.
+//
+// Arithmetic: FP64 tensor-core MMA (mma.sync m8n8k4 f64, "DMMA"; engine 0)
+// or plain FP64 FMAs from a per-thread register tile (engine 1).
+#include <algorithm>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace cht {
+
+namespace {
+
+constexpr int kThreads = 128;  // 4 warps, a 2 x 2 grid of warp tiles
+constexpr int64_t kDrainBudgetNs = 2000000000LL;
+
+template <int B>
+struct LeafCfg {
+  static constexpr int kLeaf = B * B;
+  static constexpr int kStages = (B == 64) ? 2 : 3;
+  static constexpr size_t kSmem = sizeof(double) * 2 * kStages * kLeaf + 16 * kStages;
+};
+
+template <int B, bool TX>
+__device__ __forceinline__ double ldx(const double *xs, int row, int k) {
+  return TX ? xs[k * B + row] : xs[row * B + k];
+}
+template <int B, bool TY>
+__device__ __forceinline__ double ldy(const double *ys, int k, int col) {
+  return TY ? ys[col * B + k] : ys[k * B + col];
+}
+
+// Per-thread accumulator tile and the compute / store of one leaf product.
+template <int B, bool TX, bool TY, int ENGINE>
+struct Tile;
+
+// DMMA: warp tile (B/2) x (B/2) = MT x NT tiles of 8 x 8.
+template <int B, bool TX, bool TY>
+struct Tile<B, TX, TY, 0> {
+  static constexpr int WT = B / 2, MT = WT / 8, NT = WT / 8;
+  double acc[MT][NT][2];
+  __device__ void zero() {
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+      for (int j = 0; j < NT; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+  }
+  __device__ void mac(const double *xs, const double *ys) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = (warp >> 1) * WT, wn = (warp & 1) * WT;
+    const int gr = lane >> 2, gc = lane & 3;
+#pragma unroll 4
+    for (int k = 0; k < B; k += 4) {
+      double a[MT], b[NT];
+#pragma unroll
+      for (int i = 0; i < MT; ++i) a[i] = ldx<B, TX>(xs, wm + i * 8 + gr, k + gc);
+#pragma unroll
+      for (int j = 0; j < NT; ++j) b[j] = ldy<B, TY>(ys, k + gc, wn + j * 8 + gr);
+#pragma unroll
+      for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) dmma_8x8x4(acc[i][j][0], acc[i][j][1], a[i], b[j]);
+    }
+  }
+  __device__ void store(double *z) const {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = (warp >> 1) * WT, wn = (warp & 1) * WT;
+    const int gr = lane >> 2, gc = lane & 3;
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        double2 v = make_double2(acc[i][j][0], acc[i][j][1]);
+        *reinterpret_cast<double2 *>(z + (wm + i * 8 + gr) * B + wn + j * 8 + 2 * gc) = v;
+      }
+  }
+};
+
+// DFMA: thread tile RM x RN; 16 row groups x 8 column groups of threads.
+template <int B, bool TX, bool TY>
+struct Tile<B, TX, TY, 1> {
+  static constexpr int RM = B / 16, RN = B / 8;
+  double acc[RM][RN];
+  __device__ void zero() {
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; ++j) acc[i][j] = 0.0;
+  }
+  __device__ void mac(const double *xs, const double *ys) {
+    const int tr = threadIdx.x >> 3, tc = threadIdx.x & 7;
+#pragma unroll 2
+    for (int k = 0; k < B; ++k) {
+      double a[RM], b[RN];
+#pragma unroll
+      for (int i = 0; i < RM; ++i) a[i] = ldx<B, TX>(xs, tr * RM + i, k);
+#pragma unroll
+      for (int j = 0; j < RN; ++j) b[j] = ldy<B, TY>(ys, k, tc * RN + j);
+#pragma unroll
+      for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+  }
+  __device__ void store(double *z) const {
+    const int tr = threadIdx.x >> 3, tc = threadIdx.x & 7;
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; j += 2)
+        *reinterpret_cast<double2 *>(z + (tr * RM + i) * B + tc * RN + j) =
+            make_double2(acc[i][j], acc[i][j + 1]);
+  }
+};
+
+template <int B, bool TX, bool TY, int ENGINE>
+__global__ void __launch_bounds__(kThreads)
+    k_leafgemm_f64(const GemmWork w, int *__restrict__ status, int64_t wait_ns,
+                   unsigned long long *__restrict__ next_unit) {
+  using Cfg = LeafCfg<B>;
+  constexpr int S = Cfg::kStages, LEAF = Cfg::kLeaf;
+  constexpr uint32_t kBytes = LEAF * sizeof(double);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double *sx = reinterpret_cast<double *>(smem_raw);
+  double *sy = sx + S * LEAF;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sy + S * LEAF);
+  __shared__ long long s_unit;
+
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st) mbar_init(&full[st], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int64_t p, uint32_t st) {
+    const double *xsrc = w.X + static_cast<int64_t>(w.px[p]) * LEAF;
+    const double *ysrc = w.Y + static_cast<int64_t>(w.py[p]) * LEAF;
+    mbar_arrive_expect_tx(&full[st], 2 * kBytes);
+    bulk_g2s(sx + st * LEAF, xsrc, kBytes, &full[st]);
+    bulk_g2s(sy + st * LEAF, ysrc, kBytes, &full[st]);
+  };
+
+  Tile<B, TX, TY, ENGINE> tile;
+  uint32_t it = 0;  // pairs consumed so far by this CTA
+  for (;;) {
+    if (tid == 0) s_unit = static_cast<long long>(atomicAdd(next_unit, 1ULL));
+    __syncthreads();
+    const int64_t u = s_unit;
+    __syncthreads();
+    if (u >= w.nunits) break;
+    const int64_t o = w.order[u];
+    const int64_t p0 = w.seg[o], np = w.seg[o + 1] - p0;
+    tile.zero();
+    if (tid == 0)
+      for (int64_t j = 0; j < S - 1 && j < np; ++j) issue(p0 + j, (it + j) % S);
+    for (int64_t i = 0; i < np; ++i) {
+      if (tid == 0 && i + S - 1 < np) issue(p0 + i + S - 1, (it + i + S - 1) % S);
+      const uint32_t st = (it + i) % S, parity = ((it + i) / S) & 1u;
+      const bool ok = mbar_wait_bounded(&full[st], parity, wait_ns);
+      if (__syncthreads_or(!ok)) {
+        // Timed out: record it, let this CTA's copies in flight land, return.
+        if (tid == 0) {
+          atomicOr(status, DEV_STATUS_TIMEOUT);
+          const int64_t issued = (i + S < np) ? i + S : np;
+          for (int64_t j = i; j < issued; ++j)
+            mbar_wait_bounded(&full[(it + j) % S], ((it + j) / S) & 1u, kDrainBudgetNs);
+        }
+        __syncthreads();
+        return;
+      }
+      tile.mac(sx + st * LEAF, sy + st * LEAF);
+      __syncthreads();  // stage st may be refilled after this point
+    }
+    it += static_cast<uint32_t>(np);
+    tile.store(w.Z + o * LEAF);
+  }
+}
+
+template <int B, bool TX, bool TY, int ENGINE>
+int launch_t(const GemmWork &w, cudaStream_t s, int *status, unsigned long long *counter) {
+  using Cfg = LeafCfg<B>;
+  auto kern = k_leafgemm_f64<B, TX, TY, ENGINE>;
+  CHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(Cfg::kSmem)));
+  int sms = 0;
+  CHT_TRY(num_sms(&sms));
+  int per_sm = g_opt.ctas_per_sm;
+  if (per_sm <= 0) {
+    int occ = 0;
+    CHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, Cfg::kSmem));
+    per_sm = std::max(1, occ);
+  }
+  int64_t grid = std::min<int64_t>(w.nunits, static_cast<int64_t>(sms) * per_sm);
+  if (grid < 1) grid = 1;
+  kern<<<static_cast<unsigned>(grid), kThreads, Cfg::kSmem, s>>>(w, status, g_opt.wait_budget_ns,
+                                                                 counter);
+  return launched("leafgemm_f64");
+}
+
+template <int B, int ENGINE>
+int launch_b(const GemmWork &w, cudaStream_t s, int *status, unsigned long long *counter) {
+  if (!w.trans_x && !w.trans_y) return launch_t<B, false, false, ENGINE>(w, s, status, counter);
+  if (!w.trans_x && w.trans_y) return launch_t<B, false, true, ENGINE>(w, s, status, counter);
+  if (w.trans_x && !w.trans_y) return launch_t<B, true, false, ENGINE>(w, s, status, counter);
+  return launch_t<B, true, true, ENGINE>(w, s, status, counter);
+}
+
+// ----------------------------------------------------------- FP64 peak --
+__global__ void k_peak_dfma(double *out, int iters) {
+  double a[8], x = 1.0 + 1e-9 * threadIdx.x, y = 0.999999999;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = i;
+  for (int n = 0; n < iters; ++n)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = fma(a[i], y, x);
+  double s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += a[i];
+  if (s == 12345.0) out[0] = s;
+}
+
+__global__ void k_peak_dmma(double *out, int iters) {
+  double d[8][2];
+  const double a = 1.0 + 1e-9 * threadIdx.x, b = 0.999999999;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d[i][0] = d[i][1] = i;
+  for (int n = 0; n < iters; ++n)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dmma_8x8x4(d[i][0], d[i][1], a, b);
+  double s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += d[i][0] + d[i][1];
+  if (s == 12345.0) out[0] = s;
+}
+
+}  // namespace
+
+int launch_leafgemm_f64(const GemmWork &w, cudaStream_t s) {
+  if (w.nunits <= 0) return CHT_OK;
+  int *status = nullptr;
+  CHT_TRY(device_status_ptr(&status));
+  DevArray<unsigned long long> counter;
+  CHT_TRY(counter.alloc(1, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), s));
+  const int engine = g_opt.fp64_engine;
+  if (w.b == 64)
+    return engine ? launch_b<64, 1>(w, s, status, counter.p) : launch_b<64, 0>(w, s, status, counter.p);
+  if (w.b == 32)
+    return engine ? launch_b<32, 1>(w, s, status, counter.p) : launch_b<32, 0>(w, s, status, counter.p);
+  set_error("leaf size %d: the numeric kernels take b = 32 or b = 64", w.b);
+  return CHT_ERR_UNSUPPORTED;
+}
+
+int launch_fp64_peak(int engine, cudaStream_t s, double *tflops) {
+  int sms = 0;
+  CHT_TRY(num_sms(&sms));
+  DevArray<double> out;
+  CHT_TRY(out.alloc(1, s));
+  const int threads = 256, per_sm = 4, iters = 4096;
+  const int grid = sms * per_sm;
+  cudaEvent_t e0, e1;
+  CHT_CUDA_TRY(cudaEventCreate(&e0));
+  CHT_CUDA_TRY(cudaEventCreate(&e1));
+  // warm up, then time
+  for (int rep = 0; rep < 2; ++rep) {
+    if (rep == 1) CHT_CUDA_TRY(cudaEventRecord(e0, s));
+    if (engine == 0)
+      k_peak_dmma<<<grid, threads, 0, s>>>(out.p, iters);
+    else
+      k_peak_dfma<<<grid, threads, 0, s>>>(out.p, iters);
+    CHT_TRY(launched("fp64_peak"));
+  }
+  CHT_CUDA_TRY(cudaEventRecord(e1, s));
+  CHT_CUDA_TRY(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CHT_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // per thread per iteration: 8 FMAs (DFMA); per warp per iteration:
+  // 8 MMAs of 8x8x4 (DMMA)
+  const double warps = static_cast<double>(grid) * threads / 32.0;
+  const double flops = engine == 0 ? warps * iters * 8.0 * 2.0 * 8 * 8 * 4
+                                   : static_cast<double>(grid) * threads * iters * 8.0 * 2.0;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  return CHT_OK;
+}
+
+}  // namespace cht

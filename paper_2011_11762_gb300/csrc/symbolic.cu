@@ -1,0 +1,382 @@
+// Symbolic phase of C = A*B (steps S1-S5): the (A-leaf, B-leaf) pairs, the
+// product's leaf pattern, each C leaf's pair segment and the work schedule.
+//
+// Paper, Section 2: the multiply works level by level on quadrant pairs and
+// yields nil whenever an operand is nil, so only pairs of stored leaves that
+// meet on an inner index K contribute, and C's stored leaves are exactly the
+// (I, J) reached by such a pair.  Flattened, the recursion's leaf-level work
+// is the set of triples (I, K, J) with A(I, K) and B(K, J) stored.  Sorting the
+// triples by (Morton(I, J), K) groups them per C leaf in Morton order, with
+// ascending K inside each group.  All of this is exact integer work.
+#include "device.cuh"
+#include "internal.h"
+
+namespace cht {
+
+namespace {
+
+unsigned grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 65535LL * 8) g = 65535LL * 8;
+  return static_cast<unsigned>(g);
+}
+
+#define GRID_STRIDE(i, n)                                                              \
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < (n); \
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+
+// S1: pairs of A leaf (I, K) = stored leaves in row K of B.
+__global__ void k_pair_count(const int32_t *__restrict__ a_col, int64_t nA,
+                             const int64_t *__restrict__ b_rowptr, int32_t *__restrict__ cnt) {
+  GRID_STRIDE(a, nA) {
+    const int32_t K = a_col[a];
+    cnt[a] = static_cast<int32_t>(b_rowptr[K + 1] - b_rowptr[K]);
+  }
+}
+
+// S3: one warp per A leaf writes its pairs: key (Morton(I, J) << L) | K.
+__global__ void k_pair_fill(const int32_t *__restrict__ a_row, const int32_t *__restrict__ a_col,
+                            int64_t nA, const int64_t *__restrict__ off,
+                            const int64_t *__restrict__ b_rowptr,
+                            const int32_t *__restrict__ b_rowcol,
+                            const int32_t *__restrict__ b_rowleaf, int L,
+                            uint64_t *__restrict__ key, int32_t *__restrict__ pa,
+                            int32_t *__restrict__ pb, int32_t *__restrict__ idx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t a = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5; a < nA;
+       a += warps) {
+    const uint32_t I = static_cast<uint32_t>(a_row[a]);
+    const uint32_t K = static_cast<uint32_t>(a_col[a]);
+    const int64_t base = off[a], cnt = off[a + 1] - off[a];
+    const int64_t rs = b_rowptr[K];
+    for (int64_t t = lane; t < cnt; t += 32) {
+      const int64_t p = base + t;
+      const uint32_t J = static_cast<uint32_t>(b_rowcol[rs + t]);
+      key[p] = (morton(I, J) << L) | K;
+      pa[p] = static_cast<int32_t>(a);
+      pb[p] = b_rowleaf[rs + t];
+      idx[p] = static_cast<int32_t>(p);
+    }
+  }
+}
+
+// S4 (after the sort): permute the pair payloads into sorted order.
+__global__ void k_pair_gather(const int32_t *__restrict__ sidx, int64_t P,
+                              const int32_t *__restrict__ pa_in, const int32_t *__restrict__ pb_in,
+                              int32_t *__restrict__ pa, int32_t *__restrict__ pb) {
+  GRID_STRIDE(i, P) {
+    const int32_t s = sidx[i];
+    pa[i] = pa_in[s];
+    pb[i] = pb_in[s];
+  }
+}
+
+// S4: a new C leaf starts where the Morton(I, J) part of the key changes.
+__global__ void k_heads(const uint64_t *__restrict__ skey, int64_t P, int L,
+                        int32_t *__restrict__ head) {
+  GRID_STRIDE(i, P) head[i] = (i == 0 || (skey[i] >> L) != (skey[i - 1] >> L)) ? 1 : 0;
+}
+
+// S4: C leaf of every pair, and each C leaf's Morton key and segment start.
+__global__ void k_segments(const uint64_t *__restrict__ skey, const int64_t *__restrict__ cpos,
+                           const int32_t *__restrict__ head, int64_t P, int L, int64_t nC,
+                           uint64_t *__restrict__ ckey, int64_t *__restrict__ cseg,
+                           int32_t *__restrict__ pc) {
+  GRID_STRIDE(i, P) {
+    const int64_t c = cpos[i] - (head[i] ? 0 : 1);
+    pc[i] = static_cast<int32_t>(c);
+    if (head[i]) {
+      cseg[c] = i;
+      ckey[c] = skey[i] >> L;
+    }
+    if (i == 0) cseg[nC] = P;
+  }
+}
+
+// S5: longest-first order key (stable sort keeps Morton order among ties).
+__global__ void k_lpt_keys(const int64_t *__restrict__ seg, int64_t n, uint64_t *__restrict__ key,
+                           int32_t *__restrict__ idx) {
+  GRID_STRIDE(u, n) {
+    int64_t len = seg[u + 1] - seg[u];
+    if (len > 0xffffffffLL) len = 0xffffffffLL;
+    key[u] = 0xffffffffULL - static_cast<uint64_t>(len);
+    idx[u] = static_cast<int32_t>(u);
+  }
+}
+
+__global__ void k_iota(int32_t *__restrict__ v, int64_t n) {
+  GRID_STRIDE(i, n) v[i] = static_cast<int32_t>(i);
+}
+
+// Backward regrouping keys: (unit << L) | minor, payload = pair index.
+__global__ void k_regroup_keys(const int32_t *__restrict__ unit, const int32_t *__restrict__ pc,
+                               const int32_t *__restrict__ c_minor, int64_t P, int L,
+                               uint64_t *__restrict__ key, int32_t *__restrict__ idx) {
+  GRID_STRIDE(p, P) {
+    key[p] = (static_cast<uint64_t>(unit[p]) << L) | static_cast<uint32_t>(c_minor[pc[p]]);
+    idx[p] = static_cast<int32_t>(p);
+  }
+}
+
+__global__ void k_gather2(const int32_t *__restrict__ sidx, int64_t P,
+                          const int32_t *__restrict__ u_in, const int32_t *__restrict__ v_in,
+                          int32_t *__restrict__ u_out, int32_t *__restrict__ v_out) {
+  GRID_STRIDE(i, P) {
+    const int32_t s = sidx[i];
+    u_out[i] = u_in[s];
+    v_out[i] = v_in[s];
+  }
+}
+
+__global__ void k_count_units(const int32_t *__restrict__ unit, int64_t P, int32_t *__restrict__ cnt) {
+  GRID_STRIDE(p, P) atomicAdd(&cnt[unit[p]], 1);
+}
+
+// Recompute path: keep a triple only if dC stores leaf (I, J); pc = its index.
+__global__ void k_lookup_dc(const uint64_t *__restrict__ key, int64_t P, int L, const int64_t *__restrict__ c_rowptr,
+                            const int32_t *__restrict__ c_rowcol,
+                            const int32_t *__restrict__ c_rowleaf, int32_t *__restrict__ pc,
+                            int32_t *__restrict__ keep) {
+  GRID_STRIDE(p, P) {
+    const uint64_t m = key[p] >> L;
+    const int32_t I = static_cast<int32_t>(morton_row(m)), J = static_cast<int32_t>(morton_col(m));
+    int64_t lo = c_rowptr[I], hi = c_rowptr[I + 1];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (c_rowcol[mid] < J) lo = mid + 1; else hi = mid;
+    }
+    const bool found = lo < c_rowptr[I + 1] && c_rowcol[lo] == J;
+    pc[p] = found ? c_rowleaf[lo] : -1;
+    keep[p] = found ? 1 : 0;
+  }
+}
+
+__global__ void k_compact3(const int32_t *__restrict__ keep, const int64_t *__restrict__ pos,
+                           int64_t P, const int32_t *__restrict__ a, const int32_t *__restrict__ b,
+                           const int32_t *__restrict__ c, int32_t *__restrict__ ao,
+                           int32_t *__restrict__ bo, int32_t *__restrict__ co) {
+  GRID_STRIDE(p, P) {
+    if (!keep[p]) continue;
+    const int64_t q = pos[p];
+    ao[q] = a[p];
+    bo[q] = b[p];
+    co[q] = c[p];
+  }
+}
+
+}  // namespace
+
+// Triples (I, K, J) of stored A(I,K), B(K,J), sorted by (Morton(I,J), K):
+// outputs key[P] (sorted), pa[P], pb[P].  Synchronises once to read P.
+static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
+                        DevArray<uint64_t> &skey, DevArray<int32_t> &pa, DevArray<int32_t> &pb,
+                        int64_t *P_out) {
+  const int L = A.L;
+  DevArray<int32_t> cnt;
+  DevArray<int64_t> off;
+  CHT_TRY(cnt.alloc(A.nnz, s));
+  CHT_TRY(off.alloc(A.nnz + 1, s));
+  if (A.nnz > 0) {
+    k_pair_count<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.bcol.p, A.nnz, B.rowptr.p, cnt.p);
+    CHT_TRY(launched("pair_count"));
+  }
+  CHT_TRY(scan_exclusive(cnt.p, off.p, A.nnz, s));
+  int64_t P = 0;
+  CHT_TRY(read_i64(off.p + A.nnz, &P, s));
+  if (P > 0x7fffffffLL) {
+    set_error("%lld leaf pairs exceed the int32 pair index", (long long)P);
+    return CHT_ERR_UNSUPPORTED;
+  }
+  DevArray<uint64_t> key;
+  DevArray<int32_t> idx, sidx, pa0, pb0;
+  CHT_TRY(key.alloc(P, s));
+  CHT_TRY(idx.alloc(P, s));
+  CHT_TRY(sidx.alloc(P, s));
+  CHT_TRY(pa0.alloc(P, s));
+  CHT_TRY(pb0.alloc(P, s));
+  CHT_TRY(skey.alloc(P, s));
+  CHT_TRY(pa.alloc(P, s));
+  CHT_TRY(pb.alloc(P, s));
+  if (P > 0) {
+    k_pair_fill<<<grid_for(A.nnz * 32, 256), 256, 0, s>>>(A.brow.p, A.bcol.p, A.nnz, off.p,
+                                                          B.rowptr.p, B.rowcol.p, B.rowleaf.p, L,
+                                                          key.p, pa0.p, pb0.p, idx.p);
+    CHT_TRY(launched("pair_fill"));
+    CHT_TRY(radix_sort_pairs(key.p, idx.p, skey.p, sidx.p, P, 3 * L, s));
+    k_pair_gather<<<grid_for(P, 256), 256, 0, s>>>(sidx.p, P, pa0.p, pb0.p, pa.p, pb.p);
+    CHT_TRY(launched("pair_gather"));
+  }
+  *P_out = P;
+  return CHT_OK;
+}
+
+int schedule_units(const int64_t *seg, int64_t n, int32_t *order, cudaStream_t s) {
+  if (n <= 0) return CHT_OK;
+  if (g_opt.schedule == 1) {
+    k_iota<<<grid_for(n, 256), 256, 0, s>>>(order, n);
+    return launched("iota");
+  }
+  DevArray<uint64_t> key, skey;
+  DevArray<int32_t> idx;
+  CHT_TRY(key.alloc(n, s));
+  CHT_TRY(skey.alloc(n, s));
+  CHT_TRY(idx.alloc(n, s));
+  k_lpt_keys<<<grid_for(n, 256), 256, 0, s>>>(seg, n, key.p, idx.p);
+  CHT_TRY(launched("lpt_keys"));
+  return radix_sort_pairs(key.p, idx.p, skey.p, order, n, 32, s);
+}
+
+int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out) {
+  const int L = A.L;
+  if (3 * L > 63) {
+    set_error("leaf grid of %lld per side is too large for 64-bit pair keys", (long long)A.G);
+    return CHT_ERR_UNSUPPORTED;
+  }
+  auto plan = std::make_unique<cht_plan>();
+  plan->id = next_id();
+  plan->n = A.n;
+  plan->b = A.b;
+  plan->nA = A.nnz;
+  plan->nB = B.nnz;
+  plan->patA = A.id;
+  plan->patB = B.id;
+
+  DevArray<uint64_t> skey;
+  DevArray<int32_t> pa, pb;
+  int64_t P = 0;
+  CHT_TRY(make_triples(A, B, s, skey, pa, pb, &P));
+  plan->npairs = P;
+
+  DevArray<int32_t> head;
+  DevArray<int64_t> cpos;
+  CHT_TRY(head.alloc(P, s));
+  CHT_TRY(cpos.alloc(P + 1, s));
+  if (P > 0) {
+    k_heads<<<grid_for(P, 256), 256, 0, s>>>(skey.p, P, L, head.p);
+    CHT_TRY(launched("heads"));
+  }
+  CHT_TRY(scan_exclusive(head.p, cpos.p, P, s));
+  int64_t nC = 0;
+  CHT_TRY(read_i64(cpos.p + P, &nC, s));
+
+  auto C = std::make_shared<Pattern>();
+  C->n = A.n;
+  C->b = A.b;
+  C->G = A.G;
+  C->L = L;
+  C->nnz = nC;
+  C->id = next_id();
+  CHT_TRY(C->mkey.alloc(nC, s));
+  CHT_TRY(plan->cseg.alloc(nC + 1, s));
+  CHT_TRY(plan->pc.alloc(P, s));
+  CHT_TRY(plan->order.alloc(nC, s));
+  if (P > 0) {
+    k_segments<<<grid_for(P, 256), 256, 0, s>>>(skey.p, cpos.p, head.p, P, L, nC, C->mkey.p,
+                                                plan->cseg.p, plan->pc.p);
+    CHT_TRY(launched("segments"));
+  } else {
+    CHT_CUDA_TRY(cudaMemsetAsync(plan->cseg.p, 0, sizeof(int64_t), s));
+  }
+  CHT_TRY(build_pattern_index(*C, s));
+  CHT_TRY(schedule_units(plan->cseg.p, nC, plan->order.p, s));
+  plan->pa = std::move(pa);
+  plan->pb = std::move(pb);
+  plan->C = std::move(C);
+  *out = plan.release();
+  return CHT_OK;
+}
+
+// Regroups triples (pa, pb, pc over C pattern `Cp`) by A leaf (ordered by J)
+// and by B leaf (ordered by I) for the two sampled backward products.
+static int regroup(const Pattern &A, const Pattern &B, const Pattern &Cp, const int32_t *pa,
+                   const int32_t *pb, const int32_t *pc, int64_t P, cudaStream_t s,
+                   cht_plan &out) {
+  const int L = A.L;
+  CHT_TRY(out.segA.alloc(A.nnz + 1, s));
+  CHT_TRY(out.segB.alloc(B.nnz + 1, s));
+  CHT_TRY(out.dA_c.alloc(P, s));
+  CHT_TRY(out.dA_b.alloc(P, s));
+  CHT_TRY(out.dB_a.alloc(P, s));
+  CHT_TRY(out.dB_c.alloc(P, s));
+  CHT_TRY(out.idA.alloc(A.nnz, s));
+  CHT_TRY(out.idB.alloc(B.nnz, s));
+  DevArray<uint64_t> key, skey;
+  DevArray<int32_t> idx, sidx, cnt;
+  CHT_TRY(key.alloc(P, s));
+  CHT_TRY(skey.alloc(P, s));
+  CHT_TRY(idx.alloc(P, s));
+  CHT_TRY(sidx.alloc(P, s));
+  const int ubitsA = bits_for(A.nnz + 1), ubitsB = bits_for(B.nnz + 1);
+  // dA: units = A leaves, minor = J (C leaf column)
+  CHT_TRY(cnt.alloc(A.nnz, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * cnt.n, s));
+  if (P > 0) {
+    k_regroup_keys<<<grid_for(P, 256), 256, 0, s>>>(pa, pc, Cp.bcol.p, P, L, key.p, idx.p);
+    CHT_TRY(launched("regroup_keys"));
+    CHT_TRY(radix_sort_pairs(key.p, idx.p, skey.p, sidx.p, P, ubitsA + L, s));
+    k_gather2<<<grid_for(P, 256), 256, 0, s>>>(sidx.p, P, pc, pb, out.dA_c.p, out.dA_b.p);
+    CHT_TRY(launched("gather2"));
+    k_count_units<<<grid_for(P, 256), 256, 0, s>>>(pa, P, cnt.p);
+    CHT_TRY(launched("count_units"));
+  }
+  CHT_TRY(scan_exclusive(cnt.p, out.segA.p, A.nnz, s));
+  // dB: units = B leaves, minor = I (C leaf row)
+  CHT_TRY(cnt.alloc(B.nnz, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * cnt.n, s));
+  if (P > 0) {
+    k_regroup_keys<<<grid_for(P, 256), 256, 0, s>>>(pb, pc, Cp.brow.p, P, L, key.p, idx.p);
+    CHT_TRY(launched("regroup_keys"));
+    CHT_TRY(radix_sort_pairs(key.p, idx.p, skey.p, sidx.p, P, ubitsB + L, s));
+    k_gather2<<<grid_for(P, 256), 256, 0, s>>>(sidx.p, P, pa, pc, out.dB_a.p, out.dB_c.p);
+    CHT_TRY(launched("gather2"));
+    k_count_units<<<grid_for(P, 256), 256, 0, s>>>(pb, P, cnt.p);
+    CHT_TRY(launched("count_units"));
+  }
+  CHT_TRY(scan_exclusive(cnt.p, out.segB.p, B.nnz, s));
+  CHT_TRY(schedule_units(out.segA.p, A.nnz, out.idA.p, s));
+  CHT_TRY(schedule_units(out.segB.p, B.nnz, out.idB.p, s));
+  out.have_bwd = true;
+  return CHT_OK;
+}
+
+int backward_lists_from_plan(cht_plan &plan, const Pattern &A, const Pattern &B,
+                             cudaStream_t s) {
+  if (plan.have_bwd) return CHT_OK;
+  return regroup(A, B, *plan.C, plan.pa.p, plan.pb.p, plan.pc.p, plan.npairs, s, plan);
+}
+
+// Triples restricted to dC's stored leaves, regrouped for the backward.
+int backward_lists_recompute(const Pattern &A, const Pattern &B, const Pattern &dC,
+                             cudaStream_t s, cht_plan &out) {
+  DevArray<uint64_t> skey;
+  DevArray<int32_t> pa, pb;
+  int64_t P = 0;
+  CHT_TRY(make_triples(A, B, s, skey, pa, pb, &P));
+  DevArray<int32_t> pc, keep, ka, kb, kc;
+  DevArray<int64_t> pos;
+  CHT_TRY(pc.alloc(P, s));
+  CHT_TRY(keep.alloc(P, s));
+  CHT_TRY(pos.alloc(P + 1, s));
+  if (P > 0) {
+    k_lookup_dc<<<grid_for(P, 256), 256, 0, s>>>(skey.p, P, A.L, dC.rowptr.p,
+                                                 dC.rowcol.p, dC.rowleaf.p, pc.p, keep.p);
+    CHT_TRY(launched("lookup_dc"));
+  }
+  CHT_TRY(scan_exclusive(keep.p, pos.p, P, s));
+  int64_t Pk = 0;
+  CHT_TRY(read_i64(pos.p + P, &Pk, s));
+  CHT_TRY(ka.alloc(Pk, s));
+  CHT_TRY(kb.alloc(Pk, s));
+  CHT_TRY(kc.alloc(Pk, s));
+  if (P > 0) {
+    k_compact3<<<grid_for(P, 256), 256, 0, s>>>(keep.p, pos.p, P, pa.p, pb.p, pc.p, ka.p, kb.p,
+                                                kc.p);
+    CHT_TRY(launched("compact3"));
+  }
+  out.npairs = Pk;
+  return regroup(A, B, dC, ka.p, kb.p, kc.p, Pk, s, out);
+}
+
+}  // namespace cht

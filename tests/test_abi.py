@@ -1,0 +1,82 @@
+"""The C-ABI library builds, loads, and exports every function that
+include/*.h declares (no GPU needed; no compute calls)."""
+
+from __future__ import annotations
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(cht_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2011_11762_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("cht_mat_from_blocks", "cht_symbolic_multiply", "cht_multiply",
+                     "cht_multiply_backward", "cht_to_dense"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in sorted(_declared_functions()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_the_header():
+    from paper_2011_11762_gb300 import _lib
+    assert _declared_functions() <= set(_lib.SIGNATURES)
+
+
+def test_host_only_calls(libpath):
+    import paper_2011_11762_gb300 as cht
+    lib = cht.load()
+    assert lib.cht_status_str(cht.CHT_ERR_TIMEOUT) == b"CHT_ERR_TIMEOUT"
+    assert lib.cht_status_str(0) == b"CHT_OK"
+    assert lib.cht_set_option(cht.OPT_SCHEDULE, 7) == cht.CHT_ERR_INVALID
+    assert b"invalid option" in lib.cht_last_error()
+    v = ctypes.c_int64()
+    assert lib.cht_get_option(cht.OPT_WAIT_BUDGET_NS, ctypes.byref(v)) == 0
+    assert v.value == 2_000_000_000
+    # argument checks happen on the host before any device work
+    h = ctypes.c_void_p()
+    assert lib.cht_mat_from_blocks(100, 32, 0, None, None, None, None,
+                                   ctypes.byref(h)) == cht.CHT_ERR_INVALID
+    assert lib.cht_mat_from_blocks(128, 16, 0, None, None, None, None,
+                                   ctypes.byref(h)) == cht.CHT_ERR_INVALID
+    assert lib.cht_multiply(None, None, None, 0, 0, None, None, None) == cht.CHT_ERR_INVALID
+    assert lib.cht_set_allocator(ctypes.c_void_p(1), None, None) == cht.CHT_ERR_INVALID
+    assert lib.cht_batch_create(0, None, None, None, 0, 0, None,
+                                ctypes.byref(h)) == cht.CHT_ERR_INVALID
+
+
+def test_product_path_has_no_oracle_dependency():
+    # the GPU library and its binding never import or link the oracle
+    pkg = os.path.join(ROOT, "paper_2011_11762_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*"), recursive=True):
+        if os.path.isdir(path) or "_build" in path:
+            continue
+        if path.endswith((".py", ".cu", ".cuh", ".h")):
+            text = open(path).read()
+            assert "import oracle" not in text and "from oracle" not in text, path
+            assert "liborc" not in text, path
