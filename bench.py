@@ -1,0 +1,463 @@
+#!/usr/bin/env python
+"""Benchmark of the block-sparse quadtree product C = A*B on GB300.
+
+Metric: useful TFLOP/s = 2 b^3 P / time, with P the number of (A-leaf,
+B-leaf) pairs (the paper's work definition; Table 1's flop counts are
+2 * sum_k nnz(A[:,k]) nnz(B[k,:])).
+
+Default workload: 3D-locality product, N = 65536 points on a jittered
+32x32x64 lattice in Morton order, 64x64 leaves, leaf (I, J) stored iff the
+point groups come closer than 6, entries exp(-0.5 r) U[-1, 1].  One step =
+symbolic phase + FP64 numeric phase (one full product); inputs (4 GB) are
+resident in HBM and larger than L2.
+
+Further sections on their own workloads (each reported in the same JSON
+line): the split-precision form, the backward of L = ||A B - T||_F^2, and
+the batched form.
+
+``--impl reference`` times the CPU oracle (the plain recursive quadtree
+multiply) on a bounded sample of the same workload on the host cores.
+
+Run: python bench.py [--gpus N] [--steps K] [--warmup W]; for N > 1 under
+torchrun, every rank runs its own replica of the workload (weak scaling,
+no collective on the data path) and the slowest rank's time is reported.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "block-sparse C=A·B useful TFLOP/s, FP64 vs split form at stated rel. error"
+UNIT = "TFLOP/s"
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, profiling recipe's nominal figure
+L2_BYTES = 129e6
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=65536, help="3D-locality workload size")
+    ap.add_argument("--sections", default="split,backward,batched",
+                    help="extra sections (comma list; '' for none)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------- distributed --
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- workloads --
+
+def locality_workload(n: int):
+    import workloads as w
+    a, b = w.config2(n)
+    return a, b
+
+
+def unique_bytes(nA, nB, nC, b):
+    return (nA + nB + nC) * b * b * 8
+
+
+# -------------------------------------------------------------- GPU timing --
+
+class Timer:
+    """CUDA-event timing of a region on the launching stream."""
+
+    def __init__(self, stream):
+        import torch
+        self.torch = torch
+        self.stream = stream
+        self.pairs = []
+
+    def start(self):
+        e = self.torch.cuda.Event(enable_timing=True)
+        e.record(self.stream)
+        return e
+
+    def stop(self, e0):
+        e1 = self.torch.cuda.Event(enable_timing=True)
+        e1.record(self.stream)
+        self.pairs.append((e0, e1))
+
+    def ms(self):
+        self.torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in self.pairs]
+
+
+def fp64_main(args, world, rank, cht, torch):
+    """The headline: symbolic + FP64 numeric phase on the locality workload."""
+    a, b = locality_workload(args.n)
+    A, B = cht.from_block_matrix(a), cht.from_block_matrix(b)
+    stream = torch.cuda.current_stream()
+    plan = cht.cht_symbolic_multiply(A, B)
+    C, _ = cht.cht_multiply(plan, A, B, sync=True)
+    del C
+    flops = plan.useful_flops
+    nbytes = unique_bytes(A.nblocks, B.nblocks, plan.nnzb_C, A.b)
+
+    def step(timer=None):
+        p = cht.cht_symbolic_multiply(A, B)
+        e = timer.start() if timer else None
+        out, _ = cht.cht_multiply(p, A, B)
+        if timer:
+            timer.stop(e)
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    cht.sync_status()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    launches0 = cht.launch_count()
+    kern = Timer(stream)
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e_start.record(stream)
+    for _ in range(args.steps):
+        step(kern)
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = cht.launch_count() - launches0
+    clk = clocks.stop()
+    cht.sync_status()
+    total_ms = max_over_ranks(e_start.elapsed_time(e_end), world)
+    kms = kern.ms()
+    kernel_ms = statistics.mean(kms)
+    ms_per_step = total_ms / args.steps
+    value = flops * world * args.steps / (total_ms * 1e-3) / 1e12
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    return {
+        "value": value, "ms_per_step": ms_per_step, "flops": flops, "npairs": plan.npairs,
+        "nC": plan.nnzb_C, "nA": A.nblocks, "nB": B.nblocks, "b": A.b,
+        "unique_bytes": nbytes, "kernel_ms": kernel_ms, "kernel_achieved": achieved,
+        "launches": launches, "clocks": clk, "inputs_bytes": (A.nblocks + B.nblocks) * A.b ** 2 * 8,
+        "symbolic_ms": ms_per_step - kernel_ms,
+        "host": (a, b),
+    }
+
+
+def fp64_e2e(args, world, cht, torch, a, b):
+    """Same metric through the public API with host buffers: H2D of the
+    leaf lists from pinned memory, build, symbolic, multiply, D2H of C."""
+    import numpy as np
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    ha = [pin(a.brow), pin(a.bcol), pin(a.vals)]
+    hb = [pin(b.brow), pin(b.bcol), pin(b.vals)]
+    h2d = sum(t.numel() * t.element_size() for t in ha + hb)
+    stream = torch.cuda.current_stream()
+    out_host = None
+    flops = None
+
+    def step():
+        nonlocal out_host, flops
+        da = [t.to("cuda", non_blocking=True) for t in ha]
+        db = [t.to("cuda", non_blocking=True) for t in hb]
+        A = cht.cht_mat_from_blocks(a.n, a.b, *da)
+        B = cht.cht_mat_from_blocks(b.n, b.b, *db)
+        p = cht.cht_symbolic_multiply(A, B)
+        C, _ = cht.cht_multiply(p, A, B)
+        v = C.values()
+        if out_host is None or out_host.numel() != v.numel():
+            out_host = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+        out_host.copy_(v, non_blocking=True)
+        flops = p.useful_flops
+        stream.synchronize()
+        return v.numel() * 8
+
+    d2h = 0
+    for _ in range(max(1, args.warmup)):
+        d2h = step()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    el = max_over_ranks(time.perf_counter() - t0, world)
+    return {"value": flops * world * args.steps / el / 1e12, "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": el * 1e3 / args.steps}
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+def oracle_sample(a, b, target_s: float):
+    """Time the CPU oracle on the first R leaf rows of A times B (an exact
+    slice of the product: C's first R leaf rows), R sized so the run takes
+    about target_s seconds.  Returns (tflops, seconds, pairs, R, threads)."""
+    import numpy as np
+
+    import oracle
+    import workloads as w
+
+    def sub(rows):
+        keep = a.brow < rows
+        return w.BlockMatrix(a.n, a.b, a.brow[keep], a.bcol[keep], a.vals[keep])
+
+    OB = oracle.OMatrix.from_block_matrix(b)
+    rows = 2
+    while True:
+        OA = oracle.OMatrix.from_block_matrix(sub(rows))
+        t0 = time.perf_counter()
+        _, npairs = OA.multiply(OB)
+        dt = time.perf_counter() - t0
+        if dt >= target_s * 0.5 or rows >= a.grid:
+            flops = 2 * a.b ** 3 * npairs
+            return flops / dt / 1e12, dt, npairs, rows, oracle.threads()
+        scale = target_s / max(dt, 1e-3)
+        rows = int(min(a.grid, max(rows + 1, math.floor(rows * min(scale, 16.0)))))
+        del OA
+        _ = np
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    a, b = locality_workload(args.n)
+    # calibrate the sample so that K + W steps take a few minutes
+    per_step = min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup))
+    tf0, dt0, npairs0, rows, threads = oracle_sample(a, b, per_step)
+    import workloads as w
+    keep = a.brow < rows
+    sa = w.BlockMatrix(a.n, a.b, a.brow[keep], a.bcol[keep], a.vals[keep])
+    OA, OB = oracle.OMatrix.from_block_matrix(sa), oracle.OMatrix.from_block_matrix(b)
+    times = []
+    npairs = 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, npairs = OA.multiply(OB)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    flops = 2 * a.b ** 3 * npairs
+    total = sum(times)
+    value = flops * len(times) / total / 1e12
+    sample = (f"first {rows} of {a.grid} leaf rows of A times B ({npairs} leaf pairs, "
+              f"{flops / 1e9:.1f} GFLOP per step) of the 3D-locality N={args.n} b={a.b} product")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total * 1e3 / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"3d_locality_N{args.n}_b{a.b}_cutoff6", "n": args.n,
+                   "leaf": a.b, "l2": "CPU run"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ main --
+
+def read_profile_traffic(kernel: str):
+    """Per-launch DRAM traffic recorded from an ncu capture (profiles/)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for ln in open(path):
+        if ":" in ln and not ln.startswith("#"):
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    return vals
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+
+    import paper_2011_11762_gb300 as cht
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    cht.load()
+
+    res = fp64_main(args, world, rank, cht, torch)
+    a, b = res.pop("host")
+    fp64_peak_meas = max(cht.measure_fp64_peak(1), cht.measure_fp64_peak(0))
+
+    extra = {}
+    sections = [s for s in args.sections.split(",") if s and s != "none"]
+    for sec in sections:
+        fn = globals().get(f"section_{sec}")
+        if fn is None:
+            extra[sec] = {"status": "not built"}
+            continue
+        try:
+            extra[sec] = fn(args, world, cht, torch)
+        except Exception as e:  # report, do not hide the headline
+            extra[sec] = {"status": "error", "error": f"{type(e).__name__}: {e}"}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = fp64_e2e(args, world, cht, torch, a, b)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        tf, dt, npairs, rows, threads = oracle_sample(a, b, args.cpu_seconds)
+        cpu = {"value": tf, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": (f"first {rows} of {a.grid} leaf rows of A times B "
+                          f"({npairs} leaf pairs, {dt:.1f} s) of the same workload")}
+
+    prof = read_profile_traffic("leafgemm_f64_3d_locality")
+    traffic = None
+    if prof and "dram_bytes_per_pair" in prof:
+        traffic = float(prof["dram_bytes_per_pair"]) * res["npairs"]
+    roofline = {
+        "kernel": "k_leafgemm_f64 (DFMA)", "bound": "alu",
+        "achieved": res["kernel_achieved"], "peak": FP64_NOMINAL_TFLOPS, "unit": UNIT,
+        "frac": res["kernel_achieved"] / FP64_NOMINAL_TFLOPS, "traffic": traffic,
+        "peak_source": ("GB300 nominal dense FP64 (profiling recipe; no FP64 entry in the "
+                        "measured peaks); FP64 microbenchmark on this GPU: "
+                        f"{fp64_peak_meas:.3f} TFLOP/s"),
+        "algorithmic_flops_per_launch": res["flops"],
+        "hbm_floor_ms": res["unique_bytes"] / 6760.6e9 * 1e3,
+    }
+    line = {
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"3d_locality_N{args.n}_b{res['b']}_cutoff6",
+                   "n": args.n, "leaf": res["b"], "pairs": res["npairs"], "nnzb_A": res["nA"],
+                   "nnzb_B": res["nB"], "nnzb_C": res["nC"], "step": "symbolic + FP64 numeric",
+                   "l2": f"inputs {res['inputs_bytes'] / 1e9:.1f} GB > L2 {L2_BYTES / 1e6:.0f} MB",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": res["launches"], "clocks": res["clocks"],
+        "symbolic_ms": res["symbolic_ms"], "numeric_ms": res["kernel_ms"],
+    }
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

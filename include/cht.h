@@ -215,7 +215,8 @@ typedef enum {
                                  (default 2e9; 0 makes every wait expire:
                                  a test hook for the timeout path)         */
   CHT_OPT_CTAS_PER_SM = 2,    /* persistent grid = SMs * this (0 = auto)   */
-  CHT_OPT_FP64_ENGINE = 3     /* 0 = DMMA (mma.sync f64), 1 = DFMA          */
+  CHT_OPT_FP64_ENGINE = 3     /* 0 = DMMA (mma.sync f64), 1 = DFMA (default:
+                                 the faster of the two on GB300)           */
 } cht_option;
 int cht_set_option(int option, int64_t value);
 int cht_get_option(int option, int64_t *value);

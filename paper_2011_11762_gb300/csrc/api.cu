@@ -75,8 +75,24 @@ int launched(const char *name) {
 
 uint64_t next_id() { return g_next_id.fetch_add(1); }
 
+// Keeps freed blocks in the device's default stream-ordered pool instead of
+// returning them to the driver at every synchronisation (this process only).
+static void keep_pool_memory() {
+  static bool done[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ULL;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done[dev] = true;
+}
+
 void *dev_alloc(size_t bytes, cudaStream_t s) {
   if (g_alloc) return g_alloc(bytes, s, g_alloc_ctx);
+  keep_pool_memory();
   void *p = nullptr;
   if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
     cudaGetLastError();

@@ -272,7 +272,7 @@ int launch_fp64_peak(int engine, cudaStream_t s, double *tflops) {
   CHT_TRY(num_sms(&sms));
   DevArray<double> out;
   CHT_TRY(out.alloc(1, s));
-  const int threads = 256, per_sm = 4, iters = 4096;
+  const int threads = 256, per_sm = 4, iters = 1 << 15;
   const int grid = sms * per_sm;
   cudaEvent_t e0, e1;
   CHT_CUDA_TRY(cudaEventCreate(&e0));

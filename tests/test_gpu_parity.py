@@ -52,7 +52,7 @@ def test_multiply_matches_oracle(lib, name, engine):
     try:
         C, bound = lib.cht_multiply(plan, A, B, sync=True)
     finally:
-        lib.set_option(lib.OPT_FP64_ENGINE, 0)
+        lib.set_option(lib.OPT_FP64_ENGINE, 1)
     gu.assert_same_pattern(C, Co)
     gu.assert_values_close(C, Co, FP64_TOL)
     assert 0 < bound < 1e-10
