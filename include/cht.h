@@ -170,6 +170,34 @@ int cht_multiply(cht_plan_t plan, cht_mat_t A, cht_mat_t B, int mode,
                  double *max_rel_err_est);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free FP64 numeric multiply.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory on the
+ * call path -- for example a serving process that reserves its whole device
+ * memory budget at start-up and may not grow it per request, or code whose
+ * device memory belongs to another framework's allocator.  cht_multiply
+ * takes an 8-byte work counter from the stream-ordered pool on every call
+ * (and allocates C when *C is NULL); this call allocates nothing.
+ *
+ * Computes the same C = A*B as cht_multiply(plan, A, B, CHT_FP64, ...) with
+ * the same kernel, writing into C, which must already exist on the plan's
+ * product pattern (a matrix returned by cht_multiply for this plan, or
+ * cht_mat_like of one).  Returns without waiting for the GPU.
+ * Scratch: a file-scope device array of 256 bytes (held by every GPU that
+ * loads the library until the process exits); this call uses its first
+ * 8 bytes as the work counter and clears them at every call.  The array is
+ * shared by all calls on a device: calls whose kernels overlap on the GPU
+ * (e.g. on two streams) race on it and give wrong results -- order them.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.
+ * Limits: at most 2^31 - 1 output leaves per call (else
+ * CHT_ERR_UNSUPPORTED); b = 32 or 64.  Errors as for cht_multiply, plus
+ * CHT_ERR_INVALID when C is not on the plan's pattern.
+ * ---------------------------------------------------------------------- */
+int cht_multiply_f64_noalloc(cht_plan_t plan, cht_mat_t A, cht_mat_t B,
+                             cht_mat_t C, void *stream);
+
+/* ------------------------------------------------------------------------
  * Backward of C = A*B for a loss L(C), given dC = dL/dC:
  *   dA = (dC * B^T) restricted to A's pattern,
  *   dB = (A^T * dC) restricted to B's pattern

@@ -31,6 +31,7 @@ SIGNATURES = {
     "cht_multiply": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _I32, _VP, _PVP, _PD]),
     "cht_multiply_backward": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP, _PVP,
                                              _PVP]),
+    "cht_multiply_f64_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "cht_batch_create": (ctypes.c_int, [_I32, _PVP, _PVP, _PVP, ctypes.c_int, _I32, _VP,
                                         _PVP]),
     "cht_batch_run": (ctypes.c_int, [_VP, _VP]),

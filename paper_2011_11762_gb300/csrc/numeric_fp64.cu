@@ -18,6 +18,7 @@
 // Arithmetic: FP64 tensor-core MMA (mma.sync m8n8k4 f64, "DMMA"; engine 0)
 // or plain FP64 FMAs from a per-thread register tile (engine 1).
 #include <algorithm>
+#include <mutex>
 
 #include "device.cuh"
 #include "internal.h"
@@ -302,3 +303,92 @@ int launch_fp64_peak(int engine, cudaStream_t s, double *tflops) {
 }
 
 }  // namespace cht
+
+// ---------------------------------------------------------------------------
+// Allocation-free FP64 multiply (cht_multiply_f64_noalloc in cht.h).
+//
+// For callers that cannot allocate device memory on the call path.  The only
+// scratch the numeric kernel needs -- its 8-byte work counter, which
+// cht_multiply takes from the stream-ordered pool on every call -- lives here
+// in a file-scope device array instead.  The array's host-side name is only a
+// stand-in for the symbol; its device address is looked up once per device
+// with cudaGetSymbolAddress and passed to the kernel.
+namespace cht {
+namespace {
+constexpr int kNoAllocScratchBytes = 256;  // stated maximum; this call uses 8
+constexpr int kNoAllocMaxDevices = 64;
+__device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocScratchBytes / 8];
+std::mutex g_noalloc_mutex;
+unsigned long long *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+int noalloc_scratch(unsigned long long **out) {
+  int dev = 0;
+  CHT_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_error("device ordinal %d out of range", dev);
+    return CHT_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_ptr[dev] = static_cast<unsigned long long *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return CHT_OK;
+}
+}  // namespace
+
+}  // namespace cht
+
+extern "C" int cht_multiply_f64_noalloc(cht_plan_t plan, cht_mat_t A, cht_mat_t B, cht_mat_t C,
+                                        void *stream) {
+  using namespace cht;
+  if (!plan || !A || !B || !C) {
+    set_error("null plan or matrix handle");
+    return CHT_ERR_INVALID;
+  }
+  if (A->pat->n != plan->n || B->pat->n != plan->n || A->pat->b != plan->b ||
+      B->pat->b != plan->b || A->pat->nnz != plan->nA || B->pat->nnz != plan->nB) {
+    set_error("matrices do not match the plan's operands");
+    return CHT_ERR_SHAPE;
+  }
+  if (C->pat->id != plan->C->id) {
+    set_error("C must be a matrix on the plan's product pattern (from cht_multiply or "
+              "cht_mat_like of one)");
+    return CHT_ERR_INVALID;
+  }
+  if (plan->C->nnz > 0x7fffffffLL) {
+    set_error("%lld output leaves exceed the 2^31 - 1 work units of one call",
+              (long long)plan->C->nnz);
+    return CHT_ERR_UNSUPPORTED;
+  }
+  if (plan->b != 32 && plan->b != 64) {
+    set_error("leaf size %d: the numeric kernels take b = 32 or b = 64", plan->b);
+    return CHT_ERR_UNSUPPORTED;
+  }
+  if (plan->C->nnz == 0) return CHT_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long *counter = nullptr;
+  CHT_TRY(noalloc_scratch(&counter));
+  int *status = nullptr;
+  CHT_TRY(device_status_ptr(&status));
+  // the work counter must start at zero; the array keeps the last call's value
+  CHT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+  GemmWork w{};
+  w.X = A->values();
+  w.Y = B->values();
+  w.Z = C->values();
+  w.px = plan->pa.p;
+  w.py = plan->pb.p;
+  w.seg = plan->cseg.p;
+  w.order = plan->order.p;
+  w.nunits = plan->C->nnz;
+  w.b = plan->b;
+  const int engine = g_opt.fp64_engine;
+  if (w.b == 64)
+    return engine ? launch_b<64, 1>(w, s, status, counter) : launch_b<64, 0>(w, s, status, counter);
+  return engine ? launch_b<32, 1>(w, s, status, counter) : launch_b<32, 0>(w, s, status, counter);
+}
+
