@@ -294,6 +294,93 @@ def fp64_e2e(args, world, cht, torch, a, b):
             "ms_per_step": el * 1e3 / args.steps}
 
 
+# ------------------------------------------------------- extra sections --
+
+def _time_steps(torch, stream, fn, steps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _rel_fro(torch, x, ref):
+    den = torch.linalg.norm(ref.reshape(-1))
+    return float(torch.linalg.norm((x - ref).reshape(-1)) / den) if float(den) > 0 else 0.0
+
+
+def section_split(args, world, cht, torch):
+    """Split-precision form (6 BF16 slices, tcgen05) vs the FP64 path: the
+    3D-locality workload of the headline and the random-leaf workload
+    (N = 32768, 32x32 leaves, p = 0.01, N(0,1))."""
+    import workloads as w
+    stream = torch.cuda.current_stream()
+    out = {"nslices": 6, "bits_per_slice": 8}
+    peak_bf16 = _measured_peak("bf16_tflops")
+    for name, gen in (("3d_locality_N%d_b64" % args.n, lambda: w.config2(args.n)),
+                      ("random_N32768_b32_p0.01", lambda: w.config3())):
+        a, b = gen()
+        A, B = cht.from_block_matrix(a), cht.from_block_matrix(b)
+        plan = cht.cht_symbolic_multiply(A, B)
+        Cs, bound = cht.cht_multiply(plan, A, B, mode=cht.CHT_SPLIT_BF16, sync=True)
+        Cd, _ = cht.cht_multiply(plan, A, B, sync=True)
+        err = _rel_fro(torch, Cs.values(), Cd.values())
+        del Cd
+        flops = plan.useful_flops
+
+        def step_split():
+            p = cht.cht_symbolic_multiply(A, B)
+            cht.cht_multiply(p, A, B, mode=cht.CHT_SPLIT_BF16, out=None)
+
+        ms_split = _time_steps(torch, stream, step_split, args.steps, args.warmup)
+        kern = Timer(stream)
+
+        def numeric_only():
+            e = kern.start()
+            cht.cht_multiply(plan, A, B, mode=cht.CHT_SPLIT_BF16, out=Cs)
+            kern.stop(e)
+
+        _time_steps(torch, stream, numeric_only, args.steps, 1)
+        kms = statistics.mean(kern.ms()[1:])
+        nblk, N = (12, 64) if A.b == 64 else (8, 32)
+        slice_flops = plan.npairs * nblk * 2 * 128 * N * A.b
+        entry = {
+            "value": flops * world / (ms_split * 1e-3) / 1e12, "unit": UNIT,
+            "ms_per_step": ms_split, "numeric_ms": kms, "pairs": plan.npairs,
+            "rel_fro_err_vs_fp64": err, "a_priori_bound": bound,
+            "roofline": {"kernel": "k_split_gemm (tcgen05 kind::f16) + split kernels",
+                         "bound": "tensor", "achieved": slice_flops / (kms * 1e-3) / 1e12,
+                         "peak": peak_bf16, "unit": "TFLOP/s",
+                         "frac": slice_flops / (kms * 1e-3) / 1e12 / peak_bf16,
+                         "traffic": None,
+                         "algorithmic_flops_per_launch": slice_flops,
+                         "peak_source": "measured bf16 dense (burst)"},
+        }
+        if name.startswith("random"):
+            def step_fp64():
+                p = cht.cht_symbolic_multiply(A, B)
+                cht.cht_multiply(p, A, B)
+            ms64 = _time_steps(torch, stream, step_fp64, args.steps, args.warmup)
+            entry["fp64_value"] = flops * world / (ms64 * 1e-3) / 1e12
+            entry["fp64_ms_per_step"] = ms64
+        out[name] = entry
+        cht.sync_status()
+    return out
+
+
+def _measured_peak(key):
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))[key])
+    except Exception:
+        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0}[key]
+
+
 # ------------------------------------------------------------ CPU oracle --
 
 def oracle_sample(a, b, target_s: float):

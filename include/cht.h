@@ -133,7 +133,8 @@ int cht_mat_free(cht_mat_t M);
  * A and B must have equal n and b (else CHT_ERR_SHAPE).
  * *nnzb_C and *npairs (either may be NULL) get the number of C leaves and of
  * pairs; the useful work of the numeric phase is 2 * b^3 * npairs flops.
- * Synchronises `stream` twice (to size the pair list and C's pattern).
+ * Synchronises `stream` three times (to size the pair list and C's pattern,
+ * and to record the longest pair segment).
  * ---------------------------------------------------------------------- */
 int cht_symbolic_multiply(cht_mat_t A, cht_mat_t B, void *stream,
                           cht_plan_t *out, int64_t *nnzb_C, int64_t *npairs);
@@ -164,6 +165,11 @@ int cht_plan_free(cht_plan_t P);
  *          stores an a-priori bound on |C - A*B| / (|A| |B|) elementwise.
  * Each C leaf is summed in ascending K by one CTA: results are bitwise
  * reproducible run to run.  No atomics touch C.
+ * CHT_SPLIT_BF16: nslices = 0 or 6 (6 digits of 8 bits per operand, 48
+ * bits); inputs must be finite; b = 32 or 64; a C leaf may have at most
+ * 254 (b = 64) or 1016 (b = 32) leaf pairs (else CHT_ERR_UNSUPPORTED).  The
+ * bound returned is relative to 2^(e_r + f_c), the powers of two just above
+ * the largest |A| in row r and |B| in column c.
  * ---------------------------------------------------------------------- */
 int cht_multiply(cht_plan_t plan, cht_mat_t A, cht_mat_t B, int mode,
                  int32_t nslices, void *stream, cht_mat_t *C,

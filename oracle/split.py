@@ -66,25 +66,32 @@ def slice_pairs(s: int, extra: bool = False) -> list:
     return [(i, j) for i in range(1, s + 1) for j in range(1, s + 1) if i + j <= s + 1]
 
 
-def split_product(a: np.ndarray, b: np.ndarray, s: int, w: int, pairs=None):
+def split_product(a: np.ndarray, b: np.ndarray, s: int, w: int, pairs=None,
+                  sa: int | None = None):
     """Dense emulation of the split product of dense a (m x k) and b (k x n).
+    ``sa`` digits are taken for A (default s; digit i keeps weight 2^(-w i)
+    whatever the count), s for B.  Each S_ij = sum_k d_i g_j is an exact int64
+    matrix product (|S_ij| <= k (2^w - 1)^2 < 2^63); the weighted sum over
+    pairs and the final scaling are exact Python integers, rounded once.
     Returns (C_split as float64, e_row, f_col)."""
     if pairs is None:
         pairs = slice_pairs(s)
+    sa = s if sa is None else sa
     e = row_exponents(a, axis=1)
     f = row_exponents(b, axis=0)
-    da = digits(fixed_point(a, e, 1, s, w), s, w)
+    da = digits(fixed_point(a, e, 1, sa, w), sa, w)
     db = digits(fixed_point(b, f, 0, s, w), s, w)
     m, n = a.shape[0], b.shape[1]
+    top = max(i + j for i, j in pairs)
     acc = np.zeros((m, n), dtype=object)
     acc[:] = 0
     for i, j in pairs:
-        sij = da[i - 1].astype(object) @ db[j - 1].astype(object)  # exact integers
-        acc = acc + sij * (1 << (w * (2 * s - i - j)))
+        sij = (da[i - 1] @ db[j - 1]).astype(object)
+        acc = acc + sij * (1 << (w * (top - i - j)))
     out = np.empty((m, n), dtype=np.float64)
     for r in range(m):
         for c in range(n):
-            out[r, c] = _to_double(acc[r, c], int(e[r]) + int(f[c]) - 2 * s * w)
+            out[r, c] = _to_double(acc[r, c], int(e[r]) + int(f[c]) - w * top)
     return out, e, f
 
 

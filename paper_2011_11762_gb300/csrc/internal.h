@@ -161,6 +161,7 @@ struct cht_plan {
   uint64_t patA = 0, patB = 0;       // pattern ids of A and B
   std::shared_ptr<cht::Pattern> C;   // product pattern
   int64_t npairs = 0;
+  int64_t max_seg = 0;               // most pairs of any C leaf
   cht::DevArray<int64_t> cseg;       // [nC + 1]
   cht::DevArray<int32_t> pa, pb, pc; // per pair (sorted by C leaf, then K)
   cht::DevArray<int32_t> order;      // schedule [nC]

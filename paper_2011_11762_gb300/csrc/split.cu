@@ -1,11 +1,737 @@
-// Split-precision numeric phase (step S7): placeholder until the tcgen05
-// kernel lands.
+// Split-precision numeric phase (step S7): C = A*B with FP64 operands split
+// into bfloat16 digit slices, slice products on the tcgen05 tensor cores
+// (kind::f16, FP32 accumulation in TMEM), and an integer recombination.
+//
+// Splitting (error-free transformation in the style of Ozaki, Ogita, Oishi
+// and Rump, Numer. Algorithms 59, 2012): with e_r the exponent of the largest
+// |a| in global row r of A (max < 2^e_r) and f_c that of column c of B,
+//     a_rk = 2^e_r * sum_i d_i 2^(-8i),   b_kc = 2^f_c * sum_j g_j 2^(-8j)
+// up to truncation after the last digit, with signed integer digits
+// |d|, |g| <= 255 (exact in bfloat16).  Then
+//     C_rc = 2^(e_r + f_c) * sum_t S_t 2^(-8t),   S_t = sum_{i+j=t} sum_k d_i g_j,
+// and every S_t is an integer.  Slice pairs with i + j > 7 are dropped (their
+// weight is below the 48-bit truncation).
+//
+// Tensor-core mapping (one CTA per C leaf at a time; b = 64 shown, b = 32 in
+// brackets): the A operand of an MMA stacks 2 [4] consecutive slices of the
+// A leaf along M = 128, the B operand is one slice of the B leaf (N = b).
+// An MMA with first A slice u and B slice j lands in TMEM region t = u + j;
+// part p of the region (rows p*b .. p*b + b) then holds S_{t+p}.  Blocks with
+// the same t share the region, so a region holds whole diagonals.
+//
+// Exactness: regions 2..5 (diagonals 2..5 and their parts) carry the high
+// bits and must be exact.  An FP32 accumulator is exact while every partial
+// sum stays below 2^24, which holds for a window of 2 [8] leaf pairs:
+// 2 blocks * 64 * 2 * 255^2 < 2^24 [1 * 32 * 8 * 255^2 < 2^24].  After each
+// window the epilogue warps read these regions and add them, converted to
+// integers, into int64 accumulators; the next window restarts them.
+// Regions 6 and 7 (weight <= 2^-32 of the leading one) accumulate over the
+// whole C leaf in FP32 and are read once.  The final value
+//     T = sum_parts (2^16 Q_p + rnd(2^16 (R6 2^-8 + R7 2^-16))) 2^(-8p)
+// is an integer in units of 2^-56 and becomes a double by bit assembly; no
+// FP64 arithmetic is used (FP64 is the slowest unit on GB300).
+//
+// Roles (320 threads): warp 0 = bulk-copy producer, warp 1 = TMEM owner and
+// MMA issuer (one thread), warps 2..9 = epilogue (two warps per TMEM lane
+// quarter, splitting the columns).  Units are the C leaves in Morton order,
+// dealt round-robin to the persistent CTAs (neighbouring leaves run together,
+// so their A and B slices are shared through L2).  Every wait is bounded.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "device.cuh"
 #include "internal.h"
 
 namespace cht {
 
-int split_multiply(cht_plan *, cht_mat *, cht_mat *, int, cudaStream_t, double *, double *) {
-  set_error("the split-precision form is not built yet");
+namespace {
+
+constexpr int kW = 8;               // bits per digit
+constexpr int kSB = 6;              // B slices (and the split depth s)
+constexpr int kExactLast = 5;       // regions 2..5 are exact
+constexpr int kRegions = 6;         // regions t = 2..7
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr int64_t kDrainNs = 2000000000LL;
+
+template <int B>
+struct Cfg;
+template <>
+struct Cfg<64> {
+  static constexpr int N = 64, PARTS = 2, SA = 6, KSTEPS = 4, STAGES = 2, WINDOW = 2;
+  static constexpr int NBLK = 12;
+  static constexpr int TMEM_COLS = 512;
+};
+template <>
+struct Cfg<32> {
+  static constexpr int N = 32, PARTS = 4, SA = 8, KSTEPS = 2, STAGES = 3, WINDOW = 8;
+  static constexpr int NBLK = 8;
+  static constexpr int TMEM_COLS = 256;
+};
+
+// MMA blocks (first stacked A slice u, B slice j), 1-based; region t = u + j.
+__constant__ int8_t c_blk64[12][2] = {{1, 1}, {1, 2}, {1, 3}, {3, 1}, {1, 4}, {3, 2},
+                                       {1, 5}, {3, 3}, {5, 1}, {1, 6}, {3, 4}, {5, 2}};
+__constant__ int8_t c_blk32[8][2] = {{1, 1}, {1, 2}, {1, 3}, {1, 4},
+                                      {1, 5}, {5, 1}, {1, 6}, {5, 2}};
+
+template <int B>
+struct Smem {
+  static constexpr int TILE = B * 128;  // one slice: B rows x 64 bf16 (SW128 K-major)
+  static constexpr int A_BYTES = Cfg<B>::SA * TILE;
+  static constexpr int B_BYTES = kSB * TILE;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int XBUF = (Cfg<B>::PARTS - 1) * B * B * 8;
+  static constexpr int TOTAL = Cfg<B>::STAGES * STAGE + XBUF + 256;
+  static constexpr size_t DYN = TOTAL + 1024;  // + alignment slack
+};
+
+// ------------------------------------------------------------ tcgen05 PTX --
+__device__ inline void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_addr(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ inline void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ inline void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ inline void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ inline void tc_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(bar))
+      : "memory");
+}
+__device__ inline void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                              uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ inline void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 32 lanes x 32 consecutive 32-bit columns (one column block per thread).
+__device__ inline void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ inline void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <int E>
+__device__ inline void tmem_ld(uint32_t taddr, float (&v)[E]);
+template <>
+__device__ inline void tmem_ld<32>(uint32_t taddr, float (&v)[32]) { tmem_ld32(taddr, v); }
+template <>
+__device__ inline void tmem_ld<16>(uint32_t taddr, float (&v)[16]) { tmem_ld16(taddr, v); }
+
+// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
+// layout (rows of 128 bytes, 8-row groups 1024 bytes apart).
+__device__ inline uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3ffff) >> 4);  // start address
+  d |= static_cast<uint64_t>(1) << 16;                 // leading offset (unused here)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;         // stride: 8-row group pitch
+  d |= static_cast<uint64_t>(1) << 46;                 // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;                 // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// Bounded mbarrier wait that also gives up when another role aborted.
+__device__ inline bool wait_or_abort(uint64_t *bar, uint32_t parity, int64_t budget_ns,
+                                     volatile int *abort_flag) {
+  if (budget_ns <= 0) return false;
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (global_ns() - t0 > static_cast<uint64_t>(budget_ns)) return false;
+  }
+}
+
+// -------------------------------------------------------- digits / scale --
+// The "no exponent" marker (all-zero line); also the byte-0x80 memset value.
+constexpr int kNoExp = static_cast<int>(0x80808080u);
+
+// frexp exponent (x in [2^(e-1), 2^e)) from the bits; kNoExp for zero.
+__device__ inline int exp_of(double x) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int biased = static_cast<int>((bits >> 52) & 0x7ff);
+  const unsigned long long mant = bits & ((1ULL << 52) - 1);
+  if (biased) return biased - 1022;
+  if (!mant) return kNoExp;
+  return (64 - __clzll(static_cast<long long>(mant))) - 1074;
+}
+
+// Magnitude of trunc(|x| * 2^(nbits - e)) and the sign of x.
+__device__ inline unsigned long long fixed_mag(double x, int e, int nbits, bool *neg) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+  *neg = (bits >> 63) != 0;
+  const int biased = static_cast<int>((bits >> 52) & 0x7ff);
+  unsigned long long mant = bits & ((1ULL << 52) - 1);
+  int ex;
+  if (biased) {
+    mant |= 1ULL << 52;
+    ex = biased - 1075;
+  } else {
+    ex = -1074;
+  }
+  if (!mant || e == kNoExp) return 0;
+  const int sh = ex + nbits - e;
+  if (sh >= 0) return mant << sh;  // sh <= nbits - 53
+  if (sh <= -64) return 0;
+  return mant >> (-sh);
+}
+
+__device__ inline uint32_t pack_bf16x2(int lo, int hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(static_cast<float>(lo), static_cast<float>(hi));
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// Byte offset of logical 16-byte chunk c of row r in a 128-byte-swizzled tile.
+__host__ __device__ inline int sw128_offset(int r, int c) {
+  return (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
+}
+
+// v * 2^e2 rounded to nearest-even, from a 128-bit integer, with integer ops.
+__device__ inline double scaled_i128_to_double(__int128 v, int e2) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = v < 0 ? (1ULL << 63) : 0ULL;
+  const unsigned __int128 m = v < 0 ? static_cast<unsigned __int128>(0) - static_cast<unsigned __int128>(v)
+                                    : static_cast<unsigned __int128>(v);
+  const unsigned long long hi = static_cast<unsigned long long>(m >> 64);
+  const unsigned long long lo = static_cast<unsigned long long>(m);
+  int top = hi ? 127 - __clzll(static_cast<long long>(hi)) : 63 - __clzll(static_cast<long long>(lo));
+  unsigned long long mant;
+  const int sh = top - 52;
+  if (sh > 0) {
+    const unsigned __int128 one = 1;
+    const unsigned __int128 rem = m & ((one << sh) - 1);
+    const unsigned __int128 half = one << (sh - 1);
+    mant = static_cast<unsigned long long>(m >> sh);
+    if (rem > half || (rem == half && (mant & 1ULL))) {
+      ++mant;
+      if (mant >> 53) {
+        mant >>= 1;
+        ++top;
+      }
+    }
+  } else {
+    mant = lo << (-sh);
+  }
+  const int biased = top + e2 + 1023;
+  if (biased <= 0 || biased >= 2047) {  // outside the normal range: rare path
+    const double hd = ldexp(static_cast<double>(hi), 64 + e2) + ldexp(static_cast<double>(lo), e2);
+    return sgn ? -hd : hd;
+  }
+  return __longlong_as_double(static_cast<long long>(
+      sgn | (static_cast<unsigned long long>(biased) << 52) | (mant & ((1ULL << 52) - 1))));
+}
+
+// ------------------------------------------------------------ pre-kernels --
+
+// Row exponents of A: warp per (leaf, row).
+__global__ void k_row_exp(const double *__restrict__ vals, const int32_t *__restrict__ brow,
+                          int64_t nleaves, int b, int *__restrict__ row_exp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t total = nleaves * b;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t w = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5; w < total;
+       w += warps) {
+    const int64_t leaf = w / b;
+    const int r = static_cast<int>(w % b);
+    const double *row = vals + leaf * b * b + static_cast<int64_t>(r) * b;
+    int e = kNoExp;
+    for (int k = lane; k < b; k += 32) e = max(e, exp_of(row[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (lane == 0 && e != kNoExp) atomicMax(&row_exp[static_cast<int64_t>(brow[leaf]) * b + r], e);
+  }
+}
+
+// Column exponents of B: thread per (leaf, column).
+__global__ void k_col_exp(const double *__restrict__ vals, const int32_t *__restrict__ bcol,
+                          int64_t nleaves, int b, int *__restrict__ col_exp) {
+  const int64_t total = nleaves * b;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t leaf = t / b;
+    const int c = static_cast<int>(t % b);
+    const double *col = vals + leaf * b * b + c;
+    int e = kNoExp;
+    for (int k = 0; k < b; ++k) e = max(e, exp_of(col[static_cast<int64_t>(k) * b]));
+    if (e != kNoExp) atomicMax(&col_exp[static_cast<int64_t>(bcol[leaf]) * b + c], e);
+  }
+}
+
+// A slices: thread per (leaf, row r, chunk c of 8 K values).  Leaf layout in
+// global memory = the shared-memory image: [SA][B rows][128 bytes], swizzled.
+template <int B, int SA>
+__global__ void k_split_a(const double *__restrict__ vals, const int32_t *__restrict__ brow,
+                          int64_t nleaves, const int *__restrict__ row_exp,
+                          uint8_t *__restrict__ out) {
+  constexpr int CH = B / 8;  // logical chunks per row holding data
+  constexpr int TILE = B * 128;
+  const int64_t total = nleaves * B * CH;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t leaf = t / (B * CH);
+    const int r = static_cast<int>((t / CH) % B), c = static_cast<int>(t % CH);
+    const int e = row_exp[static_cast<int64_t>(brow[leaf]) * B + r];
+    const double *src = vals + leaf * B * B + static_cast<int64_t>(r) * B + c * 8;
+    int d[SA][8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      bool neg;
+      const unsigned long long mag = fixed_mag(src[k], e, SA * kW, &neg);
+#pragma unroll
+      for (int i = 0; i < SA; ++i) {
+        const int di = static_cast<int>((mag >> (kW * (SA - 1 - i))) & 0xff);
+        d[i][k] = neg ? -di : di;
+      }
+    }
+    uint8_t *base = out + leaf * SA * TILE + sw128_offset(r, c);
+#pragma unroll
+    for (int i = 0; i < SA; ++i) {
+      uint4 v;
+      v.x = pack_bf16x2(d[i][0], d[i][1]);
+      v.y = pack_bf16x2(d[i][2], d[i][3]);
+      v.z = pack_bf16x2(d[i][4], d[i][5]);
+      v.w = pack_bf16x2(d[i][6], d[i][7]);
+      *reinterpret_cast<uint4 *>(base + i * TILE) = v;
+    }
+  }
+}
+
+// B slices, stored transposed (tile row n = column n of the leaf, K-major):
+// thread per (leaf, column n, chunk c of 8 K values).
+template <int B>
+__global__ void k_split_b(const double *__restrict__ vals, const int32_t *__restrict__ bcol,
+                          int64_t nleaves, const int *__restrict__ col_exp,
+                          uint8_t *__restrict__ out) {
+  constexpr int CH = B / 8;
+  constexpr int TILE = B * 128;
+  const int64_t total = nleaves * CH * B;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t leaf = t / (CH * B);
+    const int c = static_cast<int>((t / B) % CH), n = static_cast<int>(t % B);
+    const int f = col_exp[static_cast<int64_t>(bcol[leaf]) * B + n];
+    const double *src = vals + leaf * B * B + static_cast<int64_t>(c * 8) * B + n;
+    int g[kSB][8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      bool neg;
+      const unsigned long long mag = fixed_mag(src[static_cast<int64_t>(k) * B], f, kSB * kW, &neg);
+#pragma unroll
+      for (int j = 0; j < kSB; ++j) {
+        const int gj = static_cast<int>((mag >> (kW * (kSB - 1 - j))) & 0xff);
+        g[j][k] = neg ? -gj : gj;
+      }
+    }
+    uint8_t *base = out + leaf * kSB * TILE + sw128_offset(n, c);
+#pragma unroll
+    for (int j = 0; j < kSB; ++j) {
+      uint4 v;
+      v.x = pack_bf16x2(g[j][0], g[j][1]);
+      v.y = pack_bf16x2(g[j][2], g[j][3]);
+      v.z = pack_bf16x2(g[j][4], g[j][5]);
+      v.w = pack_bf16x2(g[j][6], g[j][7]);
+      *reinterpret_cast<uint4 *>(base + j * TILE) = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------ main kernel --
+
+struct SplitArgs {
+  const uint8_t *a_slices;
+  const uint8_t *b_slices;
+  const int32_t *pa;
+  const int32_t *pb;
+  const int64_t *cseg;
+  const int32_t *crow;
+  const int32_t *ccol;
+  const int *row_exp;
+  const int *col_exp;
+  double *C;
+  int64_t nunits;
+};
+
+template <int B>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_split_gemm(const SplitArgs args, int *__restrict__ status, int64_t wait_ns) {
+  using CF = Cfg<B>;
+  using SM = Smem<B>;
+  constexpr int N = CF::N, PARTS = CF::PARTS, STAGES = CF::STAGES, WINDOW = CF::WINDOW;
+  constexpr int E = N / 2;  // columns per epilogue thread
+  constexpr uint32_t IDESC = make_idesc(128, N);
+  constexpr uint32_t STAGE_TX = SM::STAGE;
+
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte aligned base for the swizzled tiles
+  const uint32_t raw_addr = smem_addr(smem_raw);
+  uint8_t *smem = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
+  uint8_t *stage_base = smem;
+  int64_t *xbuf = reinterpret_cast<int64_t *>(smem + STAGES * SM::STAGE);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * SM::STAGE + SM::XBUF);
+  uint64_t *full = bars;                // [STAGES]
+  uint64_t *empty = bars + STAGES;      // [STAGES]
+  uint64_t *acc_full = bars + 2 * STAGES;
+  uint64_t *acc_empty = acc_full + 1;
+  uint64_t *drain = acc_full + 2;
+  uint64_t *ep_bar = acc_full + 3;  // epilogue-only barrier (8 warps)
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ep_bar + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kEpiWarps);
+    mbar_init(drain, 1);
+    mbar_init(ep_bar, kEpiWarps);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, CF::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto fail = [&]() {
+    atomicOr(status, DEV_STATUS_TIMEOUT);
+    *abort_flag = 1;
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------- producer --
+    if (lane == 0) {
+      uint32_t k = 0;  // pairs issued
+      bool ok = true;
+      for (int64_t u = blockIdx.x; ok && u < args.nunits; u += gridDim.x) {
+        const int64_t p0 = args.cseg[u], p1 = args.cseg[u + 1];
+        for (int64_t p = p0; p < p1; ++p, ++k) {
+          const uint32_t st = k % STAGES, ph = (k / STAGES) & 1u;
+          if (!wait_or_abort(&empty[st], ph ^ 1u, wait_ns, abort_flag)) {
+            fail();
+            ok = false;
+            break;
+          }
+          uint8_t *sa = stage_base + st * SM::STAGE;
+          mbar_arrive_expect_tx(&full[st], STAGE_TX);
+          bulk_g2s(sa, args.a_slices + static_cast<int64_t>(args.pa[p]) * SM::A_BYTES, SM::A_BYTES,
+                   &full[st]);
+          bulk_g2s(sa + SM::A_BYTES, args.b_slices + static_cast<int64_t>(args.pb[p]) * SM::B_BYTES,
+                   SM::B_BYTES, &full[st]);
+        }
+      }
+      // copies in flight must land before shared memory goes away (after a
+      // normal run these phases completed long ago)
+      for (uint32_t j = (k >= STAGES ? k - STAGES : 0); j < k; ++j)
+        mbar_wait_bounded(&full[j % STAGES], (j / STAGES) & 1u, kDrainNs);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------ MMA issuer --
+    if (lane == 0) {
+      uint32_t k = 0;   // pairs consumed
+      uint32_t win = 0; // windows issued
+      bool ok = true;
+      for (int64_t u = blockIdx.x; ok && u < args.nunits; u += gridDim.x) {
+        const int64_t p0 = args.cseg[u], np = args.cseg[u + 1] - p0;
+        bool fresh[kRegions];
+#pragma unroll
+        for (int t = 0; t < kRegions; ++t) fresh[t] = true;
+        for (int64_t w0 = 0; ok && w0 < np; w0 += WINDOW, ++win) {
+          // the epilogue must have read the regions of the previous window
+          if (!wait_or_abort(acc_empty, (win & 1u) ^ 1u, wait_ns, abort_flag)) {
+            fail();
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int t = 0; t <= kExactLast - 2; ++t) fresh[t] = true;
+          const int64_t w1 = min(np, w0 + WINDOW);
+          for (int64_t i = w0; i < w1; ++i, ++k) {
+            const uint32_t st = k % STAGES, ph = (k / STAGES) & 1u;
+            if (!wait_or_abort(&full[st], ph, wait_ns, abort_flag)) {
+              fail();
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_addr(stage_base + st * SM::STAGE);
+            const uint32_t sb = sa + SM::A_BYTES;
+#pragma unroll
+            for (int bi = 0; bi < CF::NBLK; ++bi) {
+              const int bu = (B == 64) ? c_blk64[bi][0] : c_blk32[bi][0];
+              const int bj = (B == 64) ? c_blk64[bi][1] : c_blk32[bi][1];
+              const int t = bu + bj - 2;  // region index 0..5
+              const uint64_t ad = sw128_desc(sa + (bu - 1) * SM::TILE);
+              const uint64_t bd = sw128_desc(sb + (bj - 1) * SM::TILE);
+              const uint32_t dt = tmem + static_cast<uint32_t>(t * N);
+#pragma unroll
+              for (int kk = 0; kk < CF::KSTEPS; ++kk) {
+                const uint32_t acc = (fresh[t] && kk == 0) ? 0u : 1u;
+                tc_mma(dt, ad + 2 * kk, bd + 2 * kk, IDESC, acc);
+              }
+              fresh[t] = false;
+            }
+            tc_commit(&empty[st]);  // frees the stage when these MMAs finish
+          }
+          if (ok) tc_commit(acc_full);
+        }
+      }
+      // in-flight MMAs must finish before TMEM is released
+      tc_commit(drain);
+      mbar_wait_bounded(drain, 0, kDrainNs);
+    }
+  } else {
+    // -------------------------------------------------------- epilogue --
+    const int q = warp & 3;                  // TMEM lane quarter of this warp
+    const int half = (warp >= 6) ? 1 : 0;    // which half of the columns
+    const int part = (B == 64) ? (q >> 1) : q;
+    const int row = (B == 64) ? ((q & 1) * 32 + lane) : lane;
+    const int c0 = half * E;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * q) << 16);
+    uint32_t win = 0, epb = 0;
+    bool ok = true;
+    // bounded barrier among the 8 epilogue warps
+    auto ep_sync = [&]() -> bool {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ep_bar);
+      const bool r = wait_or_abort(ep_bar, epb & 1u, wait_ns, abort_flag);
+      ++epb;
+      return r;
+    };
+    for (int64_t u = blockIdx.x; ok && u < args.nunits; u += gridDim.x) {
+      const int64_t np = args.cseg[u + 1] - args.cseg[u];
+      long long Q[E];
+#pragma unroll
+      for (int c = 0; c < E; ++c) Q[c] = 0;
+      for (int64_t w0 = 0; w0 < np; w0 += WINDOW, ++win) {
+        const bool last = w0 + WINDOW >= np;
+        if (!wait_or_abort(acc_full, win & 1u, wait_ns, abort_flag)) {
+          fail();
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        float v[E];
+#pragma unroll
+        for (int t = 0; t <= kExactLast - 2; ++t) {
+          tmem_ld<E>(lane_base + static_cast<uint32_t>(t * N + c0), v);
+          tc_wait_ld();
+#pragma unroll
+          for (int c = 0; c < E; ++c)
+            Q[c] += static_cast<long long>(__float2int_rn(v[c])) << (kW * (kExactLast - 2 - t));
+        }
+        float rl[E];  // low regions, folded: R6 2^-8 + R7 2^-16
+        if (last) {
+          tmem_ld<E>(lane_base + static_cast<uint32_t>(4 * N + c0), v);
+          tc_wait_ld();
+#pragma unroll
+          for (int c = 0; c < E; ++c) rl[c] = v[c] * 0x1p-8f;
+          tmem_ld<E>(lane_base + static_cast<uint32_t>(5 * N + c0), v);
+          tc_wait_ld();
+#pragma unroll
+          for (int c = 0; c < E; ++c) rl[c] = fmaf(v[c], 0x1p-16f, rl[c]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);
+        if (last) {
+          // part value in units of 2^-(8 (5 + part) + 16); parts > 0 are then
+          // rounded to units of 2^-56 (the plan limits the window count so
+          // that they fit 64 bits) and handed to part 0 through shared memory
+          auto part_value = [&](int c) -> __int128 {
+            return (static_cast<__int128>(Q[c]) << 16) +
+                   static_cast<__int128>(__float2ll_rn(rl[c] * 65536.0f));
+          };
+          if (part > 0) {
+            const int sh = kW * part;
+#pragma unroll
+            for (int c = 0; c < E; ++c)
+              xbuf[(static_cast<int64_t>(part - 1) * B + row) * B + c0 + c] =
+                  static_cast<long long>((part_value(c) + (static_cast<__int128>(1) << (sh - 1))) >> sh);
+          }
+          if (!ep_sync()) {
+            fail();
+            ok = false;
+            break;
+          }
+          if (part == 0) {
+            const int er = args.row_exp[static_cast<int64_t>(args.crow[u]) * B + row];
+            const int64_t colbase = static_cast<int64_t>(args.ccol[u]) * B;
+            double *dst = args.C + u * B * B + static_cast<int64_t>(row) * B + c0;
+#pragma unroll
+            for (int c = 0; c < E; c += 2) {
+              __int128 t0 = part_value(c), t1 = part_value(c + 1);
+#pragma unroll
+              for (int p = 1; p < PARTS; ++p) {
+                t0 += xbuf[(static_cast<int64_t>(p - 1) * B + row) * B + c0 + c];
+                t1 += xbuf[(static_cast<int64_t>(p - 1) * B + row) * B + c0 + c + 1];
+              }
+              const int f0 = args.col_exp[colbase + c0 + c], f1 = args.col_exp[colbase + c0 + c + 1];
+              const bool z0 = er == kNoExp || f0 == kNoExp, z1 = er == kNoExp || f1 == kNoExp;
+              double2 out;
+              out.x = z0 ? 0.0 : scaled_i128_to_double(t0, er + f0 - 56);
+              out.y = z1 ? 0.0 : scaled_i128_to_double(t1, er + f1 - 56);
+              *reinterpret_cast<double2 *>(dst + c) = out;
+            }
+          }
+          if (!ep_sync()) {
+            fail();
+            ok = false;
+            break;
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, CF::TMEM_COLS);
+}
+
+unsigned grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 65535LL * 8) g = 65535LL * 8;
+  return static_cast<unsigned>(g);
+}
+
+template <int B>
+int run_split(cht_plan *plan, cht_mat *A, cht_mat *Bm, cudaStream_t s, double *Cvals) {
+  using CF = Cfg<B>;
+  using SM = Smem<B>;
+  const Pattern &pa = *A->pat, &pb = *Bm->pat;
+  const int64_t n = pa.n;
+  DevArray<int> row_exp, col_exp;
+  DevArray<uint8_t> a_sl, b_sl;
+  CHT_TRY(row_exp.alloc(n, s));
+  CHT_TRY(col_exp.alloc(n, s));
+  CHT_TRY(a_sl.alloc(static_cast<size_t>(pa.nnz) * SM::A_BYTES, s));
+  CHT_TRY(b_sl.alloc(static_cast<size_t>(pb.nnz) * SM::B_BYTES, s));
+  // kNoExp fill (every byte 0x80)
+  CHT_CUDA_TRY(cudaMemsetAsync(row_exp.p, 0x80, sizeof(int) * n, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(col_exp.p, 0x80, sizeof(int) * n, s));
+  if (pa.nnz > 0) {
+    k_row_exp<<<grid_for(pa.nnz * B * 32, 256), 256, 0, s>>>(A->values(), pa.brow.p, pa.nnz, B,
+                                                             row_exp.p);
+    CHT_TRY(launched("row_exp"));
+  }
+  if (pb.nnz > 0) {
+    k_col_exp<<<grid_for(pb.nnz * B, 256), 256, 0, s>>>(Bm->values(), pb.bcol.p, pb.nnz, B,
+                                                        col_exp.p);
+    CHT_TRY(launched("col_exp"));
+  }
+  if (pa.nnz > 0) {
+    k_split_a<B, CF::SA><<<grid_for(pa.nnz * B * (B / 8), 256), 256, 0, s>>>(
+        A->values(), pa.brow.p, pa.nnz, row_exp.p, a_sl.p);
+    CHT_TRY(launched("split_a"));
+  }
+  if (pb.nnz > 0) {
+    k_split_b<B><<<grid_for(pb.nnz * B * (B / 8), 256), 256, 0, s>>>(
+        Bm->values(), pb.bcol.p, pb.nnz, col_exp.p, b_sl.p);
+    CHT_TRY(launched("split_b"));
+  }
+  const int64_t units = plan->C->nnz;
+  if (units == 0) return CHT_OK;
+  int *status = nullptr;
+  CHT_TRY(device_status_ptr(&status));
+  int sms = 0;
+  CHT_TRY(num_sms(&sms));
+  auto kern = k_split_gemm<B>;
+  CHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(SM::DYN)));
+  SplitArgs a{};
+  a.a_slices = a_sl.p;
+  a.b_slices = b_sl.p;
+  a.pa = plan->pa.p;
+  a.pb = plan->pb.p;
+  a.cseg = plan->cseg.p;
+  a.crow = plan->C->brow.p;
+  a.ccol = plan->C->bcol.p;
+  a.row_exp = row_exp.p;
+  a.col_exp = col_exp.p;
+  a.C = Cvals;
+  a.nunits = units;
+  const int64_t grid = std::min<int64_t>(units, sms);
+  kern<<<static_cast<unsigned>(grid), kThreads, SM::DYN, s>>>(a, status, g_opt.wait_budget_ns);
+  return launched("split_gemm");
+}
+
+}  // namespace
+
+int split_multiply(cht_plan *plan, cht_mat *A, cht_mat *B, int nslices, cudaStream_t s,
+                   double *Cvals, double *err_bound) {
+  if (nslices != 0 && nslices != kSB) {
+    set_error("the split form uses %d slices (nslices = 0 or %d)", kSB, kSB);
+    return CHT_ERR_UNSUPPORTED;
+  }
+  const int b = plan->b;
+  // the parts handed between epilogue warps hold (windows * 2^56) in 64 bits
+  const int window = b == 64 ? Cfg<64>::WINDOW : Cfg<32>::WINDOW;
+  if ((plan->max_seg + window - 1) / window >= 128) {
+    set_error("split form: a C leaf has %lld leaf pairs (at most %d); use CHT_FP64",
+              (long long)plan->max_seg, 127 * window);
+    return CHT_ERR_UNSUPPORTED;
+  }
+  // elementwise bound relative to 2^(e_r + f_c): K (s + 3) 2^(-s w) with
+  // K <= n, plus the FP32 rounding of the low regions (below 2^-50)
+  const double K = static_cast<double>(plan->n);
+  *err_bound = K * (kSB + 3) * 0x1p-48 + 0x1p-50;
+  if (b == 64) return run_split<64>(plan, A, B, s, Cvals);
+  if (b == 32) return run_split<32>(plan, A, B, s, Cvals);
+  set_error("leaf size %d: the split form takes b = 32 or b = 64", b);
   return CHT_ERR_UNSUPPORTED;
 }
 

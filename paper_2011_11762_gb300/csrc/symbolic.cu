@@ -106,6 +106,15 @@ __global__ void k_lpt_keys(const int64_t *__restrict__ seg, int64_t n, uint64_t 
   }
 }
 
+__global__ void k_max_seg(const int64_t *__restrict__ seg, int64_t n,
+                          unsigned long long *__restrict__ out) {
+  unsigned long long m = 0;
+  GRID_STRIDE(u, n) m = max(m, static_cast<unsigned long long>(seg[u + 1] - seg[u]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 __global__ void k_iota(int32_t *__restrict__ v, int64_t n) {
   GRID_STRIDE(i, n) v[i] = static_cast<int32_t>(i);
 }
@@ -281,6 +290,15 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out)
   }
   CHT_TRY(build_pattern_index(*C, s));
   CHT_TRY(schedule_units(plan->cseg.p, nC, plan->order.p, s));
+  if (nC > 0) {
+    DevArray<int64_t> mx;
+    CHT_TRY(mx.alloc(1, s));
+    CHT_CUDA_TRY(cudaMemsetAsync(mx.p, 0, sizeof(int64_t), s));
+    k_max_seg<<<grid_for(nC, 256), 256, 0, s>>>(plan->cseg.p, nC,
+                                                 reinterpret_cast<unsigned long long *>(mx.p));
+    CHT_TRY(launched("max_seg"));
+    CHT_TRY(read_i64(mx.p, &plan->max_seg, s));
+  }
   plan->pa = std::move(pa);
   plan->pb = std::move(pb);
   plan->C = std::move(C);

@@ -1,0 +1,146 @@
+"""GPU split-precision form (BF16 slices on tcgen05) against the oracles.
+
+Two comparisons:
+1. with the exact emulation of the same splitting (oracle/split.py, the same
+   slice pairs as the kernel's MMA blocks): only the FP32 rounding of the two
+   low-weight TMEM regions and the final rounding separate them;
+2. with the FP64 product: within the a-priori bound of the splitting, and the
+   relative Frobenius error is reported.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+from oracle import split as sp
+from tests import gpu_util as gu
+from tests import setref
+
+pytestmark = pytest.mark.gpu
+
+S, W = 6, 8
+
+
+def _kernel_pairs(b):
+    """Slice pairs the kernel's MMA blocks compute (A slices stacked along M)."""
+    if b == 64:
+        blocks = [(u, j) for u, js in ((1, 6), (3, 4), (5, 2)) for j in range(1, js + 1)]
+        parts, sa = 2, 6
+    else:
+        blocks = [(u, j) for u, js in ((1, 6), (5, 2)) for j in range(1, js + 1)]
+        parts, sa = 4, 8
+    return sorted({(u + p, j) for u, j in blocks for p in range(parts)}), sa
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return gu.cht()
+
+
+def _dense_on(M, n):
+    br, bc, v = gu.host_leaves(M)
+    out = np.zeros((n, n))
+    b = M.b
+    for i in range(len(br)):
+        out[br[i] * b:(br[i] + 1) * b, bc[i] * b:(bc[i] + 1) * b] = v[i]
+    return out
+
+
+@pytest.mark.parametrize("b,n,p", [(64, 256, 0.6), (32, 256, 0.5), (64, 192, 1.0),
+                                   (32, 96, 1.0)])
+def test_split_matches_exact_emulation(lib, b, n, p):
+    a = w.random_blocks(n, b, p, 11 + b, dist="uniform")
+    bm = w.random_blocks(n, b, p, 12 + b, dist="normal")
+    a.vals *= np.exp2(np.random.default_rng(5).integers(-12, 12, size=(a.nblocks, b, 1)))
+    A, B = gu.upload(lib, a), gu.upload(lib, bm)
+    plan = lib.cht_symbolic_multiply(A, B)
+    C, bound = lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
+    got = _dense_on(C, n)
+    ad, bd = a.to_dense(), bm.to_dense()
+    pairs, sa = _kernel_pairs(b)
+    emu, e, f = sp.split_product(ad, bd, S, W, pairs=pairs, sa=sa)
+    scale = np.ldexp(1.0, (e[:, None] + f[None, :]).astype(np.int64))
+    mask = _dense_on(C, n) != 0
+    # FP32 rounding of regions of weight <= 2^-40 relative to 2^(e_r + f_c)
+    tol = scale * n * 2.0 ** -60 + 2 * np.spacing(np.abs(emu))
+    diff = np.abs(got - emu)
+    assert np.all(diff[mask] <= tol[mask]), float((diff / tol).max())
+    ref = ad @ bd
+    within = np.abs(got - ref) <= sp.error_bound(ad, bd, S, W) + 2 * np.spacing(np.abs(ref))
+    assert np.all(within)
+    assert 0 < bound < 1e-6
+
+
+@pytest.mark.parametrize("name", ["banded_4096_b32", "locality_8192_b64", "random_4096_b32"])
+def test_split_close_to_fp64(lib, name):
+    if name == "banded_4096_b32":
+        a, b = w.config1()
+    elif name == "locality_8192_b64":
+        a, b = w.config2(8192)
+    else:
+        a, b = (w.random_blocks(4096, 32, 0.03, 1003), w.random_blocks(4096, 32, 0.03, 2003))
+    A, B = gu.upload(lib, a), gu.upload(lib, b)
+    plan = lib.cht_symbolic_multiply(A, B)
+    Cs, _ = lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
+    Cd, _ = lib.cht_multiply(plan, A, B, sync=True)
+    Co, _ = gu.oracle_product(a, b)
+    gu.assert_same_pattern(Cs, Co)
+    err = gu.assert_values_close(Cs, Co, 1e-12)
+    e64 = setref.rel_fro(Cs.values().cpu().numpy(), Cd.values().cpu().numpy())
+    print(f"{name}: split vs oracle rel. Frobenius {err:.2e}, vs FP64 path {e64:.2e}")
+    assert e64 <= 1e-12
+
+
+def test_split_zero_rows_and_empty(lib):
+    a = w.random_blocks(512, 64, 0.5, 21, dist="uniform")
+    a.vals[:, 5, :] = 0.0  # an all-zero row inside every leaf
+    b = w.random_blocks(512, 64, 0.5, 22, dist="uniform")
+    A, B = gu.upload(lib, a), gu.upload(lib, b)
+    plan = lib.cht_symbolic_multiply(A, B)
+    C, _ = lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
+    ref = a.to_dense() @ b.to_dense()
+    got = C.to_dense().cpu().numpy()
+    assert np.all(got[5::64] == 0.0)
+    assert setref.rel_fro(got, ref) <= 1e-12
+    empty = w.BlockMatrix(512, 64, np.zeros(0, np.int32), np.zeros(0, np.int32),
+                          np.zeros((0, 64, 64)))
+    E = gu.upload(lib, empty)
+    plan = lib.cht_symbolic_multiply(A, E)
+    C, _ = lib.cht_multiply(plan, A, E, mode=lib.CHT_SPLIT_BF16, sync=True)
+    assert C.nblocks == 0
+
+
+def test_split_long_segments(lib):
+    # many pairs per C leaf: many exact windows per leaf (dense 12 x 12 grid)
+    a = w.random_blocks(768, 64, 1.0, 31, dist="uniform")
+    b = w.random_blocks(768, 64, 1.0, 32, dist="uniform")
+    A, B = gu.upload(lib, a), gu.upload(lib, b)
+    plan = lib.cht_symbolic_multiply(A, B)
+    C, _ = lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
+    ref = a.to_dense() @ b.to_dense()
+    got = C.to_dense().cpu().numpy()
+    bound = sp.error_bound(a.to_dense(), b.to_dense(), S, W)
+    assert np.all(np.abs(got - ref) <= bound + 2 * np.spacing(np.abs(ref)))
+    assert setref.rel_fro(got, ref) <= 1e-12
+
+
+def test_split_timeout_path(lib):
+    a, b = w.config1(1024, 32, 2)
+    A, B = gu.upload(lib, a), gu.upload(lib, b)
+    plan = lib.cht_symbolic_multiply(A, B)
+    old = lib.get_option(lib.OPT_WAIT_BUDGET_NS)
+    lib.set_option(lib.OPT_WAIT_BUDGET_NS, 0)
+    try:
+        with pytest.raises(lib.ChtError) as e:
+            lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
+        assert e.value.code == lib.CHT_ERR_TIMEOUT
+    finally:
+        lib.set_option(lib.OPT_WAIT_BUDGET_NS, old)
+    lib.sync_status()
+    C, _ = lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
+    Co, _ = gu.oracle_product(a, b)
+    gu.assert_values_close(C, Co, 1e-12)
+    _ = oracle
