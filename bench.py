@@ -374,6 +374,96 @@ def section_split(args, world, cht, torch):
     return out
 
 
+def section_backward(args, world, cht, torch):
+    """Forward + backward of L = ||A B - T||_F^2 through the autograd binding:
+    A banded (+-8 leaves), B 3D locality (32^3 lattice, cutoff 6), N = 32768,
+    64x64 leaves, T ~ N(0, 1) on C's pattern.  Useful work per step: the
+    forward product and the two sampled backward products, 3 * 2 b^3 P."""
+    import workloads as w
+    from paper_2011_11762_gb300 import autograd as cag
+    stream = torch.cuda.current_stream()
+    a, b = w.config5()
+    A, B = cht.from_block_matrix(a), cht.from_block_matrix(b)
+    plan = cht.cht_symbolic_multiply(A, B)
+    C0, _ = cht.cht_multiply(plan, A, B, sync=True)
+    crow, ccol = (x.cpu().numpy() for x in C0.coords())
+    T = cht.from_block_matrix(w.values_on_pattern(a.n, a.b, crow, ccol, w.SEED_T + 5))
+    tv = T.values()
+    del C0
+    out = {"workload": "banded8_x_3d_locality_N32768_b64", "pairs": plan.npairs}
+    for name, recompute in (("stored_pairs", False), ("recomputed_pairs", True)):
+        a_vals = A.values().detach().requires_grad_()
+        b_vals = B.values().detach().requires_grad_()
+        losses = []
+
+        def step():
+            a_vals.grad = None
+            b_vals.grad = None
+            c, _ = cag.matmul(A, B, a_vals, b_vals, plan=plan, recompute_pairs=recompute)
+            loss = ((c - tv) ** 2).sum()
+            loss.backward()
+            losses.append(loss.detach())
+
+        ms = _time_steps(torch, stream, step, args.steps, args.warmup)
+        cht.sync_status()
+        flops = 3 * plan.useful_flops
+        out[name] = {"value": flops * world / (ms * 1e-3) / 1e12, "unit": UNIT,
+                     "ms_per_step": ms, "loss": float(losses[-1]),
+                     "grad_norm_A": float(torch.linalg.norm(a_vals.grad.reshape(-1))),
+                     "grad_norm_B": float(torch.linalg.norm(b_vals.grad.reshape(-1)))}
+    return out
+
+
+def section_batched(args, world, cht, torch):
+    """64 independent products of log-uniform size (2048..32768) with cycling
+    structures, leaf size and work order chosen by the autotuner, run as one
+    persistent launch replayed from a CUDA graph.  Useful work counts the
+    products at their native 32-leaf structure (zero fill of 64-leaves is
+    not counted)."""
+    import workloads as w
+    from paper_2011_11762_gb300 import autotune
+    prods = w.batched_products()
+    spec = []
+    native_flops = 0
+    for _, a, b in prods:
+        ta = (torch.from_numpy(a.brow), torch.from_numpy(a.bcol), torch.from_numpy(a.vals))
+        tb = (torch.from_numpy(b.brow), torch.from_numpy(b.bcol), torch.from_numpy(b.vals))
+        spec.append((a.n, ta, tb))
+        A32, B32 = cht.from_block_matrix(a), cht.from_block_matrix(b)
+        native_flops += cht.cht_symbolic_multiply(A32, B32).useful_flops
+        del A32, B32
+    del prods
+    out = {"products": len(spec), "native_useful_flops": native_flops}
+    results = {}
+    for name, mode in (("fp64", cht.CHT_FP64), ("split", cht.CHT_SPLIT_BF16)):
+        tuned = autotune.tune(spec, mode=mode, reps=1)
+        bt = tuned.batch
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            bt.run(stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            bt.run()
+        ms = _time_steps(torch, torch.cuda.current_stream(), g.replay, args.steps, args.warmup)
+        cht.sync_status()
+        results[name] = [bt.output(i).values() for i in range(bt.count)]
+        out[name] = {"value": native_flops * world / (ms * 1e-3) / 1e12, "unit": UNIT,
+                     "ms_per_step": ms, "leaf_sizes": {"32": tuned.leaf_sizes.count(32),
+                                                       "64": tuned.leaf_sizes.count(64)},
+                     "schedule": tuned.schedule, "launches_per_step": "1 graph replay",
+                     "graph": True}
+        out[name]["_keep"] = (tuned, g)
+    num = sum(float(torch.linalg.norm((x - y).reshape(-1))) ** 2
+              for x, y in zip(results["split"], results["fp64"])) ** 0.5
+    den = sum(float(torch.linalg.norm(y.reshape(-1))) ** 2 for y in results["fp64"]) ** 0.5
+    out["split"]["rel_fro_err_vs_fp64"] = num / den
+    for k in ("fp64", "split"):
+        out[k].pop("_keep")
+    return out
+
+
 def _measured_peak(key):
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))[key])

@@ -240,6 +240,44 @@ def cht_multiply_backward(plan: Plan | None, A: Matrix, B: Matrix, dC: Matrix,
     return ra, rb
 
 
+class Batch:
+    """Many independent products in one persistent launch (cht_batch_*).
+
+    Keeps the plans and matrices it was built from alive.  ``run()`` only
+    launches kernels, so it can be captured in a CUDA graph."""
+
+    def __init__(self, plans, As, Bs, mode: int = CHT_FP64, nslices: int = 0, stream=None):
+        n = len(plans)
+        if not (n == len(As) == len(Bs)) or n == 0:
+            raise ValueError("plans, As and Bs must be non-empty and of equal length")
+        arr = lambda xs: (_VP * n)(*[x.handle.value for x in xs])
+        h = _VP()
+        _check(_lib.load().cht_batch_create(n, arr(plans), arr(As), arr(Bs), mode, nslices,
+                                            _stream(stream), ctypes.byref(h)),
+               "cht_batch_create")
+        self._h = h
+        self._keep = (list(plans), list(As), list(Bs))
+        self.count = n
+        self.mode = mode
+        self.useful_flops = sum(p.useful_flops for p in plans)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            try:
+                _lib.load().cht_batch_free(self._h)
+            except Exception:
+                pass
+            self._h = None
+
+    def run(self, stream=None):
+        _check(_lib.load().cht_batch_run(self._h, _stream(stream)), "cht_batch_run")
+
+    def output(self, i: int) -> Matrix:
+        h = _VP()
+        _check(_lib.load().cht_batch_output(self._h, i, ctypes.byref(h)), "cht_batch_output")
+        return Matrix(h, owned=False, parent=self)
+
+
 def cht_to_dense(M: Matrix, stream=None) -> torch.Tensor:
     return M.to_dense(stream)
 

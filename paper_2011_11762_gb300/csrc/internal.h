@@ -139,6 +139,22 @@ struct GemmWork {
 // Z[o] = sum_p op(X[px[p]]) op(Y[py[p]]) for every unit; FP64.
 int launch_leafgemm_f64(const GemmWork &w, cudaStream_t s);
 
+// One product of a batch, as the batched kernels see it.
+struct ProdDesc {
+  const double *X;
+  const double *Y;
+  double *Z;
+  const int32_t *px;
+  const int32_t *py;
+  const int64_t *seg;
+  int32_t b;
+  int32_t pad;
+};
+// Batched FP64 multiply: units (product << 32 | output leaf) in one launch.
+// d_counter: 8 bytes of device scratch, zeroed by the call.
+int launch_leafgemm_f64_batch(const ProdDesc *d_prods, const int64_t *d_units, int64_t nunits,
+                              unsigned long long *d_counter, cudaStream_t s);
+
 int launch_fp64_peak(int engine, cudaStream_t s, double *tflops);
 
 }  // namespace cht
@@ -171,4 +187,21 @@ struct cht_plan {
   cht::DevArray<int32_t> dA_c, dA_b;      // pairs grouped by A leaf
   cht::DevArray<int32_t> dB_a, dB_c;      // pairs grouped by B leaf
   cht::DevArray<int32_t> idA, idB;        // identity schedules
+};
+
+// A batch of independent products run by one persistent launch.
+struct cht_batch {
+  int32_t count = 0;
+  int mode = CHT_FP64;
+  int nslices = 0;
+  std::vector<cht_plan *> plans;  // not owned: the caller keeps them alive
+  std::vector<cht_mat *> As, Bs;  // not owned
+  cht::DevArray<cht::ProdDesc> prods;
+  cht::DevArray<int64_t> units;   // (product << 32) | C leaf, in run order
+  cht::DevArray<double> cvals;    // every product's C values
+  cht::DevArray<unsigned long long> counter;
+  int64_t nunits = 0;
+  std::vector<std::unique_ptr<cht_mat>> views;
+  void *split_state = nullptr;    // owned by the split path
+  ~cht_batch();
 };

@@ -129,13 +129,60 @@ struct Tile<B, TX, TY, 1> {
   }
 };
 
+// One output leaf: Z = sum over the pair segment [p0, p0 + np) of
+// op(X[px[p]]) op(Y[py[p]]), with a ring of S shared-memory stages (stage
+// pitch `pitch` doubles).  `it` counts the pairs this CTA consumed so far
+// (it fixes each stage's mbarrier phase).  Returns false after a timeout
+// (recorded in `status`; this CTA's copies in flight have landed).
+template <int B, bool TX, bool TY, int ENGINE, int S>
+__device__ bool run_unit(const double *__restrict__ X, const double *__restrict__ Y,
+                         double *__restrict__ Z, const int32_t *__restrict__ px,
+                         const int32_t *__restrict__ py, int64_t p0, int64_t np, double *sx,
+                         double *sy, int pitch, uint64_t *full, uint32_t &it, int64_t wait_ns,
+                         int *status) {
+  constexpr int LEAF = B * B;
+  constexpr uint32_t kBytes = LEAF * sizeof(double);
+  const int tid = threadIdx.x;
+  auto issue = [&](int64_t p, uint32_t st) {
+    const double *xsrc = X + static_cast<int64_t>(px[p]) * LEAF;
+    const double *ysrc = Y + static_cast<int64_t>(py[p]) * LEAF;
+    mbar_arrive_expect_tx(&full[st], 2 * kBytes);
+    bulk_g2s(sx + st * pitch, xsrc, kBytes, &full[st]);
+    bulk_g2s(sy + st * pitch, ysrc, kBytes, &full[st]);
+  };
+  Tile<B, TX, TY, ENGINE> tile;
+  tile.zero();
+  if (tid == 0)
+    for (int64_t j = 0; j < S - 1 && j < np; ++j) issue(p0 + j, (it + j) % S);
+  for (int64_t i = 0; i < np; ++i) {
+    if (tid == 0 && i + S - 1 < np) issue(p0 + i + S - 1, (it + i + S - 1) % S);
+    const uint32_t st = (it + i) % S, parity = ((it + i) / S) & 1u;
+    const bool ok = mbar_wait_bounded(&full[st], parity, wait_ns);
+    if (__syncthreads_or(!ok)) {
+      // Timed out: record it, let this CTA's copies in flight land, return.
+      if (tid == 0) {
+        atomicOr(status, DEV_STATUS_TIMEOUT);
+        const int64_t issued = (i + S < np) ? i + S : np;
+        for (int64_t j = i; j < issued; ++j)
+          mbar_wait_bounded(&full[(it + j) % S], ((it + j) / S) & 1u, kDrainBudgetNs);
+      }
+      __syncthreads();
+      return false;
+    }
+    tile.mac(sx + st * pitch, sy + st * pitch);
+    __syncthreads();  // stage st may be refilled after this point
+  }
+  it += static_cast<uint32_t>(np);
+  tile.store(Z);
+  return true;
+}
+
 template <int B, bool TX, bool TY, int ENGINE>
 __global__ void __launch_bounds__(kThreads)
     k_leafgemm_f64(const GemmWork w, int *__restrict__ status, int64_t wait_ns,
                    unsigned long long *__restrict__ next_unit) {
   using Cfg = LeafCfg<B>;
   constexpr int S = Cfg::kStages, LEAF = Cfg::kLeaf;
-  constexpr uint32_t kBytes = LEAF * sizeof(double);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double *sx = reinterpret_cast<double *>(smem_raw);
   double *sy = sx + S * LEAF;
@@ -149,15 +196,6 @@ __global__ void __launch_bounds__(kThreads)
   }
   __syncthreads();
 
-  auto issue = [&](int64_t p, uint32_t st) {
-    const double *xsrc = w.X + static_cast<int64_t>(w.px[p]) * LEAF;
-    const double *ysrc = w.Y + static_cast<int64_t>(w.py[p]) * LEAF;
-    mbar_arrive_expect_tx(&full[st], 2 * kBytes);
-    bulk_g2s(sx + st * LEAF, xsrc, kBytes, &full[st]);
-    bulk_g2s(sy + st * LEAF, ysrc, kBytes, &full[st]);
-  };
-
-  Tile<B, TX, TY, ENGINE> tile;
   uint32_t it = 0;  // pairs consumed so far by this CTA
   for (;;) {
     if (tid == 0) s_unit = static_cast<long long>(atomicAdd(next_unit, 1ULL));
@@ -167,29 +205,50 @@ __global__ void __launch_bounds__(kThreads)
     if (u >= w.nunits) break;
     const int64_t o = w.order[u];
     const int64_t p0 = w.seg[o], np = w.seg[o + 1] - p0;
-    tile.zero();
-    if (tid == 0)
-      for (int64_t j = 0; j < S - 1 && j < np; ++j) issue(p0 + j, (it + j) % S);
-    for (int64_t i = 0; i < np; ++i) {
-      if (tid == 0 && i + S - 1 < np) issue(p0 + i + S - 1, (it + i + S - 1) % S);
-      const uint32_t st = (it + i) % S, parity = ((it + i) / S) & 1u;
-      const bool ok = mbar_wait_bounded(&full[st], parity, wait_ns);
-      if (__syncthreads_or(!ok)) {
-        // Timed out: record it, let this CTA's copies in flight land, return.
-        if (tid == 0) {
-          atomicOr(status, DEV_STATUS_TIMEOUT);
-          const int64_t issued = (i + S < np) ? i + S : np;
-          for (int64_t j = i; j < issued; ++j)
-            mbar_wait_bounded(&full[(it + j) % S], ((it + j) / S) & 1u, kDrainBudgetNs);
-        }
-        __syncthreads();
-        return;
-      }
-      tile.mac(sx + st * LEAF, sy + st * LEAF);
-      __syncthreads();  // stage st may be refilled after this point
-    }
-    it += static_cast<uint32_t>(np);
-    tile.store(w.Z + o * LEAF);
+    if (!run_unit<B, TX, TY, ENGINE, S>(w.X, w.Y, w.Z + o * LEAF, w.px, w.py, p0, np, sx, sy,
+                                        LEAF, full, it, wait_ns, status))
+      return;
+  }
+}
+
+// Batched form: units from many products (each with its own leaf size) in
+// one launch.  Unit u is product units[u] >> 32, output leaf units[u] & 0xffffffff.
+template <int ENGINE>
+__global__ void __launch_bounds__(kThreads)
+    k_leafgemm_f64_batch(const ProdDesc *__restrict__ prods, const int64_t *__restrict__ units,
+                         int64_t nunits, int *__restrict__ status, int64_t wait_ns,
+                         unsigned long long *__restrict__ next_unit) {
+  constexpr int S = 2, PITCH = 64 * 64;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double *sx = reinterpret_cast<double *>(smem_raw);
+  double *sy = sx + S * PITCH;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sy + S * PITCH);
+  __shared__ long long s_unit;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st) mbar_init(&full[st], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t it = 0;
+  for (;;) {
+    if (tid == 0) s_unit = static_cast<long long>(atomicAdd(next_unit, 1ULL));
+    __syncthreads();
+    const int64_t u = s_unit;
+    __syncthreads();
+    if (u >= nunits) break;
+    const int64_t packed = units[u];
+    const ProdDesc d = prods[packed >> 32];
+    const int64_t o = packed & 0xffffffffLL;
+    const int64_t p0 = d.seg[o], np = d.seg[o + 1] - p0;
+    bool ok;
+    if (d.b == 64)
+      ok = run_unit<64, false, false, ENGINE, S>(d.X, d.Y, d.Z + o * 4096, d.px, d.py, p0, np, sx,
+                                                 sy, PITCH, full, it, wait_ns, status);
+    else
+      ok = run_unit<32, false, false, ENGINE, S>(d.X, d.Y, d.Z + o * 1024, d.px, d.py, p0, np, sx,
+                                                 sy, PITCH, full, it, wait_ns, status);
+    if (!ok) return;
   }
 }
 
@@ -266,6 +325,26 @@ int launch_leafgemm_f64(const GemmWork &w, cudaStream_t s) {
     return engine ? launch_b<32, 1>(w, s, status, counter.p) : launch_b<32, 0>(w, s, status, counter.p);
   set_error("leaf size %d: the numeric kernels take b = 32 or b = 64", w.b);
   return CHT_ERR_UNSUPPORTED;
+}
+
+int launch_leafgemm_f64_batch(const ProdDesc *d_prods, const int64_t *d_units, int64_t nunits,
+                              unsigned long long *d_counter, cudaStream_t s) {
+  if (nunits <= 0) return CHT_OK;
+  int *status = nullptr;
+  CHT_TRY(device_status_ptr(&status));
+  int sms = 0;
+  CHT_TRY(num_sms(&sms));
+  const size_t smem = sizeof(double) * 2 * 2 * 64 * 64 + 16 * 2;
+  auto kern = g_opt.fp64_engine ? k_leafgemm_f64_batch<1> : k_leafgemm_f64_batch<0>;
+  CHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem)));
+  int occ = 0;
+  CHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
+  const int64_t grid = std::min<int64_t>(nunits, static_cast<int64_t>(sms) * std::max(1, occ));
+  CHT_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s));
+  kern<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(d_prods, d_units, nunits, status,
+                                                          g_opt.wait_budget_ns, d_counter);
+  return launched("leafgemm_f64_batch");
 }
 
 int launch_fp64_peak(int engine, cudaStream_t s, double *tflops) {

@@ -384,253 +384,329 @@ __global__ void k_split_b(const double *__restrict__ vals, const int32_t *__rest
 
 // ------------------------------------------------------------ main kernel --
 
-struct SplitArgs {
-  const uint8_t *a_slices;
-  const uint8_t *b_slices;
-  const int32_t *pa;
-  const int32_t *pb;
-  const int64_t *cseg;
+// One product as the split kernel sees it.
+struct SplitProd {
+  const uint8_t *a_slices;  // [nA][SA][tile], tiles in the shared-memory image
+  const uint8_t *b_slices;  // [nB][6][tile]
+  const int32_t *pa;        // per pair: A leaf (pairs sorted by C leaf, then K)
+  const int32_t *pb;        // per pair: B leaf
+  const int64_t *cseg;      // per C leaf: pair segment
   const int32_t *crow;
   const int32_t *ccol;
   const int *row_exp;
   const int *col_exp;
   double *C;
-  int64_t nunits;
+  int32_t b;
+  int32_t pad;
 };
 
-template <int B>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_split_gemm(const SplitArgs args, int *__restrict__ status, int64_t wait_ns) {
+// Kernel-wide sizes for the largest leaf size a launch serves.
+template <int MAXB>
+struct KCfg;
+template <>
+struct KCfg<64> {
+  static constexpr int STAGES = 2, STAGE = Smem<64>::STAGE, XBUF = Smem<64>::XBUF;
+  static constexpr int TMEM_COLS = 512;
+};
+template <>
+struct KCfg<32> {
+  static constexpr int STAGES = 3, STAGE = Smem<32>::STAGE, XBUF = Smem<32>::XBUF;
+  static constexpr int TMEM_COLS = 256;
+};
+template <int MAXB>
+constexpr size_t kernel_smem() {
+  return static_cast<size_t>(KCfg<MAXB>::STAGES) * KCfg<MAXB>::STAGE + KCfg<MAXB>::XBUF + 256 +
+         1024;
+}
+
+// Per-CTA control block (pointers into shared memory).
+struct Ctl {
+  uint8_t *stage_base;
+  int stage_bytes;
+  int64_t *xbuf;
+  uint64_t *full, *empty, *acc_full, *acc_empty, *drain, *ep_bar;
+  volatile int *abort_flag;
+  uint32_t tmem;
+  int64_t wait_ns;
+};
+
+// Producer: the pairs of C leaf o into the stage ring.
+template <int B, int S>
+__device__ bool produce_unit(const SplitProd &d, int64_t o, uint32_t &k, const Ctl &c) {
+  using SM = Smem<B>;
+  const int64_t p0 = d.cseg[o], p1 = d.cseg[o + 1];
+  for (int64_t p = p0; p < p1; ++p, ++k) {
+    const uint32_t st = k % S, ph = (k / S) & 1u;
+    if (!wait_or_abort(&c.empty[st], ph ^ 1u, c.wait_ns, c.abort_flag)) return false;
+    uint8_t *sa = c.stage_base + st * c.stage_bytes;
+    mbar_arrive_expect_tx(&c.full[st], SM::STAGE);
+    bulk_g2s(sa, d.a_slices + static_cast<int64_t>(d.pa[p]) * SM::A_BYTES, SM::A_BYTES,
+             &c.full[st]);
+    bulk_g2s(sa + SM::A_BYTES, d.b_slices + static_cast<int64_t>(d.pb[p]) * SM::B_BYTES,
+             SM::B_BYTES, &c.full[st]);
+  }
+  return true;
+}
+
+// MMA issuer: all slice-product blocks of C leaf o, window by window.
+template <int B, int S>
+__device__ bool mma_unit(const SplitProd &d, int64_t o, uint32_t &k, uint32_t &win,
+                         const Ctl &c) {
   using CF = Cfg<B>;
   using SM = Smem<B>;
-  constexpr int N = CF::N, PARTS = CF::PARTS, STAGES = CF::STAGES, WINDOW = CF::WINDOW;
-  constexpr int E = N / 2;  // columns per epilogue thread
+  constexpr int N = CF::N;
   constexpr uint32_t IDESC = make_idesc(128, N);
-  constexpr uint32_t STAGE_TX = SM::STAGE;
+  const int64_t p0 = d.cseg[o], np = d.cseg[o + 1] - p0;
+  bool fresh[kRegions];
+#pragma unroll
+  for (int t = 0; t < kRegions; ++t) fresh[t] = true;
+  for (int64_t w0 = 0; w0 < np; w0 += CF::WINDOW, ++win) {
+    // the epilogue must have read the regions of the previous window
+    if (!wait_or_abort(c.acc_empty, (win & 1u) ^ 1u, c.wait_ns, c.abort_flag)) return false;
+    tc_fence_after();
+#pragma unroll
+    for (int t = 0; t <= kExactLast - 2; ++t) fresh[t] = true;
+    const int64_t w1 = min(np, w0 + CF::WINDOW);
+    for (int64_t i = w0; i < w1; ++i, ++k) {
+      const uint32_t st = k % S, ph = (k / S) & 1u;
+      if (!wait_or_abort(&c.full[st], ph, c.wait_ns, c.abort_flag)) return false;
+      tc_fence_after();
+      const uint32_t sa = smem_addr(c.stage_base + st * c.stage_bytes);
+      const uint32_t sb = sa + SM::A_BYTES;
+#pragma unroll
+      for (int bi = 0; bi < CF::NBLK; ++bi) {
+        const int bu = (B == 64) ? c_blk64[bi][0] : c_blk32[bi][0];
+        const int bj = (B == 64) ? c_blk64[bi][1] : c_blk32[bi][1];
+        const int t = bu + bj - 2;  // region index 0..5
+        const uint64_t ad = sw128_desc(sa + (bu - 1) * SM::TILE);
+        const uint64_t bd = sw128_desc(sb + (bj - 1) * SM::TILE);
+        const uint32_t dt = c.tmem + static_cast<uint32_t>(t * N);
+#pragma unroll
+        for (int kk = 0; kk < CF::KSTEPS; ++kk) {
+          const uint32_t acc = (fresh[t] && kk == 0) ? 0u : 1u;
+          tc_mma(dt, ad + 2 * kk, bd + 2 * kk, IDESC, acc);
+        }
+        fresh[t] = false;
+      }
+      tc_commit(&c.empty[st]);  // frees the stage when these MMAs finish
+    }
+    tc_commit(c.acc_full);
+  }
+  return true;
+}
 
+// Epilogue (one of 8 warps): exact windows into int64, final recombination
+// and the FP64 store of C leaf o.
+template <int B>
+__device__ bool epi_unit(const SplitProd &d, int64_t o, uint32_t &win, uint32_t &epb,
+                         const Ctl &c, int *status) {
+  using CF = Cfg<B>;
+  constexpr int N = CF::N, PARTS = CF::PARTS, WINDOW = CF::WINDOW;
+  constexpr int E = N / 2;  // columns per epilogue thread
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3;                // TMEM lane quarter of this warp
+  const int half = (warp >= 6) ? 1 : 0;  // which half of the columns
+  const int part = (B == 64) ? (q >> 1) : q;
+  const int row = (B == 64) ? ((q & 1) * 32 + lane) : lane;
+  const int c0 = half * E;
+  const uint32_t lane_base = c.tmem + (static_cast<uint32_t>(32 * q) << 16);
+  auto ep_sync = [&]() -> bool {  // bounded barrier among the 8 epilogue warps
+    __syncwarp();
+    if (lane == 0) mbar_arrive(c.ep_bar);
+    const bool r = wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag);
+    ++epb;
+    return r;
+  };
+  const int64_t np = d.cseg[o + 1] - d.cseg[o];
+  long long Q[E];
+#pragma unroll
+  for (int cc = 0; cc < E; ++cc) Q[cc] = 0;
+  for (int64_t w0 = 0; w0 < np; w0 += WINDOW, ++win) {
+    const bool last = w0 + WINDOW >= np;
+    if (!wait_or_abort(c.acc_full, win & 1u, c.wait_ns, c.abort_flag)) return false;
+    tc_fence_after();
+    float v[E];
+#pragma unroll
+    for (int t = 0; t <= kExactLast - 2; ++t) {
+      tmem_ld<E>(lane_base + static_cast<uint32_t>(t * N + c0), v);
+      tc_wait_ld();
+#pragma unroll
+      for (int cc = 0; cc < E; ++cc)
+        Q[cc] += static_cast<long long>(__float2int_rn(v[cc])) << (kW * (kExactLast - 2 - t));
+    }
+    float rl[E];  // low regions, folded: R6 2^-8 + R7 2^-16
+    if (last) {
+      tmem_ld<E>(lane_base + static_cast<uint32_t>(4 * N + c0), v);
+      tc_wait_ld();
+#pragma unroll
+      for (int cc = 0; cc < E; ++cc) rl[cc] = v[cc] * 0x1p-8f;
+      tmem_ld<E>(lane_base + static_cast<uint32_t>(5 * N + c0), v);
+      tc_wait_ld();
+#pragma unroll
+      for (int cc = 0; cc < E; ++cc) rl[cc] = fmaf(v[cc], 0x1p-16f, rl[cc]);
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(c.acc_empty);
+    if (!last) continue;
+    // part value in units of 2^-(8 (5 + part) + 16); parts > 0 are rounded
+    // to units of 2^-56 (the plan limits the window count so that they fit
+    // 64 bits) and handed to part 0 through shared memory
+    auto part_value = [&](int cc) -> __int128 {
+      return (static_cast<__int128>(Q[cc]) << 16) +
+             static_cast<__int128>(__float2ll_rn(rl[cc] * 65536.0f));
+    };
+    if (part > 0) {
+      const int sh = kW * part;
+#pragma unroll
+      for (int cc = 0; cc < E; ++cc)
+        c.xbuf[(static_cast<int64_t>(part - 1) * B + row) * B + c0 + cc] = static_cast<long long>(
+            (part_value(cc) + (static_cast<__int128>(1) << (sh - 1))) >> sh);
+    }
+    if (!ep_sync()) return false;
+    if (part == 0) {
+      const int er = d.row_exp[static_cast<int64_t>(d.crow[o]) * B + row];
+      const int64_t colbase = static_cast<int64_t>(d.ccol[o]) * B;
+      double *dst = d.C + o * B * B + static_cast<int64_t>(row) * B + c0;
+#pragma unroll
+      for (int cc = 0; cc < E; cc += 2) {
+        __int128 t0 = part_value(cc), t1 = part_value(cc + 1);
+#pragma unroll
+        for (int p = 1; p < PARTS; ++p) {
+          t0 += c.xbuf[(static_cast<int64_t>(p - 1) * B + row) * B + c0 + cc];
+          t1 += c.xbuf[(static_cast<int64_t>(p - 1) * B + row) * B + c0 + cc + 1];
+        }
+        const int f0 = d.col_exp[colbase + c0 + cc], f1 = d.col_exp[colbase + c0 + cc + 1];
+        const bool z0 = er == kNoExp || f0 == kNoExp, z1 = er == kNoExp || f1 == kNoExp;
+        double2 out;
+        out.x = z0 ? 0.0 : scaled_i128_to_double(t0, er + f0 - 56);
+        out.y = z1 ? 0.0 : scaled_i128_to_double(t1, er + f1 - 56);
+        *reinterpret_cast<double2 *>(dst + cc) = out;
+      }
+    }
+    if (!ep_sync()) return false;
+  }
+  (void)status;
+  return true;
+}
+
+// The persistent split kernel.  Units are dealt round-robin to the CTAs:
+// with `prods` NULL the units are the C leaves 0..nunits-1 of `single`;
+// otherwise unit u is product units[u] >> 32, C leaf units[u] & 0xffffffff.
+template <int MAXB>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_split_gemm(const SplitProd single, const SplitProd *__restrict__ prods,
+                 const int64_t *__restrict__ units, int64_t nunits, int *__restrict__ status,
+                 int64_t wait_ns) {
+  using KC = KCfg<MAXB>;
+  constexpr int S = KC::STAGES;
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
   const uint32_t raw_addr = smem_addr(smem_raw);
   uint8_t *smem = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
-  uint8_t *stage_base = smem;
-  int64_t *xbuf = reinterpret_cast<int64_t *>(smem + STAGES * SM::STAGE);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * SM::STAGE + SM::XBUF);
-  uint64_t *full = bars;                // [STAGES]
-  uint64_t *empty = bars + STAGES;      // [STAGES]
-  uint64_t *acc_full = bars + 2 * STAGES;
-  uint64_t *acc_empty = acc_full + 1;
-  uint64_t *drain = acc_full + 2;
-  uint64_t *ep_bar = acc_full + 3;  // epilogue-only barrier (8 warps)
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ep_bar + 1);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * KC::STAGE + KC::XBUF);
+  Ctl c;
+  c.stage_base = smem;
+  c.stage_bytes = KC::STAGE;
+  c.xbuf = reinterpret_cast<int64_t *>(smem + S * KC::STAGE);
+  c.full = bars;
+  c.empty = bars + S;
+  c.acc_full = bars + 2 * S;
+  c.acc_empty = c.acc_full + 1;
+  c.drain = c.acc_full + 2;
+  c.ep_bar = c.acc_full + 3;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(c.ep_bar + 1);
+  c.abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  c.wait_ns = wait_ns;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+    for (int st = 0; st < S; ++st) {
+      mbar_init(&c.full[st], 1);
+      mbar_init(&c.empty[st], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, kEpiWarps);
-    mbar_init(drain, 1);
-    mbar_init(ep_bar, kEpiWarps);
-    *abort_flag = 0;
+    mbar_init(c.acc_full, 1);
+    mbar_init(c.acc_empty, kEpiWarps);
+    mbar_init(c.drain, 1);
+    mbar_init(c.ep_bar, kEpiWarps);
+    *c.abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 1) tmem_alloc(tmem_slot, CF::TMEM_COLS);
+  if (warp == 1) tmem_alloc(tmem_slot, KC::TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
+  c.tmem = *tmem_slot;
 
   auto fail = [&]() {
     atomicOr(status, DEV_STATUS_TIMEOUT);
-    *abort_flag = 1;
+    *c.abort_flag = 1;
+  };
+  auto unit = [&](int64_t u, int64_t &o) -> SplitProd {
+    if (!prods) {
+      o = u;
+      return single;
+    }
+    const int64_t packed = units[u];
+    o = packed & 0xffffffffLL;
+    return prods[packed >> 32];
   };
 
   if (warp == 0) {
-    // ------------------------------------------------------- producer --
     if (lane == 0) {
       uint32_t k = 0;  // pairs issued
-      bool ok = true;
-      for (int64_t u = blockIdx.x; ok && u < args.nunits; u += gridDim.x) {
-        const int64_t p0 = args.cseg[u], p1 = args.cseg[u + 1];
-        for (int64_t p = p0; p < p1; ++p, ++k) {
-          const uint32_t st = k % STAGES, ph = (k / STAGES) & 1u;
-          if (!wait_or_abort(&empty[st], ph ^ 1u, wait_ns, abort_flag)) {
-            fail();
-            ok = false;
-            break;
-          }
-          uint8_t *sa = stage_base + st * SM::STAGE;
-          mbar_arrive_expect_tx(&full[st], STAGE_TX);
-          bulk_g2s(sa, args.a_slices + static_cast<int64_t>(args.pa[p]) * SM::A_BYTES, SM::A_BYTES,
-                   &full[st]);
-          bulk_g2s(sa + SM::A_BYTES, args.b_slices + static_cast<int64_t>(args.pb[p]) * SM::B_BYTES,
-                   SM::B_BYTES, &full[st]);
+      for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        int64_t o;
+        const SplitProd d = unit(u, o);
+        bool ok;
+        if constexpr (MAXB == 64)
+          ok = d.b == 64 ? produce_unit<64, S>(d, o, k, c) : produce_unit<32, S>(d, o, k, c);
+        else
+          ok = produce_unit<32, S>(d, o, k, c);
+        if (!ok) {
+          fail();
+          break;
         }
       }
       // copies in flight must land before shared memory goes away (after a
       // normal run these phases completed long ago)
-      for (uint32_t j = (k >= STAGES ? k - STAGES : 0); j < k; ++j)
-        mbar_wait_bounded(&full[j % STAGES], (j / STAGES) & 1u, kDrainNs);
+      for (uint32_t j = (k >= S ? k - S : 0); j < k; ++j)
+        mbar_wait_bounded(&c.full[j % S], (j / S) & 1u, kDrainNs);
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------ MMA issuer --
     if (lane == 0) {
-      uint32_t k = 0;   // pairs consumed
-      uint32_t win = 0; // windows issued
-      bool ok = true;
-      for (int64_t u = blockIdx.x; ok && u < args.nunits; u += gridDim.x) {
-        const int64_t p0 = args.cseg[u], np = args.cseg[u + 1] - p0;
-        bool fresh[kRegions];
-#pragma unroll
-        for (int t = 0; t < kRegions; ++t) fresh[t] = true;
-        for (int64_t w0 = 0; ok && w0 < np; w0 += WINDOW, ++win) {
-          // the epilogue must have read the regions of the previous window
-          if (!wait_or_abort(acc_empty, (win & 1u) ^ 1u, wait_ns, abort_flag)) {
-            fail();
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-#pragma unroll
-          for (int t = 0; t <= kExactLast - 2; ++t) fresh[t] = true;
-          const int64_t w1 = min(np, w0 + WINDOW);
-          for (int64_t i = w0; i < w1; ++i, ++k) {
-            const uint32_t st = k % STAGES, ph = (k / STAGES) & 1u;
-            if (!wait_or_abort(&full[st], ph, wait_ns, abort_flag)) {
-              fail();
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t sa = smem_addr(stage_base + st * SM::STAGE);
-            const uint32_t sb = sa + SM::A_BYTES;
-#pragma unroll
-            for (int bi = 0; bi < CF::NBLK; ++bi) {
-              const int bu = (B == 64) ? c_blk64[bi][0] : c_blk32[bi][0];
-              const int bj = (B == 64) ? c_blk64[bi][1] : c_blk32[bi][1];
-              const int t = bu + bj - 2;  // region index 0..5
-              const uint64_t ad = sw128_desc(sa + (bu - 1) * SM::TILE);
-              const uint64_t bd = sw128_desc(sb + (bj - 1) * SM::TILE);
-              const uint32_t dt = tmem + static_cast<uint32_t>(t * N);
-#pragma unroll
-              for (int kk = 0; kk < CF::KSTEPS; ++kk) {
-                const uint32_t acc = (fresh[t] && kk == 0) ? 0u : 1u;
-                tc_mma(dt, ad + 2 * kk, bd + 2 * kk, IDESC, acc);
-              }
-              fresh[t] = false;
-            }
-            tc_commit(&empty[st]);  // frees the stage when these MMAs finish
-          }
-          if (ok) tc_commit(acc_full);
+      uint32_t k = 0, win = 0;
+      for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        int64_t o;
+        const SplitProd d = unit(u, o);
+        bool ok;
+        if constexpr (MAXB == 64)
+          ok = d.b == 64 ? mma_unit<64, S>(d, o, k, win, c) : mma_unit<32, S>(d, o, k, win, c);
+        else
+          ok = mma_unit<32, S>(d, o, k, win, c);
+        if (!ok) {
+          fail();
+          break;
         }
       }
       // in-flight MMAs must finish before TMEM is released
-      tc_commit(drain);
-      mbar_wait_bounded(drain, 0, kDrainNs);
+      tc_commit(c.drain);
+      mbar_wait_bounded(c.drain, 0, kDrainNs);
     }
   } else {
-    // -------------------------------------------------------- epilogue --
-    const int q = warp & 3;                  // TMEM lane quarter of this warp
-    const int half = (warp >= 6) ? 1 : 0;    // which half of the columns
-    const int part = (B == 64) ? (q >> 1) : q;
-    const int row = (B == 64) ? ((q & 1) * 32 + lane) : lane;
-    const int c0 = half * E;
-    const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * q) << 16);
     uint32_t win = 0, epb = 0;
-    bool ok = true;
-    // bounded barrier among the 8 epilogue warps
-    auto ep_sync = [&]() -> bool {
-      __syncwarp();
-      if (lane == 0) mbar_arrive(ep_bar);
-      const bool r = wait_or_abort(ep_bar, epb & 1u, wait_ns, abort_flag);
-      ++epb;
-      return r;
-    };
-    for (int64_t u = blockIdx.x; ok && u < args.nunits; u += gridDim.x) {
-      const int64_t np = args.cseg[u + 1] - args.cseg[u];
-      long long Q[E];
-#pragma unroll
-      for (int c = 0; c < E; ++c) Q[c] = 0;
-      for (int64_t w0 = 0; w0 < np; w0 += WINDOW, ++win) {
-        const bool last = w0 + WINDOW >= np;
-        if (!wait_or_abort(acc_full, win & 1u, wait_ns, abort_flag)) {
-          fail();
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        float v[E];
-#pragma unroll
-        for (int t = 0; t <= kExactLast - 2; ++t) {
-          tmem_ld<E>(lane_base + static_cast<uint32_t>(t * N + c0), v);
-          tc_wait_ld();
-#pragma unroll
-          for (int c = 0; c < E; ++c)
-            Q[c] += static_cast<long long>(__float2int_rn(v[c])) << (kW * (kExactLast - 2 - t));
-        }
-        float rl[E];  // low regions, folded: R6 2^-8 + R7 2^-16
-        if (last) {
-          tmem_ld<E>(lane_base + static_cast<uint32_t>(4 * N + c0), v);
-          tc_wait_ld();
-#pragma unroll
-          for (int c = 0; c < E; ++c) rl[c] = v[c] * 0x1p-8f;
-          tmem_ld<E>(lane_base + static_cast<uint32_t>(5 * N + c0), v);
-          tc_wait_ld();
-#pragma unroll
-          for (int c = 0; c < E; ++c) rl[c] = fmaf(v[c], 0x1p-16f, rl[c]);
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(acc_empty);
-        if (last) {
-          // part value in units of 2^-(8 (5 + part) + 16); parts > 0 are then
-          // rounded to units of 2^-56 (the plan limits the window count so
-          // that they fit 64 bits) and handed to part 0 through shared memory
-          auto part_value = [&](int c) -> __int128 {
-            return (static_cast<__int128>(Q[c]) << 16) +
-                   static_cast<__int128>(__float2ll_rn(rl[c] * 65536.0f));
-          };
-          if (part > 0) {
-            const int sh = kW * part;
-#pragma unroll
-            for (int c = 0; c < E; ++c)
-              xbuf[(static_cast<int64_t>(part - 1) * B + row) * B + c0 + c] =
-                  static_cast<long long>((part_value(c) + (static_cast<__int128>(1) << (sh - 1))) >> sh);
-          }
-          if (!ep_sync()) {
-            fail();
-            ok = false;
-            break;
-          }
-          if (part == 0) {
-            const int er = args.row_exp[static_cast<int64_t>(args.crow[u]) * B + row];
-            const int64_t colbase = static_cast<int64_t>(args.ccol[u]) * B;
-            double *dst = args.C + u * B * B + static_cast<int64_t>(row) * B + c0;
-#pragma unroll
-            for (int c = 0; c < E; c += 2) {
-              __int128 t0 = part_value(c), t1 = part_value(c + 1);
-#pragma unroll
-              for (int p = 1; p < PARTS; ++p) {
-                t0 += xbuf[(static_cast<int64_t>(p - 1) * B + row) * B + c0 + c];
-                t1 += xbuf[(static_cast<int64_t>(p - 1) * B + row) * B + c0 + c + 1];
-              }
-              const int f0 = args.col_exp[colbase + c0 + c], f1 = args.col_exp[colbase + c0 + c + 1];
-              const bool z0 = er == kNoExp || f0 == kNoExp, z1 = er == kNoExp || f1 == kNoExp;
-              double2 out;
-              out.x = z0 ? 0.0 : scaled_i128_to_double(t0, er + f0 - 56);
-              out.y = z1 ? 0.0 : scaled_i128_to_double(t1, er + f1 - 56);
-              *reinterpret_cast<double2 *>(dst + c) = out;
-            }
-          }
-          if (!ep_sync()) {
-            fail();
-            ok = false;
-            break;
-          }
-        }
+    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+      int64_t o;
+      const SplitProd d = unit(u, o);
+      bool ok;
+      if constexpr (MAXB == 64)
+        ok = d.b == 64 ? epi_unit<64>(d, o, win, epb, c, status)
+                       : epi_unit<32>(d, o, win, epb, c, status);
+      else
+        ok = epi_unit<32>(d, o, win, epb, c, status);
+      if (!ok) {
+        fail();
+        break;
       }
     }
   }
@@ -638,7 +714,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem, CF::TMEM_COLS);
+  if (warp == 1) tmem_dealloc(c.tmem, KC::TMEM_COLS);
 }
 
 unsigned grid_for(int64_t n, int threads) {
@@ -648,66 +724,105 @@ unsigned grid_for(int64_t n, int threads) {
   return static_cast<unsigned>(g);
 }
 
-template <int B>
-int run_split(cht_plan *plan, cht_mat *A, cht_mat *Bm, cudaStream_t s, double *Cvals) {
-  using CF = Cfg<B>;
-  using SM = Smem<B>;
-  const Pattern &pa = *A->pat, &pb = *Bm->pat;
-  const int64_t n = pa.n;
+// Scratch of one operand pair: line exponents and slices.
+struct Operands {
   DevArray<int> row_exp, col_exp;
   DevArray<uint8_t> a_sl, b_sl;
-  CHT_TRY(row_exp.alloc(n, s));
-  CHT_TRY(col_exp.alloc(n, s));
-  CHT_TRY(a_sl.alloc(static_cast<size_t>(pa.nnz) * SM::A_BYTES, s));
-  CHT_TRY(b_sl.alloc(static_cast<size_t>(pb.nnz) * SM::B_BYTES, s));
+};
+
+int alloc_operands(const Pattern &pa, const Pattern &pb, cudaStream_t s, Operands &op) {
+  const int b = pa.b;
+  const size_t a_bytes = b == 64 ? Smem<64>::A_BYTES : Smem<32>::A_BYTES;
+  const size_t b_bytes = b == 64 ? Smem<64>::B_BYTES : Smem<32>::B_BYTES;
+  CHT_TRY(op.row_exp.alloc(pa.n, s));
+  CHT_TRY(op.col_exp.alloc(pa.n, s));
+  CHT_TRY(op.a_sl.alloc(static_cast<size_t>(pa.nnz) * a_bytes, s));
+  CHT_TRY(op.b_sl.alloc(static_cast<size_t>(pb.nnz) * b_bytes, s));
+  return CHT_OK;
+}
+
+// Exponents and slices of A and B (the pre-kernels of one product).
+template <int B>
+int split_operands(const cht_mat *A, const cht_mat *Bm, cudaStream_t s, Operands &op) {
+  using CF = Cfg<B>;
+  const Pattern &pa = *A->pat, &pb = *Bm->pat;
   // kNoExp fill (every byte 0x80)
-  CHT_CUDA_TRY(cudaMemsetAsync(row_exp.p, 0x80, sizeof(int) * n, s));
-  CHT_CUDA_TRY(cudaMemsetAsync(col_exp.p, 0x80, sizeof(int) * n, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(op.row_exp.p, 0x80, sizeof(int) * pa.n, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(op.col_exp.p, 0x80, sizeof(int) * pa.n, s));
+  const double *av = const_cast<cht_mat *>(A)->values();
+  const double *bv = const_cast<cht_mat *>(Bm)->values();
   if (pa.nnz > 0) {
-    k_row_exp<<<grid_for(pa.nnz * B * 32, 256), 256, 0, s>>>(A->values(), pa.brow.p, pa.nnz, B,
-                                                             row_exp.p);
+    k_row_exp<<<grid_for(pa.nnz * B * 32, 256), 256, 0, s>>>(av, pa.brow.p, pa.nnz, B,
+                                                             op.row_exp.p);
     CHT_TRY(launched("row_exp"));
   }
   if (pb.nnz > 0) {
-    k_col_exp<<<grid_for(pb.nnz * B, 256), 256, 0, s>>>(Bm->values(), pb.bcol.p, pb.nnz, B,
-                                                        col_exp.p);
+    k_col_exp<<<grid_for(pb.nnz * B, 256), 256, 0, s>>>(bv, pb.bcol.p, pb.nnz, B, op.col_exp.p);
     CHT_TRY(launched("col_exp"));
   }
   if (pa.nnz > 0) {
     k_split_a<B, CF::SA><<<grid_for(pa.nnz * B * (B / 8), 256), 256, 0, s>>>(
-        A->values(), pa.brow.p, pa.nnz, row_exp.p, a_sl.p);
+        av, pa.brow.p, pa.nnz, op.row_exp.p, op.a_sl.p);
     CHT_TRY(launched("split_a"));
   }
   if (pb.nnz > 0) {
-    k_split_b<B><<<grid_for(pb.nnz * B * (B / 8), 256), 256, 0, s>>>(
-        Bm->values(), pb.bcol.p, pb.nnz, col_exp.p, b_sl.p);
+    k_split_b<B><<<grid_for(pb.nnz * B * (B / 8), 256), 256, 0, s>>>(bv, pb.bcol.p, pb.nnz,
+                                                                   op.col_exp.p, op.b_sl.p);
     CHT_TRY(launched("split_b"));
   }
-  const int64_t units = plan->C->nnz;
-  if (units == 0) return CHT_OK;
+  return CHT_OK;
+}
+
+SplitProd make_prod(const cht_plan *plan, const Operands &op, double *Cvals) {
+  SplitProd d{};
+  d.a_slices = op.a_sl.p;
+  d.b_slices = op.b_sl.p;
+  d.pa = plan->pa.p;
+  d.pb = plan->pb.p;
+  d.cseg = plan->cseg.p;
+  d.crow = plan->C->brow.p;
+  d.ccol = plan->C->bcol.p;
+  d.row_exp = op.row_exp.p;
+  d.col_exp = op.col_exp.p;
+  d.C = Cvals;
+  d.b = plan->b;
+  return d;
+}
+
+template <int MAXB>
+int launch_split(const SplitProd &single, const SplitProd *prods, const int64_t *units,
+                 int64_t nunits, cudaStream_t s) {
+  if (nunits <= 0) return CHT_OK;
   int *status = nullptr;
   CHT_TRY(device_status_ptr(&status));
   int sms = 0;
   CHT_TRY(num_sms(&sms));
-  auto kern = k_split_gemm<B>;
+  auto kern = k_split_gemm<MAXB>;
+  constexpr size_t smem = kernel_smem<MAXB>();
   CHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(SM::DYN)));
-  SplitArgs a{};
-  a.a_slices = a_sl.p;
-  a.b_slices = b_sl.p;
-  a.pa = plan->pa.p;
-  a.pb = plan->pb.p;
-  a.cseg = plan->cseg.p;
-  a.crow = plan->C->brow.p;
-  a.ccol = plan->C->bcol.p;
-  a.row_exp = row_exp.p;
-  a.col_exp = col_exp.p;
-  a.C = Cvals;
-  a.nunits = units;
-  const int64_t grid = std::min<int64_t>(units, sms);
-  kern<<<static_cast<unsigned>(grid), kThreads, SM::DYN, s>>>(a, status, g_opt.wait_budget_ns);
+                                    static_cast<int>(smem)));
+  const int64_t grid = std::min<int64_t>(nunits, sms);
+  kern<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(single, prods, units, nunits, status,
+                                                          g_opt.wait_budget_ns);
   return launched("split_gemm");
 }
+
+int check_segments(const cht_plan *plan) {
+  // the parts handed between epilogue warps hold (windows * 2^56) in 64 bits
+  const int window = plan->b == 64 ? Cfg<64>::WINDOW : Cfg<32>::WINDOW;
+  if ((plan->max_seg + window - 1) / window >= 128) {
+    set_error("split form: a C leaf has %lld leaf pairs (at most %d); use CHT_FP64",
+              (long long)plan->max_seg, 127 * window);
+    return CHT_ERR_UNSUPPORTED;
+  }
+  return CHT_OK;
+}
+
+struct SplitBatch {
+  std::vector<Operands> ops;
+  DevArray<SplitProd> prods;
+  int maxb = 32;
+};
 
 }  // namespace
 
@@ -718,21 +833,63 @@ int split_multiply(cht_plan *plan, cht_mat *A, cht_mat *B, int nslices, cudaStre
     return CHT_ERR_UNSUPPORTED;
   }
   const int b = plan->b;
-  // the parts handed between epilogue warps hold (windows * 2^56) in 64 bits
-  const int window = b == 64 ? Cfg<64>::WINDOW : Cfg<32>::WINDOW;
-  if ((plan->max_seg + window - 1) / window >= 128) {
-    set_error("split form: a C leaf has %lld leaf pairs (at most %d); use CHT_FP64",
-              (long long)plan->max_seg, 127 * window);
+  if (b != 32 && b != 64) {
+    set_error("leaf size %d: the split form takes b = 32 or b = 64", b);
     return CHT_ERR_UNSUPPORTED;
   }
+  CHT_TRY(check_segments(plan));
   // elementwise bound relative to 2^(e_r + f_c): K (s + 3) 2^(-s w) with
   // K <= n, plus the FP32 rounding of the low regions (below 2^-50)
-  const double K = static_cast<double>(plan->n);
-  *err_bound = K * (kSB + 3) * 0x1p-48 + 0x1p-50;
-  if (b == 64) return run_split<64>(plan, A, B, s, Cvals);
-  if (b == 32) return run_split<32>(plan, A, B, s, Cvals);
-  set_error("leaf size %d: the split form takes b = 32 or b = 64", b);
-  return CHT_ERR_UNSUPPORTED;
+  *err_bound = static_cast<double>(plan->n) * (kSB + 3) * 0x1p-48 + 0x1p-50;
+  Operands op;
+  CHT_TRY(alloc_operands(*A->pat, *B->pat, s, op));
+  if (b == 64)
+    CHT_TRY(split_operands<64>(A, B, s, op));
+  else
+    CHT_TRY(split_operands<32>(A, B, s, op));
+  const SplitProd d = make_prod(plan, op, Cvals);
+  if (b == 64) return launch_split<64>(d, nullptr, nullptr, plan->C->nnz, s);
+  return launch_split<32>(d, nullptr, nullptr, plan->C->nnz, s);
+}
+
+int split_batch_prepare(cht_batch *bt, cudaStream_t s) {
+  if (bt->nslices != 0 && bt->nslices != kSB) {
+    set_error("the split form uses %d slices (nslices = 0 or %d)", kSB, kSB);
+    return CHT_ERR_UNSUPPORTED;
+  }
+  auto sb = std::make_unique<SplitBatch>();
+  std::vector<SplitProd> host(bt->count);
+  sb->ops.resize(bt->count);
+  for (int32_t i = 0; i < bt->count; ++i) {
+    CHT_TRY(check_segments(bt->plans[i]));
+    CHT_TRY(alloc_operands(*bt->As[i]->pat, *bt->Bs[i]->pat, s, sb->ops[i]));
+    host[i] = make_prod(bt->plans[i], sb->ops[i], bt->views[i]->view_vals);
+    sb->maxb = std::max(sb->maxb, static_cast<int>(bt->plans[i]->b));
+  }
+  CHT_TRY(sb->prods.alloc(bt->count, s));
+  CHT_CUDA_TRY(cudaMemcpyAsync(sb->prods.p, host.data(), sizeof(SplitProd) * bt->count,
+                               cudaMemcpyHostToDevice, s));
+  CHT_CUDA_TRY(cudaStreamSynchronize(s));
+  bt->split_state = sb.release();
+  return CHT_OK;
+}
+
+int split_batch_run(cht_batch *bt, cudaStream_t s) {
+  auto *sb = static_cast<SplitBatch *>(bt->split_state);
+  for (int32_t i = 0; i < bt->count; ++i) {
+    if (bt->plans[i]->b == 64)
+      CHT_TRY(split_operands<64>(bt->As[i], bt->Bs[i], s, sb->ops[i]));
+    else
+      CHT_TRY(split_operands<32>(bt->As[i], bt->Bs[i], s, sb->ops[i]));
+  }
+  const SplitProd none{};
+  if (sb->maxb == 64) return launch_split<64>(none, sb->prods.p, bt->units.p, bt->nunits, s);
+  return launch_split<32>(none, sb->prods.p, bt->units.p, bt->nunits, s);
+}
+
+void split_batch_release(cht_batch *bt) {
+  delete static_cast<SplitBatch *>(bt->split_state);
+  bt->split_state = nullptr;
 }
 
 }  // namespace cht

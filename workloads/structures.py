@@ -147,7 +147,10 @@ def locality_pattern(points: np.ndarray, b: int, cutoff: float):
     step = max(1, (1 << 22) // (b * b))
     for s in range(0, ci.shape[0], step):
         pi, pj = grp[ci[s:s + step]], grp[cj[s:s + step]]
-        d2 = ((pi[:, :, None, :] - pj[:, None, :, :]) ** 2).sum(axis=3)
+        c = pi.mean(axis=1, keepdims=True)
+        pi, pj = pi - c, pj - c
+        d2 = ((pi * pi).sum(axis=2)[:, :, None] + (pj * pj).sum(axis=2)[:, None, :]
+              - 2.0 * np.matmul(pi, pj.transpose(0, 2, 1)))
         keep[s:s + step] = d2.reshape(d2.shape[0], -1).min(axis=1) < c2
     ci, cj = ci[keep], cj[keep]
     rows = np.concatenate([ci, cj[ci != cj]])
@@ -155,23 +158,44 @@ def locality_pattern(points: np.ndarray, b: int, cutoff: float):
     return _rowmajor(rows, cols, g)
 
 
+def locality_decay(points: np.ndarray, b: int, pattern) -> np.ndarray:
+    """exp(-0.5 |x_p - x_q|) for every element (p, q) of the given leaves,
+    float64 [nblk, b, b] (distances from the expansion |u|^2 + |v|^2 - 2 u.v
+    of the points centred on the row group's mean)."""
+    brow, bcol = pattern
+    npts = points.shape[0]
+    grp = points.reshape(npts // b, b, 3)
+    out = np.empty((brow.shape[0], b, b), dtype=np.float64)
+    step = max(1, (1 << 22) // (b * b))
+    for s in range(0, brow.shape[0], step):
+        pi, pj = grp[brow[s:s + step]], grp[bcol[s:s + step]]
+        c = pi.mean(axis=1, keepdims=True)
+        pi, pj = pi - c, pj - c
+        d2 = ((pi * pi).sum(axis=2)[:, :, None] + (pj * pj).sum(axis=2)[:, None, :]
+              - 2.0 * np.matmul(pi, pj.transpose(0, 2, 1)))
+        np.maximum(d2, 0.0, out=d2)
+        np.sqrt(d2, out=d2)
+        d2 *= -0.5
+        np.exp(d2, out=out[s:s + step])
+    return out
+
+
 def locality_matrix(points: np.ndarray, b: int, cutoff: float,
-                    seed: int, pattern=None) -> BlockMatrix:
+                    seed: int, pattern=None, decay=None) -> BlockMatrix:
     """3D-locality matrix: entry (p, q) of a stored leaf is
-    exp(-0.5 |x_p - x_q|) * U[-1, 1]."""
+    exp(-0.5 |x_p - x_q|) * U[-1, 1] (``decay`` may be precomputed with
+    locality_decay on the same pattern and shared between matrices)."""
     npts = points.shape[0]
     if pattern is None:
         pattern = locality_pattern(points, b, cutoff)
     brow, bcol = pattern
     rng = np.random.default_rng(seed)
     vals = _uniform_leaves(rng, brow.shape[0], b)
-    grp = points.reshape(npts // b, b, 3)
-    step = max(1, (1 << 21) // (b * b))
-    for s in range(0, brow.shape[0], step):
-        pi, pj = grp[brow[s:s + step]], grp[bcol[s:s + step]]
-        r = np.sqrt(((pi[:, :, None, :] - pj[:, None, :, :]) ** 2).sum(axis=3))
-        vals[s:s + step] *= np.exp(-0.5 * r)
-    return BlockMatrix(npts, b, brow, bcol, vals)
+    if decay is None:
+        decay = locality_decay(points, b, pattern)
+    vals *= decay
+    _ = npts
+    return BlockMatrix(points.shape[0], b, brow, bcol, vals)
 
 
 # --------------------------------------------------------------------------
@@ -240,8 +264,9 @@ def config2(n: int = 65536, b: int = 64, cutoff: float = 6.0):
     """3D locality x 3D locality on one shared jittered lattice."""
     pts = lattice_points(n, SEED_GEOM + 2)
     pat = locality_pattern(pts, b, cutoff)
-    return (locality_matrix(pts, b, cutoff, SEED_A + 2, pattern=pat),
-            locality_matrix(pts, b, cutoff, SEED_B + 2, pattern=pat))
+    dec = locality_decay(pts, b, pat)
+    return (locality_matrix(pts, b, cutoff, SEED_A + 2, pattern=pat, decay=dec),
+            locality_matrix(pts, b, cutoff, SEED_B + 2, pattern=pat, decay=dec))
 
 
 def config3(n: int = 32768, b: int = 32, p: float = 0.01):
@@ -287,8 +312,9 @@ def batched_products(count: int = 64, n_min: int = 2048, n_max: int = 32768,
         elif kind == "locality":
             pts = lattice_points(n, SEED_GEOM + 4 + 10 * i)
             pat = locality_pattern(pts, 64, 6.0)
-            a = _split_leaves(locality_matrix(pts, 64, 6.0, sa, pattern=pat), 32)
-            bm = _split_leaves(locality_matrix(pts, 64, 6.0, sb, pattern=pat), 32)
+            dec = locality_decay(pts, 64, pat)
+            a = _split_leaves(locality_matrix(pts, 64, 6.0, sa, pattern=pat, decay=dec), 32)
+            bm = _split_leaves(locality_matrix(pts, 64, 6.0, sb, pattern=pat, decay=dec), 32)
         else:
             a = random_blocks(n, 32, 0.02, sa)
             bm = random_blocks(n, 32, 0.02, sb)
