@@ -448,17 +448,18 @@ def section_batched(args, world, cht, torch):
             bt.run()
         ms = _time_steps(torch, torch.cuda.current_stream(), g.replay, args.steps, args.warmup)
         cht.sync_status()
-        results[name] = [bt.output(i).values() for i in range(bt.count)]
+        results[name] = [(tuned.leaf_sizes[i], bt.output(i).values()) for i in range(bt.count)]
         out[name] = {"value": native_flops * world / (ms * 1e-3) / 1e12, "unit": UNIT,
                      "ms_per_step": ms, "leaf_sizes": {"32": tuned.leaf_sizes.count(32),
                                                        "64": tuned.leaf_sizes.count(64)},
                      "schedule": tuned.schedule, "launches_per_step": "1 graph replay",
                      "graph": True}
         out[name]["_keep"] = (tuned, g)
-    num = sum(float(torch.linalg.norm((x - y).reshape(-1))) ** 2
-              for x, y in zip(results["split"], results["fp64"])) ** 0.5
-    den = sum(float(torch.linalg.norm(y.reshape(-1))) ** 2 for y in results["fp64"]) ** 0.5
-    out["split"]["rel_fro_err_vs_fp64"] = num / den
+    same = [(x, y) for (bx, x), (by, y) in zip(results["split"], results["fp64"]) if bx == by]
+    num = sum(float(torch.linalg.norm((x - y).reshape(-1))) ** 2 for x, y in same) ** 0.5
+    den = sum(float(torch.linalg.norm(y.reshape(-1))) ** 2 for _, y in same) ** 0.5
+    out["split"]["rel_fro_err_vs_fp64"] = num / den if den else None
+    out["split"]["products_compared"] = len(same)
     for k in ("fp64", "split"):
         out[k].pop("_keep")
     return out

@@ -405,18 +405,33 @@ template <int MAXB>
 struct KCfg;
 template <>
 struct KCfg<64> {
-  static constexpr int STAGES = 2, STAGE = Smem<64>::STAGE, XBUF = Smem<64>::XBUF;
+  static constexpr int STAGES = 2, STAGE = Smem<64>::STAGE, XBUF = Smem<64>::XBUF, NXB = 1;
   static constexpr int TMEM_COLS = 512;
 };
 template <>
 struct KCfg<32> {
-  static constexpr int STAGES = 3, STAGE = Smem<32>::STAGE, XBUF = Smem<32>::XBUF;
+  static constexpr int STAGES = 3, STAGE = Smem<32>::STAGE, XBUF = Smem<32>::XBUF, NXB = 2;
   static constexpr int TMEM_COLS = 256;
 };
+
+// One entry of the per-CTA unit queue: a C leaf and everything the MMA and
+// epilogue warps need about it, staged in shared memory by the producer.
+constexpr int kQueue = 4;
+constexpr int16_t kNoExp16 = -32768;
+struct alignas(16) Slot {
+  double *C;          // the C leaf's values
+  int32_t np;         // its leaf pairs
+  int32_t b;          // leaf size (0 = no more units)
+  int32_t u;          // position in this CTA's unit sequence
+  int32_t pad;
+  int16_t rexp[64];   // exponents of the leaf's rows of A (kNoExp16: none)
+  int16_t cexp[64];   // exponents of the leaf's columns of B
+};
+
 template <int MAXB>
 constexpr size_t kernel_smem() {
-  return static_cast<size_t>(KCfg<MAXB>::STAGES) * KCfg<MAXB>::STAGE + KCfg<MAXB>::XBUF + 256 +
-         1024;
+  return static_cast<size_t>(KCfg<MAXB>::STAGES) * KCfg<MAXB>::STAGE +
+         KCfg<MAXB>::NXB * KCfg<MAXB>::XBUF + kQueue * sizeof(Slot) + 256 + 1024;
 }
 
 // Per-CTA control block (pointers into shared memory).
@@ -424,13 +439,20 @@ struct Ctl {
   uint8_t *stage_base;
   int stage_bytes;
   int64_t *xbuf;
-  uint64_t *full, *empty, *acc_full, *acc_empty, *drain, *ep_bar;
+  int xbuf_bytes;
+  Slot *queue;
+  uint64_t *full, *empty, *acc_full, *acc_empty, *drain, *ep_bar, *qfull, *qempty;
   volatile int *abort_flag;
   uint32_t tmem;
   int64_t wait_ns;
 };
 
-// Producer: the pairs of C leaf o into the stage ring.
+__device__ inline int16_t exp16(int e) {
+  return e == kNoExp ? kNoExp16 : static_cast<int16_t>(max(-32000, min(32000, e)));
+}
+
+// Producer warp: take the next unit, stage its metadata in queue slot n % kQueue
+// (all 32 lanes), then stream its pairs into the stage ring (lane 0).
 template <int B, int S>
 __device__ bool produce_unit(const SplitProd &d, int64_t o, uint32_t &k, const Ctl &c) {
   using SM = Smem<B>;
@@ -448,15 +470,13 @@ __device__ bool produce_unit(const SplitProd &d, int64_t o, uint32_t &k, const C
   return true;
 }
 
-// MMA issuer: all slice-product blocks of C leaf o, window by window.
+// MMA issuer: all slice-product blocks of one C leaf, window by window.
 template <int B, int S>
-__device__ bool mma_unit(const SplitProd &d, int64_t o, uint32_t &k, uint32_t &win,
-                         const Ctl &c) {
+__device__ bool mma_unit(int64_t np, uint32_t &k, uint32_t &win, const Ctl &c) {
   using CF = Cfg<B>;
   using SM = Smem<B>;
   constexpr int N = CF::N;
   constexpr uint32_t IDESC = make_idesc(128, N);
-  const int64_t p0 = d.cseg[o], np = d.cseg[o + 1] - p0;
   bool fresh[kRegions];
 #pragma unroll
   for (int t = 0; t < kRegions; ++t) fresh[t] = true;
@@ -496,10 +516,10 @@ __device__ bool mma_unit(const SplitProd &d, int64_t o, uint32_t &k, uint32_t &w
 }
 
 // Epilogue (one of 8 warps): exact windows into int64, final recombination
-// and the FP64 store of C leaf o.
+// and the FP64 store of one C leaf.  `xb` is this unit's exchange buffer.
 template <int B>
-__device__ bool epi_unit(const SplitProd &d, int64_t o, uint32_t &win, uint32_t &epb,
-                         const Ctl &c, int *status) {
+__device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *xb,
+                         const Ctl &c) {
   using CF = Cfg<B>;
   constexpr int N = CF::N, PARTS = CF::PARTS, WINDOW = CF::WINDOW;
   constexpr int E = N / 2;  // columns per epilogue thread
@@ -510,14 +530,7 @@ __device__ bool epi_unit(const SplitProd &d, int64_t o, uint32_t &win, uint32_t 
   const int row = (B == 64) ? ((q & 1) * 32 + lane) : lane;
   const int c0 = half * E;
   const uint32_t lane_base = c.tmem + (static_cast<uint32_t>(32 * q) << 16);
-  auto ep_sync = [&]() -> bool {  // bounded barrier among the 8 epilogue warps
-    __syncwarp();
-    if (lane == 0) mbar_arrive(c.ep_bar);
-    const bool r = wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag);
-    ++epb;
-    return r;
-  };
-  const int64_t np = d.cseg[o + 1] - d.cseg[o];
+  const int64_t np = sl.np;
   long long Q[E];
 #pragma unroll
   for (int cc = 0; cc < E; ++cc) Q[cc] = 0;
@@ -560,43 +573,47 @@ __device__ bool epi_unit(const SplitProd &d, int64_t o, uint32_t &win, uint32_t 
       const int sh = kW * part;
 #pragma unroll
       for (int cc = 0; cc < E; ++cc)
-        c.xbuf[(static_cast<int64_t>(part - 1) * B + row) * B + c0 + cc] = static_cast<long long>(
+        xb[(static_cast<int64_t>(part - 1) * B + row) * B + c0 + cc] = static_cast<long long>(
             (part_value(cc) + (static_cast<__int128>(1) << (sh - 1))) >> sh);
     }
-    if (!ep_sync()) return false;
+    // bounded barrier among the 8 epilogue warps: the parts are in xb
+    __syncwarp();
+    if (lane == 0) mbar_arrive(c.ep_bar);
+    if (!wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag)) return false;
+    ++epb;
     if (part == 0) {
-      const int er = d.row_exp[static_cast<int64_t>(d.crow[o]) * B + row];
-      const int64_t colbase = static_cast<int64_t>(d.ccol[o]) * B;
-      double *dst = d.C + o * B * B + static_cast<int64_t>(row) * B + c0;
+      const int er = sl.rexp[row];
+      double *dst = sl.C + static_cast<int64_t>(row) * B + c0;
 #pragma unroll
       for (int cc = 0; cc < E; cc += 2) {
         __int128 t0 = part_value(cc), t1 = part_value(cc + 1);
 #pragma unroll
         for (int p = 1; p < PARTS; ++p) {
-          t0 += c.xbuf[(static_cast<int64_t>(p - 1) * B + row) * B + c0 + cc];
-          t1 += c.xbuf[(static_cast<int64_t>(p - 1) * B + row) * B + c0 + cc + 1];
+          t0 += xb[(static_cast<int64_t>(p - 1) * B + row) * B + c0 + cc];
+          t1 += xb[(static_cast<int64_t>(p - 1) * B + row) * B + c0 + cc + 1];
         }
-        const int f0 = d.col_exp[colbase + c0 + cc], f1 = d.col_exp[colbase + c0 + cc + 1];
-        const bool z0 = er == kNoExp || f0 == kNoExp, z1 = er == kNoExp || f1 == kNoExp;
+        const int f0 = sl.cexp[c0 + cc], f1 = sl.cexp[c0 + cc + 1];
+        const bool z0 = er == kNoExp16 || f0 == kNoExp16, z1 = er == kNoExp16 || f1 == kNoExp16;
         double2 out;
         out.x = z0 ? 0.0 : scaled_i128_to_double(t0, er + f0 - 56);
         out.y = z1 ? 0.0 : scaled_i128_to_double(t1, er + f1 - 56);
         *reinterpret_cast<double2 *>(dst + cc) = out;
       }
     }
-    if (!ep_sync()) return false;
   }
-  (void)status;
   return true;
 }
 
-// The persistent split kernel.  Units are dealt round-robin to the CTAs:
-// with `prods` NULL the units are the C leaves 0..nunits-1 of `single`;
-// otherwise unit u is product units[u] >> 32, C leaf units[u] & 0xffffffff.
+// The persistent split kernel.  Units come from a device counter in order
+// (neighbouring C leaves, in Morton order within a product, run together and
+// share A and B slices through L2): with `prods` NULL unit u is C leaf u of
+// `single`; otherwise product units[u] >> 32, C leaf units[u] & 0xffffffff.
+// `next_unit` (8 bytes, zero at launch) is the unit counter.
 template <int MAXB>
 __global__ void __launch_bounds__(kThreads, 1)
     k_split_gemm(const SplitProd single, const SplitProd *__restrict__ prods,
-                 const int64_t *__restrict__ units, int64_t nunits, int *__restrict__ status,
+                 const int64_t *__restrict__ units, int64_t nunits,
+                 unsigned long long *__restrict__ next_unit, int *__restrict__ status,
                  int64_t wait_ns) {
   using KC = KCfg<MAXB>;
   constexpr int S = KC::STAGES;
@@ -604,14 +621,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   // 1024-byte aligned base for the swizzled tiles
   const uint32_t raw_addr = smem_addr(smem_raw);
   uint8_t *smem = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * KC::STAGE + KC::XBUF);
   Ctl c;
   c.stage_base = smem;
   c.stage_bytes = KC::STAGE;
   c.xbuf = reinterpret_cast<int64_t *>(smem + S * KC::STAGE);
+  c.xbuf_bytes = KC::XBUF;
+  c.queue = reinterpret_cast<Slot *>(smem + S * KC::STAGE + KC::NXB * KC::XBUF);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(c.queue + kQueue);
   c.full = bars;
   c.empty = bars + S;
-  c.acc_full = bars + 2 * S;
+  c.qfull = bars + 2 * S;
+  c.qempty = c.qfull + kQueue;
+  c.acc_full = c.qempty + kQueue;
   c.acc_empty = c.acc_full + 1;
   c.drain = c.acc_full + 2;
   c.ep_bar = c.acc_full + 3;
@@ -624,6 +645,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int st = 0; st < S; ++st) {
       mbar_init(&c.full[st], 1);
       mbar_init(&c.empty[st], 1);
+    }
+    for (int i = 0; i < kQueue; ++i) {
+      mbar_init(&c.qfull[i], 1);
+      mbar_init(&c.qempty[i], 1 + kEpiWarps);  // the MMA thread and 8 epilogue warps
     }
     mbar_init(c.acc_full, 1);
     mbar_init(c.acc_empty, kEpiWarps);
@@ -642,48 +667,89 @@ __global__ void __launch_bounds__(kThreads, 1)
     atomicOr(status, DEV_STATUS_TIMEOUT);
     *c.abort_flag = 1;
   };
-  auto unit = [&](int64_t u, int64_t &o) -> SplitProd {
-    if (!prods) {
-      o = u;
-      return single;
-    }
-    const int64_t packed = units[u];
-    o = packed & 0xffffffffLL;
-    return prods[packed >> 32];
-  };
 
   if (warp == 0) {
-    if (lane == 0) {
-      uint32_t k = 0;  // pairs issued
-      for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-        int64_t o;
-        const SplitProd d = unit(u, o);
-        bool ok;
-        if constexpr (MAXB == 64)
-          ok = d.b == 64 ? produce_unit<64, S>(d, o, k, c) : produce_unit<32, S>(d, o, k, c);
-        else
-          ok = produce_unit<32, S>(d, o, k, c);
-        if (!ok) {
-          fail();
-          break;
-        }
+    // ------------------------------------------------------- producer --
+    uint32_t k = 0;  // pairs issued (lane 0)
+    for (uint32_t n = 0;; ++n) {
+      const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
+      unsigned long long u = 0;
+      if (lane == 0) u = atomicAdd(next_unit, 1ULL);
+      u = __shfl_sync(0xffffffffu, u, 0);
+      bool ok = wait_or_abort(&c.qempty[qs], qph ^ 1u, c.wait_ns, c.abort_flag);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) {
+        if (lane == 0) fail();
+        break;
       }
+      Slot &sl = c.queue[qs];
+      if (u >= static_cast<unsigned long long>(nunits)) {
+        if (lane == 0) {
+          sl.b = 0;
+          mbar_arrive(&c.qfull[qs]);
+        }
+        break;
+      }
+      int64_t o;
+      SplitProd d;
+      if (!prods) {
+        o = static_cast<int64_t>(u);
+        d = single;
+      } else {
+        const int64_t packed = units[u];
+        o = packed & 0xffffffffLL;
+        d = prods[packed >> 32];
+      }
+      const int b = d.b;
+      const int32_t crow = d.crow[o], ccol = d.ccol[o];
+      for (int r = lane; r < b; r += 32) {
+        sl.rexp[r] = exp16(d.row_exp[static_cast<int64_t>(crow) * b + r]);
+        sl.cexp[r] = exp16(d.col_exp[static_cast<int64_t>(ccol) * b + r]);
+      }
+      if (lane == 0) {
+        sl.C = d.C + o * b * b;
+        sl.np = static_cast<int32_t>(d.cseg[o + 1] - d.cseg[o]);
+        sl.b = b;
+        sl.u = static_cast<int32_t>(n);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&c.qfull[qs]);
+      bool pok = true;
+      if (lane == 0) {
+        if constexpr (MAXB == 64)
+          pok = b == 64 ? produce_unit<64, S>(d, o, k, c) : produce_unit<32, S>(d, o, k, c);
+        else
+          pok = produce_unit<32, S>(d, o, k, c);
+        if (!pok) fail();
+      }
+      pok = __shfl_sync(0xffffffffu, pok ? 1 : 0, 0) != 0;
+      if (!pok) break;
+    }
+    if (lane == 0) {
       // copies in flight must land before shared memory goes away (after a
       // normal run these phases completed long ago)
       for (uint32_t j = (k >= S ? k - S : 0); j < k; ++j)
         mbar_wait_bounded(&c.full[j % S], (j / S) & 1u, kDrainNs);
     }
   } else if (warp == 1) {
+    // ------------------------------------------------------ MMA issuer --
     if (lane == 0) {
       uint32_t k = 0, win = 0;
-      for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-        int64_t o;
-        const SplitProd d = unit(u, o);
+      for (uint32_t n = 0;; ++n) {
+        const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
+        if (!wait_or_abort(&c.qfull[qs], qph, c.wait_ns, c.abort_flag)) {
+          fail();
+          break;
+        }
+        const int b = c.queue[qs].b;
+        const int64_t np = c.queue[qs].np;
+        if (b == 0) break;
+        mbar_arrive(&c.qempty[qs]);
         bool ok;
         if constexpr (MAXB == 64)
-          ok = d.b == 64 ? mma_unit<64, S>(d, o, k, win, c) : mma_unit<32, S>(d, o, k, win, c);
+          ok = b == 64 ? mma_unit<64, S>(np, k, win, c) : mma_unit<32, S>(np, k, win, c);
         else
-          ok = mma_unit<32, S>(d, o, k, win, c);
+          ok = mma_unit<32, S>(np, k, win, c);
         if (!ok) {
           fail();
           break;
@@ -694,20 +760,39 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait_bounded(c.drain, 0, kDrainNs);
     }
   } else {
+    // -------------------------------------------------------- epilogue --
     uint32_t win = 0, epb = 0;
-    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-      int64_t o;
-      const SplitProd d = unit(u, o);
+    for (uint32_t n = 0;; ++n) {
+      const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
+      if (!wait_or_abort(&c.qfull[qs], qph, c.wait_ns, c.abort_flag)) {
+        fail();
+        break;
+      }
+      const Slot &sl = c.queue[qs];
+      const int b = sl.b;
+      if (b == 0) break;
+      int64_t *xb = c.xbuf + (KC::NXB == 2 ? (n & 1u) * (KC::XBUF / 8) : 0);
       bool ok;
       if constexpr (MAXB == 64)
-        ok = d.b == 64 ? epi_unit<64>(d, o, win, epb, c, status)
-                       : epi_unit<32>(d, o, win, epb, c, status);
+        ok = b == 64 ? epi_unit<64>(sl, win, epb, xb, c) : epi_unit<32>(sl, win, epb, xb, c);
       else
-        ok = epi_unit<32>(d, o, win, epb, c, status);
+        ok = epi_unit<32>(sl, win, epb, xb, c);
       if (!ok) {
         fail();
         break;
       }
+      if constexpr (KC::NXB == 1) {
+        // one exchange buffer: part 0 must have read it before the next unit
+        __syncwarp();
+        if (lane == 0) mbar_arrive(c.ep_bar);
+        if (!wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag)) {
+          fail();
+          break;
+        }
+        ++epb;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&c.qempty[qs]);  // done with the slot
     }
   }
 
@@ -791,8 +876,9 @@ SplitProd make_prod(const cht_plan *plan, const Operands &op, double *Cvals) {
 
 template <int MAXB>
 int launch_split(const SplitProd &single, const SplitProd *prods, const int64_t *units,
-                 int64_t nunits, cudaStream_t s) {
+                 int64_t nunits, unsigned long long *counter, cudaStream_t s) {
   if (nunits <= 0) return CHT_OK;
+  CHT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
   int *status = nullptr;
   CHT_TRY(device_status_ptr(&status));
   int sms = 0;
@@ -802,8 +888,8 @@ int launch_split(const SplitProd &single, const SplitProd *prods, const int64_t 
   CHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem)));
   const int64_t grid = std::min<int64_t>(nunits, sms);
-  kern<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(single, prods, units, nunits, status,
-                                                          g_opt.wait_budget_ns);
+  kern<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(single, prods, units, nunits, counter,
+                                                          status, g_opt.wait_budget_ns);
   return launched("split_gemm");
 }
 
@@ -821,6 +907,7 @@ int check_segments(const cht_plan *plan) {
 struct SplitBatch {
   std::vector<Operands> ops;
   DevArray<SplitProd> prods;
+  DevArray<unsigned long long> counter;
   int maxb = 32;
 };
 
@@ -848,8 +935,10 @@ int split_multiply(cht_plan *plan, cht_mat *A, cht_mat *B, int nslices, cudaStre
   else
     CHT_TRY(split_operands<32>(A, B, s, op));
   const SplitProd d = make_prod(plan, op, Cvals);
-  if (b == 64) return launch_split<64>(d, nullptr, nullptr, plan->C->nnz, s);
-  return launch_split<32>(d, nullptr, nullptr, plan->C->nnz, s);
+  DevArray<unsigned long long> counter;
+  CHT_TRY(counter.alloc(1, s));
+  if (b == 64) return launch_split<64>(d, nullptr, nullptr, plan->C->nnz, counter.p, s);
+  return launch_split<32>(d, nullptr, nullptr, plan->C->nnz, counter.p, s);
 }
 
 int split_batch_prepare(cht_batch *bt, cudaStream_t s) {
@@ -867,6 +956,7 @@ int split_batch_prepare(cht_batch *bt, cudaStream_t s) {
     sb->maxb = std::max(sb->maxb, static_cast<int>(bt->plans[i]->b));
   }
   CHT_TRY(sb->prods.alloc(bt->count, s));
+  CHT_TRY(sb->counter.alloc(1, s));
   CHT_CUDA_TRY(cudaMemcpyAsync(sb->prods.p, host.data(), sizeof(SplitProd) * bt->count,
                                cudaMemcpyHostToDevice, s));
   CHT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -883,8 +973,9 @@ int split_batch_run(cht_batch *bt, cudaStream_t s) {
       CHT_TRY(split_operands<32>(bt->As[i], bt->Bs[i], s, sb->ops[i]));
   }
   const SplitProd none{};
-  if (sb->maxb == 64) return launch_split<64>(none, sb->prods.p, bt->units.p, bt->nunits, s);
-  return launch_split<32>(none, sb->prods.p, bt->units.p, bt->nunits, s);
+  if (sb->maxb == 64)
+    return launch_split<64>(none, sb->prods.p, bt->units.p, bt->nunits, sb->counter.p, s);
+  return launch_split<32>(none, sb->prods.p, bt->units.p, bt->nunits, sb->counter.p, s);
 }
 
 void split_batch_release(cht_batch *bt) {
