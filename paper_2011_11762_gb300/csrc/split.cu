@@ -82,7 +82,8 @@ struct Smem {
   static constexpr int A_BYTES = Cfg<B>::SA * TILE;
   static constexpr int B_BYTES = kSB * TILE;
   static constexpr int STAGE = A_BYTES + B_BYTES;
-  static constexpr int XBUF = (Cfg<B>::PARTS - 1) * B * B * 8;
+  // exchange buffer: b = 64 hands part 1 to part 0; b = 32 gathers all 4 parts
+  static constexpr int XBUF = (B == 64 ? 1 : Cfg<B>::PARTS) * B * B * 8;
   static constexpr int TOTAL = Cfg<B>::STAGES * STAGE + XBUF + 256;
   static constexpr size_t DYN = TOTAL + 1024;  // + alignment slack
 };
@@ -410,7 +411,7 @@ struct KCfg<64> {
 };
 template <>
 struct KCfg<32> {
-  static constexpr int STAGES = 3, STAGE = Smem<32>::STAGE, XBUF = Smem<32>::XBUF, NXB = 2;
+  static constexpr int STAGES = 2, STAGE = Smem<32>::STAGE, XBUF = Smem<32>::XBUF, NXB = 2;
   static constexpr int TMEM_COLS = 256;
 };
 
@@ -449,25 +450,6 @@ struct Ctl {
 
 __device__ inline int16_t exp16(int e) {
   return e == kNoExp ? kNoExp16 : static_cast<int16_t>(max(-32000, min(32000, e)));
-}
-
-// Producer warp: take the next unit, stage its metadata in queue slot n % kQueue
-// (all 32 lanes), then stream its pairs into the stage ring (lane 0).
-template <int B, int S>
-__device__ bool produce_unit(const SplitProd &d, int64_t o, uint32_t &k, const Ctl &c) {
-  using SM = Smem<B>;
-  const int64_t p0 = d.cseg[o], p1 = d.cseg[o + 1];
-  for (int64_t p = p0; p < p1; ++p, ++k) {
-    const uint32_t st = k % S, ph = (k / S) & 1u;
-    if (!wait_or_abort(&c.empty[st], ph ^ 1u, c.wait_ns, c.abort_flag)) return false;
-    uint8_t *sa = c.stage_base + st * c.stage_bytes;
-    mbar_arrive_expect_tx(&c.full[st], SM::STAGE);
-    bulk_g2s(sa, d.a_slices + static_cast<int64_t>(d.pa[p]) * SM::A_BYTES, SM::A_BYTES,
-             &c.full[st]);
-    bulk_g2s(sa + SM::A_BYTES, d.b_slices + static_cast<int64_t>(d.pb[p]) * SM::B_BYTES,
-             SM::B_BYTES, &c.full[st]);
-  }
-  return true;
 }
 
 // MMA issuer: all slice-product blocks of one C leaf, window by window.
@@ -562,43 +544,63 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
     __syncwarp();
     if (lane == 0) mbar_arrive(c.acc_empty);
     if (!last) continue;
-    // part value in units of 2^-(8 (5 + part) + 16); parts > 0 are rounded
-    // to units of 2^-56 (the plan limits the window count so that they fit
-    // 64 bits) and handed to part 0 through shared memory
-    auto part_value = [&](int cc) -> __int128 {
-      return (static_cast<__int128>(Q[cc]) << 16) +
-             static_cast<__int128>(__float2ll_rn(rl[cc] * 65536.0f));
-    };
-    if (part > 0) {
+    // part value in units of 2^-(8 (5 + part) + 8) = 2^-48 after the shift
+    // by 8 * part (rounded); the plan limits the window count so that every
+    // part fits 64 bits
+    auto part_value = [&](int cc) -> long long {
+      const long long v = (Q[cc] << 8) + __float2ll_rn(rl[cc] * 256.0f);
+      if (part == 0) return v;
       const int sh = kW * part;
+      return (v + (1LL << (sh - 1))) >> sh;
+    };
+    if (B == 64) {
+      // part 1 hands its values to part 0, which converts and stores
+      if (part > 0) {
+#pragma unroll
+        for (int cc = 0; cc < E; ++cc) xb[row * B + c0 + cc] = part_value(cc);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(c.ep_bar);
+      if (!wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag)) return false;
+      ++epb;
+      if (part == 0) {
+        const int er = sl.rexp[row];
+        double *dst = sl.C + static_cast<int64_t>(row) * B + c0;
+#pragma unroll
+        for (int cc = 0; cc < E; cc += 2) {
+          const __int128 t0 = static_cast<__int128>(part_value(cc)) + xb[row * B + c0 + cc];
+          const __int128 t1 = static_cast<__int128>(part_value(cc + 1)) + xb[row * B + c0 + cc + 1];
+          const int f0 = sl.cexp[c0 + cc], f1 = sl.cexp[c0 + cc + 1];
+          double2 out;
+          out.x = (er == kNoExp16 || f0 == kNoExp16) ? 0.0 : scaled_i128_to_double(t0, er + f0 - 48);
+          out.y = (er == kNoExp16 || f1 == kNoExp16) ? 0.0 : scaled_i128_to_double(t1, er + f1 - 48);
+          *reinterpret_cast<double2 *>(dst + cc) = out;
+        }
+      }
+    } else {
+      // every part into the buffer, then all 256 threads convert 4 elements
 #pragma unroll
       for (int cc = 0; cc < E; ++cc)
-        xb[(static_cast<int64_t>(part - 1) * B + row) * B + c0 + cc] = static_cast<long long>(
-            (part_value(cc) + (static_cast<__int128>(1) << (sh - 1))) >> sh);
-    }
-    // bounded barrier among the 8 epilogue warps: the parts are in xb
-    __syncwarp();
-    if (lane == 0) mbar_arrive(c.ep_bar);
-    if (!wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag)) return false;
-    ++epb;
-    if (part == 0) {
-      const int er = sl.rexp[row];
-      double *dst = sl.C + static_cast<int64_t>(row) * B + c0;
+        xb[(static_cast<int64_t>(part) * B + row) * B + c0 + cc] = part_value(cc);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(c.ep_bar);
+      if (!wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag)) return false;
+      ++epb;
+      const int e0 = (threadIdx.x - 64) * 4;  // epilogue thread index * 4
+      const int r = e0 / B, col = e0 % B;
+      const int er = sl.rexp[r];
+      double o4[4];
 #pragma unroll
-      for (int cc = 0; cc < E; cc += 2) {
-        __int128 t0 = part_value(cc), t1 = part_value(cc + 1);
+      for (int j = 0; j < 4; ++j) {
+        __int128 t = 0;
 #pragma unroll
-        for (int p = 1; p < PARTS; ++p) {
-          t0 += xb[(static_cast<int64_t>(p - 1) * B + row) * B + c0 + cc];
-          t1 += xb[(static_cast<int64_t>(p - 1) * B + row) * B + c0 + cc + 1];
-        }
-        const int f0 = sl.cexp[c0 + cc], f1 = sl.cexp[c0 + cc + 1];
-        const bool z0 = er == kNoExp16 || f0 == kNoExp16, z1 = er == kNoExp16 || f1 == kNoExp16;
-        double2 out;
-        out.x = z0 ? 0.0 : scaled_i128_to_double(t0, er + f0 - 56);
-        out.y = z1 ? 0.0 : scaled_i128_to_double(t1, er + f1 - 56);
-        *reinterpret_cast<double2 *>(dst + cc) = out;
+        for (int p = 0; p < PARTS; ++p) t += xb[(static_cast<int64_t>(p) * B + r) * B + col + j];
+        const int f = sl.cexp[col + j];
+        o4[j] = (er == kNoExp16 || f == kNoExp16) ? 0.0 : scaled_i128_to_double(t, er + f - 48);
       }
+      double *dst = sl.C + static_cast<int64_t>(r) * B + col;
+      *reinterpret_cast<double2 *>(dst) = make_double2(o4[0], o4[1]);
+      *reinterpret_cast<double2 *>(dst + 2) = make_double2(o4[2], o4[3]);
     }
   }
   return true;
@@ -670,60 +672,92 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------- producer --
-    uint32_t k = 0;  // pairs issued (lane 0)
-    for (uint32_t n = 0;; ++n) {
-      const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
-      unsigned long long u = 0;
-      if (lane == 0) u = atomicAdd(next_unit, 1ULL);
-      u = __shfl_sync(0xffffffffu, u, 0);
-      bool ok = wait_or_abort(&c.qempty[qs], qph ^ 1u, c.wait_ns, c.abort_flag);
-      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      if (!ok) {
-        if (lane == 0) fail();
-        break;
-      }
-      Slot &sl = c.queue[qs];
-      if (u >= static_cast<unsigned long long>(nunits)) {
-        if (lane == 0) {
-          sl.b = 0;
-          mbar_arrive(&c.qfull[qs]);
+    // Units are taken kChunk at a time; lanes resolve their metadata, the
+    // line exponents and the pair indices in parallel, lane 0 issues copies.
+    constexpr int kChunk = 2;
+    uint32_t k = 0;  // pairs issued
+    uint32_t n = 0;  // queue position
+    bool done = false;
+    while (!done) {
+      unsigned long long u0 = 0;
+      if (lane == 0) u0 = atomicAdd(next_unit, static_cast<unsigned long long>(kChunk));
+      u0 = __shfl_sync(0xffffffffu, u0, 0);
+      int valid_l = 0;
+      long long o_l = 0;
+      int prod_l = 0;
+      if (lane < kChunk) {
+        const unsigned long long u = u0 + lane;
+        if (u < static_cast<unsigned long long>(nunits)) {
+          valid_l = 1;
+          const int64_t packed = prods ? units[u] : static_cast<int64_t>(u);
+          o_l = prods ? (packed & 0xffffffffLL) : packed;
+          prod_l = prods ? static_cast<int>(packed >> 32) : 0;
         }
-        break;
       }
-      int64_t o;
-      SplitProd d;
-      if (!prods) {
-        o = static_cast<int64_t>(u);
-        d = single;
-      } else {
-        const int64_t packed = units[u];
-        o = packed & 0xffffffffLL;
-        d = prods[packed >> 32];
+      for (int j = 0; j < kChunk && !done; ++j) {
+        const int valid = __shfl_sync(0xffffffffu, valid_l, j);
+        const int64_t o = __shfl_sync(0xffffffffu, o_l, j);
+        const int prod = __shfl_sync(0xffffffffu, prod_l, j);
+        const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
+        const bool ok = wait_or_abort(&c.qempty[qs], qph ^ 1u, c.wait_ns, c.abort_flag);
+        if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
+          if (lane == 0) fail();
+          done = true;
+          break;
+        }
+        Slot &sl = c.queue[qs];
+        if (!valid) {
+          if (lane == 0) {
+            sl.b = 0;
+            mbar_arrive(&c.qfull[qs]);
+          }
+          done = true;
+          break;
+        }
+        const SplitProd d = prods ? prods[prod] : single;
+        const int b = d.b;
+        const int64_t p0 = d.cseg[o], p1 = d.cseg[o + 1];
+        const int32_t crow = d.crow[o], ccol = d.ccol[o];
+        for (int r = lane; r < b; r += 32) {
+          sl.rexp[r] = exp16(d.row_exp[static_cast<int64_t>(crow) * b + r]);
+          sl.cexp[r] = exp16(d.col_exp[static_cast<int64_t>(ccol) * b + r]);
+        }
+        if (lane == 0) {
+          sl.C = d.C + o * b * b;
+          sl.np = static_cast<int32_t>(p1 - p0);
+          sl.b = b;
+          sl.u = static_cast<int32_t>(n);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&c.qfull[qs]);
+        ++n;
+        const int a_bytes = b == 64 ? Smem<64>::A_BYTES : Smem<32>::A_BYTES;
+        const int b_bytes = b == 64 ? Smem<64>::B_BYTES : Smem<32>::B_BYTES;
+        for (int64_t base = p0; base < p1 && !done; base += 32) {
+          const int64_t pl = base + lane;
+          const int32_t pa_l = pl < p1 ? d.pa[pl] : 0, pb_l = pl < p1 ? d.pb[pl] : 0;
+          const int cnt = static_cast<int>(p1 - base < 32 ? p1 - base : 32);
+          for (int i = 0; i < cnt; ++i, ++k) {
+            const uint32_t st = k % S, ph = (k / S) & 1u;
+            const bool w_ok = wait_or_abort(&c.empty[st], ph ^ 1u, c.wait_ns, c.abort_flag);
+            const int pa_i = __shfl_sync(0xffffffffu, pa_l, i);
+            const int pb_i = __shfl_sync(0xffffffffu, pb_l, i);
+            if (!__shfl_sync(0xffffffffu, w_ok ? 1 : 0, 0)) {
+              if (lane == 0) fail();
+              done = true;
+              break;
+            }
+            if (lane == 0) {
+              uint8_t *sa = c.stage_base + st * c.stage_bytes;
+              mbar_arrive_expect_tx(&c.full[st], static_cast<uint32_t>(a_bytes + b_bytes));
+              bulk_g2s(sa, d.a_slices + static_cast<int64_t>(pa_i) * a_bytes,
+                       static_cast<uint32_t>(a_bytes), &c.full[st]);
+              bulk_g2s(sa + a_bytes, d.b_slices + static_cast<int64_t>(pb_i) * b_bytes,
+                       static_cast<uint32_t>(b_bytes), &c.full[st]);
+            }
+          }
+        }
       }
-      const int b = d.b;
-      const int32_t crow = d.crow[o], ccol = d.ccol[o];
-      for (int r = lane; r < b; r += 32) {
-        sl.rexp[r] = exp16(d.row_exp[static_cast<int64_t>(crow) * b + r]);
-        sl.cexp[r] = exp16(d.col_exp[static_cast<int64_t>(ccol) * b + r]);
-      }
-      if (lane == 0) {
-        sl.C = d.C + o * b * b;
-        sl.np = static_cast<int32_t>(d.cseg[o + 1] - d.cseg[o]);
-        sl.b = b;
-        sl.u = static_cast<int32_t>(n);
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&c.qfull[qs]);
-      bool pok = true;
-      if (lane == 0) {
-        if constexpr (MAXB == 64)
-          pok = b == 64 ? produce_unit<64, S>(d, o, k, c) : produce_unit<32, S>(d, o, k, c);
-        else
-          pok = produce_unit<32, S>(d, o, k, c);
-        if (!pok) fail();
-      }
-      pok = __shfl_sync(0xffffffffu, pok ? 1 : 0, 0) != 0;
-      if (!pok) break;
     }
     if (lane == 0) {
       // copies in flight must land before shared memory goes away (after a
