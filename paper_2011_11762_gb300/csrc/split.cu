@@ -14,21 +14,22 @@
 //
 // Tensor-core mapping (one CTA per C leaf at a time; b = 64 shown, b = 32 in
 // brackets): the A operand of an MMA stacks 2 [4] consecutive slices of the
-// A leaf along M = 128, the B operand is one slice of the B leaf (N = b).
-// An MMA with first A slice u and B slice j lands in TMEM region t = u + j;
-// part p of the region (rows p*b .. p*b + b) then holds S_{t+p}.  Blocks with
-// the same t share the region, so a region holds whole diagonals.
+// A leaf along M = 128, the B operand puts 2 consecutive slices of the B leaf
+// side by side (N = 2b).  A block with first slices u, j (both odd) computes
+// A_{u+p} B_{j+q} for parts p (rows p*b ..) and column halves q (columns
+// q*b ..): diagonal u + j + p + q.  Blocks with equal u + j share TMEM region
+// r = (u + j - 2) / 2, so every quadrant of a region holds one diagonal.
 //
-// Exactness: regions 2..5 (diagonals 2..5 and their parts) carry the high
-// bits and must be exact.  An FP32 accumulator is exact while every partial
-// sum stays below 2^24, which holds for a window of 2 [8] leaf pairs:
-// 2 blocks * 64 * 2 * 255^2 < 2^24 [1 * 32 * 8 * 255^2 < 2^24].  After each
-// window the epilogue warps read these regions and add them, converted to
-// integers, into int64 accumulators; the next window restarts them.
-// Regions 6 and 7 (weight <= 2^-32 of the leading one) accumulate over the
-// whole C leaf in FP32 and are read once.  The final value
-//     T = sum_parts (2^16 Q_p + rnd(2^16 (R6 2^-8 + R7 2^-16))) 2^(-8p)
-// is an integer in units of 2^-56 and becomes a double by bit assembly; no
+// Exactness: regions r = 0, 1 (diagonals 2..5 and the parts above them)
+// carry the high bits and must be exact.  An FP32 accumulator is exact while
+// every partial sum stays below 2^24, which holds for a window of 2 [8] leaf
+// pairs: 2 blocks * 64 * 2 * 255^2 < 2^24 [1 * 32 * 8 * 255^2 < 2^24].  After
+// each window the epilogue warps read these regions and add them, converted
+// to integers, into int64 accumulators; the next window restarts them.
+// Region 2 (weight <= 2^-32 of the leading diagonal) accumulates over the
+// whole C leaf in FP32 and is read once.  The final value
+//     T = sum_parts (2^8 Q_p + rnd(2^8 (R6 2^-8 + R7 2^-16))) 2^(-8p)
+// is an integer in units of 2^-48 and becomes a double by bit assembly; no
 // FP64 arithmetic is used (FP64 is the slowest unit on GB300).
 //
 // Roles (320 threads): warp 0 = bulk-copy producer, warp 1 = TMEM owner and
@@ -49,8 +50,8 @@ namespace {
 
 constexpr int kW = 8;               // bits per digit
 constexpr int kSB = 6;              // B slices (and the split depth s)
-constexpr int kExactLast = 5;       // regions 2..5 are exact
-constexpr int kRegions = 6;         // regions t = 2..7
+constexpr int kRegions = 3;         // TMEM region r holds base diagonal t = 2 + 2r
+constexpr int kExactRegions = 2;    // regions with t = 2 and t = 4 are exact
 constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
 constexpr int64_t kDrainNs = 2000000000LL;
@@ -59,22 +60,23 @@ template <int B>
 struct Cfg;
 template <>
 struct Cfg<64> {
-  static constexpr int N = 64, PARTS = 2, SA = 6, KSTEPS = 4, STAGES = 2, WINDOW = 2;
-  static constexpr int NBLK = 12;
+  // N is the MMA width: two B slices side by side (2 b columns)
+  static constexpr int N = 128, PARTS = 2, SA = 6, KSTEPS = 4, STAGES = 2, WINDOW = 2;
+  static constexpr int NBLK = 6;
   static constexpr int TMEM_COLS = 512;
 };
 template <>
 struct Cfg<32> {
-  static constexpr int N = 32, PARTS = 4, SA = 8, KSTEPS = 2, STAGES = 3, WINDOW = 8;
-  static constexpr int NBLK = 8;
+  static constexpr int N = 64, PARTS = 4, SA = 8, KSTEPS = 2, STAGES = 3, WINDOW = 8;
+  static constexpr int NBLK = 4;
   static constexpr int TMEM_COLS = 256;
 };
 
-// MMA blocks (first stacked A slice u, B slice j), 1-based; region t = u + j.
-__constant__ int8_t c_blk64[12][2] = {{1, 1}, {1, 2}, {1, 3}, {3, 1}, {1, 4}, {3, 2},
-                                       {1, 5}, {3, 3}, {5, 1}, {1, 6}, {3, 4}, {5, 2}};
-__constant__ int8_t c_blk32[8][2] = {{1, 1}, {1, 2}, {1, 3}, {1, 4},
-                                      {1, 5}, {5, 1}, {1, 6}, {5, 2}};
+// MMA blocks (first stacked A slice u, first B slice j; both odd), 1-based.
+// Block (u, j) computes A_{u+p} B_{j+q} for every part p and q in {0, 1}
+// into TMEM region (u + j - 2) / 2.
+__constant__ int8_t c_blk64[6][2] = {{1, 1}, {1, 3}, {3, 1}, {1, 5}, {3, 3}, {5, 1}};
+__constant__ int8_t c_blk32[4][2] = {{1, 1}, {1, 3}, {1, 5}, {5, 1}};
 
 template <int B>
 struct Smem {
@@ -461,13 +463,13 @@ __device__ bool mma_unit(int64_t np, uint32_t &k, uint32_t &win, const Ctl &c) {
   constexpr uint32_t IDESC = make_idesc(128, N);
   bool fresh[kRegions];
 #pragma unroll
-  for (int t = 0; t < kRegions; ++t) fresh[t] = true;
+  for (int r = 0; r < kRegions; ++r) fresh[r] = true;
   for (int64_t w0 = 0; w0 < np; w0 += CF::WINDOW, ++win) {
     // the epilogue must have read the regions of the previous window
     if (!wait_or_abort(c.acc_empty, (win & 1u) ^ 1u, c.wait_ns, c.abort_flag)) return false;
     tc_fence_after();
 #pragma unroll
-    for (int t = 0; t <= kExactLast - 2; ++t) fresh[t] = true;
+    for (int r = 0; r < kExactRegions; ++r) fresh[r] = true;
     const int64_t w1 = min(np, w0 + CF::WINDOW);
     for (int64_t i = w0; i < w1; ++i, ++k) {
       const uint32_t st = k % S, ph = (k / S) & 1u;
@@ -479,16 +481,16 @@ __device__ bool mma_unit(int64_t np, uint32_t &k, uint32_t &win, const Ctl &c) {
       for (int bi = 0; bi < CF::NBLK; ++bi) {
         const int bu = (B == 64) ? c_blk64[bi][0] : c_blk32[bi][0];
         const int bj = (B == 64) ? c_blk64[bi][1] : c_blk32[bi][1];
-        const int t = bu + bj - 2;  // region index 0..5
+        const int r = (bu + bj - 2) >> 1;  // region 0..2
         const uint64_t ad = sw128_desc(sa + (bu - 1) * SM::TILE);
-        const uint64_t bd = sw128_desc(sb + (bj - 1) * SM::TILE);
-        const uint32_t dt = c.tmem + static_cast<uint32_t>(t * N);
+        const uint64_t bd = sw128_desc(sb + (bj - 1) * SM::TILE);  // slices j, j+1
+        const uint32_t dt = c.tmem + static_cast<uint32_t>(r * N);
 #pragma unroll
         for (int kk = 0; kk < CF::KSTEPS; ++kk) {
-          const uint32_t acc = (fresh[t] && kk == 0) ? 0u : 1u;
+          const uint32_t acc = (fresh[r] && kk == 0) ? 0u : 1u;
           tc_mma(dt, ad + 2 * kk, bd + 2 * kk, IDESC, acc);
         }
-        fresh[t] = false;
+        fresh[r] = false;
       }
       tc_commit(&c.empty[st]);  // frees the stage when these MMAs finish
     }
@@ -504,7 +506,7 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
                          const Ctl &c) {
   using CF = Cfg<B>;
   constexpr int N = CF::N, PARTS = CF::PARTS, WINDOW = CF::WINDOW;
-  constexpr int E = N / 2;  // columns per epilogue thread
+  constexpr int E = B / 2;  // columns of the C leaf per epilogue thread
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = warp & 3;                // TMEM lane quarter of this warp
   const int half = (warp >= 6) ? 1 : 0;  // which half of the columns
@@ -521,21 +523,26 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
     if (!wait_or_abort(c.acc_full, win & 1u, c.wait_ns, c.abort_flag)) return false;
     tc_fence_after();
     float v[E];
+    // exact regions r = 0, 1 (base diagonal t = 2 + 2r); column half qq of a
+    // region holds diagonal t + part + qq, weight 2^(8 (5 - t - qq)) in
+    // units of diagonal 5 + part
 #pragma unroll
-    for (int t = 0; t <= kExactLast - 2; ++t) {
-      tmem_ld<E>(lane_base + static_cast<uint32_t>(t * N + c0), v);
-      tc_wait_ld();
+    for (int r = 0; r < kExactRegions; ++r)
 #pragma unroll
-      for (int cc = 0; cc < E; ++cc)
-        Q[cc] += static_cast<long long>(__float2int_rn(v[cc])) << (kW * (kExactLast - 2 - t));
-    }
-    float rl[E];  // low regions, folded: R6 2^-8 + R7 2^-16
+      for (int qq = 0; qq < 2; ++qq) {
+        tmem_ld<E>(lane_base + static_cast<uint32_t>(r * N + qq * B + c0), v);
+        tc_wait_ld();
+        const int sh = kW * (3 - 2 * r - qq);
+#pragma unroll
+        for (int cc = 0; cc < E; ++cc) Q[cc] += static_cast<long long>(__float2int_rn(v[cc])) << sh;
+      }
+    float rl[E];  // low region (t = 6), folded: R6 2^-8 + R7 2^-16
     if (last) {
-      tmem_ld<E>(lane_base + static_cast<uint32_t>(4 * N + c0), v);
+      tmem_ld<E>(lane_base + static_cast<uint32_t>(2 * N + c0), v);
       tc_wait_ld();
 #pragma unroll
       for (int cc = 0; cc < E; ++cc) rl[cc] = v[cc] * 0x1p-8f;
-      tmem_ld<E>(lane_base + static_cast<uint32_t>(5 * N + c0), v);
+      tmem_ld<E>(lane_base + static_cast<uint32_t>(2 * N + B + c0), v);
       tc_wait_ld();
 #pragma unroll
       for (int cc = 0; cc < E; ++cc) rl[cc] = fmaf(v[cc], 0x1p-16f, rl[cc]);

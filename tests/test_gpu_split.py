@@ -25,14 +25,16 @@ S, W = 6, 8
 
 
 def _kernel_pairs(b):
-    """Slice pairs the kernel's MMA blocks compute (A slices stacked along M)."""
+    """Slice pairs the kernel's MMA blocks compute: block (u, j) stacks A
+    slices u.. along M and B slices j, j+1 along N."""
     if b == 64:
-        blocks = [(u, j) for u, js in ((1, 6), (3, 4), (5, 2)) for j in range(1, js + 1)]
+        blocks = [(1, 1), (1, 3), (3, 1), (1, 5), (3, 3), (5, 1)]
         parts, sa = 2, 6
     else:
-        blocks = [(u, j) for u, js in ((1, 6), (5, 2)) for j in range(1, js + 1)]
+        blocks = [(1, 1), (1, 3), (1, 5), (5, 1)]
         parts, sa = 4, 8
-    return sorted({(u + p, j) for u, j in blocks for p in range(parts)}), sa
+    return sorted({(u + p, j + q) for u, j in blocks for p in range(parts)
+                   for q in range(2)}), sa
 
 
 @pytest.fixture(scope="module")
