@@ -161,6 +161,27 @@ __device__ inline void tmem_ld<32>(uint32_t taddr, float (&v)[32]) { tmem_ld32(t
 template <>
 __device__ inline void tmem_ld<16>(uint32_t taddr, float (&v)[16]) { tmem_ld16(taddr, v); }
 
+// 32 lanes x 16 columns, raw 32-bit words (load / store).
+__device__ inline void tmem_ld16u(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ inline void tmem_st16u(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ inline void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
 // layout (rows of 128 bytes, 8-row groups 1024 bytes apart).
 __device__ inline uint64_t sw128_desc(uint32_t saddr) {
@@ -515,29 +536,58 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
   const int c0 = half * E;
   const uint32_t lane_base = c.tmem + (static_cast<uint32_t>(32 * q) << 16);
   const int64_t np = sl.np;
-  long long Q[E];
-#pragma unroll
-  for (int cc = 0; cc < E; ++cc) Q[cc] = 0;
+  // The int64 accumulators of the exact regions live in TMEM columns beyond
+  // the MMA regions (2 columns per element: low, high word), so that the
+  // exact regions can be copied to registers and released to the MMA at once.
+  const uint32_t qbase = lane_base + static_cast<uint32_t>(kRegions * N + half * 2 * E);
+  float rl[E];  // low region (t = 6), folded: R6 2^-8 + R7 2^-16
   for (int64_t w0 = 0; w0 < np; w0 += WINDOW, ++win) {
-    const bool last = w0 + WINDOW >= np;
+    const bool last = w0 + WINDOW >= np, first = w0 == 0;
     if (!wait_or_abort(c.acc_full, win & 1u, c.wait_ns, c.abort_flag)) return false;
     tc_fence_after();
-    float v[E];
     // exact regions r = 0, 1 (base diagonal t = 2 + 2r); column half qq of a
     // region holds diagonal t + part + qq, weight 2^(8 (5 - t - qq)) in
-    // units of diagonal 5 + part
+    // units of diagonal 5 + part: ex[2r + qq] is shifted by 8 (3 - 2r - qq)
+    float ex[4][E];
 #pragma unroll
     for (int r = 0; r < kExactRegions; ++r)
 #pragma unroll
-      for (int qq = 0; qq < 2; ++qq) {
-        tmem_ld<E>(lane_base + static_cast<uint32_t>(r * N + qq * B + c0), v);
-        tc_wait_ld();
-        const int sh = kW * (3 - 2 * r - qq);
+      for (int qq = 0; qq < 2; ++qq)
+        tmem_ld<E>(lane_base + static_cast<uint32_t>(r * N + qq * B + c0), ex[2 * r + qq]);
+    tc_wait_ld();
+    if (!last) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(c.acc_empty);  // the MMA may go on
+    }
 #pragma unroll
-        for (int cc = 0; cc < E; ++cc) Q[cc] += static_cast<long long>(__float2int_rn(v[cc])) << sh;
+    for (int ch = 0; ch < E / 8; ++ch) {
+      uint32_t qw[16];
+      if (first) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) qw[i] = 0;
+      } else {
+        tmem_ld16u(qbase + 16 * ch, qw);
+        tc_wait_ld();
       }
-    float rl[E];  // low region (t = 6), folded: R6 2^-8 + R7 2^-16
-    if (last) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int cc = ch * 8 + e;
+        long long qv = static_cast<long long>((static_cast<unsigned long long>(qw[2 * e + 1]) << 32) |
+                                              qw[2 * e]);
+        qv += (static_cast<long long>(__float2int_rn(ex[0][cc])) << 24) +
+              (static_cast<long long>(__float2int_rn(ex[1][cc])) << 16) +
+              (static_cast<long long>(__float2int_rn(ex[2][cc])) << 8) +
+              static_cast<long long>(__float2int_rn(ex[3][cc]));
+        qw[2 * e] = static_cast<uint32_t>(qv);
+        qw[2 * e + 1] = static_cast<uint32_t>(static_cast<unsigned long long>(qv) >> 32);
+      }
+      tmem_st16u(qbase + 16 * ch, qw);
+    }
+    tc_wait_st();
+    if (!last) continue;
+    {
+      float v[E];
       tmem_ld<E>(lane_base + static_cast<uint32_t>(2 * N + c0), v);
       tc_wait_ld();
 #pragma unroll
@@ -547,10 +597,20 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
 #pragma unroll
       for (int cc = 0; cc < E; ++cc) rl[cc] = fmaf(v[cc], 0x1p-16f, rl[cc]);
     }
+    long long Q[E];
+#pragma unroll
+    for (int ch = 0; ch < E / 8; ++ch) {
+      uint32_t qw[16];
+      tmem_ld16u(qbase + 16 * ch, qw);
+      tc_wait_ld();
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        Q[ch * 8 + e] = static_cast<long long>(
+            (static_cast<unsigned long long>(qw[2 * e + 1]) << 32) | qw[2 * e]);
+    }
     tc_fence_before();
     __syncwarp();
-    if (lane == 0) mbar_arrive(c.acc_empty);
-    if (!last) continue;
+    if (lane == 0) mbar_arrive(c.acc_empty);  // the next unit may overwrite TMEM
     // part value in units of 2^-(8 (5 + part) + 8) = 2^-48 after the shift
     // by 8 * part (rounded); the plan limits the window count so that every
     // part fits 64 bits
@@ -755,12 +815,23 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             if (lane == 0) {
-              uint8_t *sa = c.stage_base + st * c.stage_bytes;
               mbar_arrive_expect_tx(&c.full[st], static_cast<uint32_t>(a_bytes + b_bytes));
-              bulk_g2s(sa, d.a_slices + static_cast<int64_t>(pa_i) * a_bytes,
-                       static_cast<uint32_t>(a_bytes), &c.full[st]);
-              bulk_g2s(sa + a_bytes, d.b_slices + static_cast<int64_t>(pb_i) * b_bytes,
-                       static_cast<uint32_t>(b_bytes), &c.full[st]);
+            }
+            __syncwarp();
+            // one copy per slice tile, spread over the lanes (many copies in
+            // flight instead of two large ones)
+            {
+              uint8_t *sa = c.stage_base + st * c.stage_bytes;
+              const int tile = b * 128;
+              const int na = a_bytes / tile, nb = b_bytes / tile;
+              if (lane < na)
+                bulk_g2s(sa + lane * tile, d.a_slices + static_cast<int64_t>(pa_i) * a_bytes +
+                                               lane * tile,
+                         static_cast<uint32_t>(tile), &c.full[st]);
+              else if (lane < na + nb)
+                bulk_g2s(sa + a_bytes + (lane - na) * tile,
+                         d.b_slices + static_cast<int64_t>(pb_i) * b_bytes + (lane - na) * tile,
+                         static_cast<uint32_t>(tile), &c.full[st]);
             }
           }
         }
