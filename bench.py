@@ -348,17 +348,23 @@ def section_split(args, world, cht, torch):
 
         _time_steps(torch, stream, numeric_only, args.steps, 1)
         kms = statistics.mean(kern.ms()[1:])
-        nblk, N = (12, 64) if A.b == 64 else (8, 32)
-        slice_flops = plan.npairs * nblk * 2 * 128 * N * A.b
+        # MMA work: per pair, (6 | 4) blocks of M = 128, N = 2b, K = b
+        nblk = 6 if A.b == 64 else 4
+        slice_flops = plan.npairs * nblk * 2 * 128 * (2 * A.b) * A.b
+        prof = read_profile_traffic("split_gemm_3d_locality" if A.b == 64
+                                    else "split_gemm_random_b32")
+        traffic = (float(prof["dram_bytes_per_pair"]) * plan.npairs
+                   if prof and "dram_bytes_per_pair" in prof else None)
         entry = {
             "value": flops * world / (ms_split * 1e-3) / 1e12, "unit": UNIT,
             "ms_per_step": ms_split, "numeric_ms": kms, "pairs": plan.npairs,
             "rel_fro_err_vs_fp64": err, "a_priori_bound": bound,
-            "roofline": {"kernel": "k_split_gemm (tcgen05 kind::f16) + split kernels",
+            "roofline": {"kernel": "k_split_gemm (tcgen05 kind::f16), timed with its "
+                                   "exponent and slicing pre-kernels",
                          "bound": "tensor", "achieved": slice_flops / (kms * 1e-3) / 1e12,
                          "peak": peak_bf16, "unit": "TFLOP/s",
                          "frac": slice_flops / (kms * 1e-3) / 1e12 / peak_bf16,
-                         "traffic": None,
+                         "traffic": traffic,
                          "algorithmic_flops_per_launch": slice_flops,
                          "peak_source": "measured bf16 dense (burst)"},
         }
