@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=65536, help="3D-locality workload size")
-    ap.add_argument("--sections", default="split,backward,batched",
+    ap.add_argument("--sections", default="split,spamm,backward,batched",
                     help="extra sections (comma list; '' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -377,6 +377,52 @@ def section_split(args, world, cht, torch):
             entry["fp64_ms_per_step"] = ms64
         out[name] = entry
         cht.sync_status()
+    return out
+
+
+def section_spamm(args, world, cht, torch):
+    """Sparse approximate product on the 3D-locality workload: pairs whose
+    leaf-norm product is below tau are dropped in the symbolic phase (leaf
+    level of the SpAMM recursion).  Reported per tau: kept pairs, time of a
+    step (SpAMM symbolic + FP64 numeric), TFLOP/s of the kept work, the
+    error against the exact FP64 product and the a-priori bound."""
+    import workloads as w
+    stream = torch.cuda.current_stream()
+    a, b = w.config2(args.n)
+    A, B = cht.from_block_matrix(a), cht.from_block_matrix(b)
+    full = cht.cht_symbolic_multiply(A, B)
+    Cx, _ = cht.cht_multiply(full, A, B, sync=True)
+    xr, xc = (t.long() for t in Cx.coords())
+    G = a.n // a.b
+    xkey = xr * G + xc
+    xorder = torch.argsort(xkey)
+    xsorted = xkey[xorder]
+    xv = Cx.values()
+    na = torch.linalg.norm(A.values().reshape(A.nblocks, -1), dim=1)
+    nb = torch.linalg.norm(B.values().reshape(B.nblocks, -1), dim=1)
+    out = {"workload": f"3d_locality_N{args.n}_b{a.b}", "pairs_exact": full.npairs}
+    scale = float(na.max() * nb.max())
+    for rel in (1e-4, 1e-3, 1e-2):
+        tau = rel * scale
+        plan = cht.cht_symbolic_multiply_spamm(A, B, tau)
+        Cs, _ = cht.cht_multiply(plan, A, B, sync=True)
+        sr, sc = (t.long() for t in Cs.coords())
+        idx = xorder[torch.searchsorted(xsorted, sr * G + sc)]
+        diff = xv.clone()
+        diff[idx] -= Cs.values()
+        err = float(torch.linalg.norm(diff.reshape(-1)) / torch.linalg.norm(xv.reshape(-1)))
+
+        def step():
+            p = cht.cht_symbolic_multiply_spamm(A, B, tau)
+            cht.cht_multiply(p, A, B)
+
+        ms = _time_steps(torch, stream, step, max(1, args.steps // 2), min(args.warmup, 3))
+        out[f"tau_{rel:g}_of_max"] = {
+            "pairs_kept": plan.npairs, "kept_fraction": plan.npairs / full.npairs,
+            "ms_per_step": ms, "value": plan.useful_flops * world / (ms * 1e-3) / 1e12,
+            "unit": UNIT, "rel_fro_err_vs_exact": err,
+            "effective_exact_tflops": full.useful_flops * world / (ms * 1e-3) / 1e12}
+    cht.sync_status()
     return out
 
 

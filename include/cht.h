@@ -139,6 +139,21 @@ int cht_mat_free(cht_mat_t M);
 int cht_symbolic_multiply(cht_mat_t A, cht_mat_t B, void *stream,
                           cht_plan_t *out, int64_t *nnzb_C, int64_t *npairs);
 
+/* Sparse approximate symbolic multiply (paper, Section 2.2: "sparse
+ * approximate multiplication", for matrices with decay): as
+ * cht_symbolic_multiply, but a pair (A(I,K), B(K,J)) is kept only if
+ * ||A(I,K)||_F * ||B(K,J)||_F >= tau (FP64 Frobenius norms of the current
+ * leaf values).  This is the leaf-level form of the SpAMM recursion, which
+ * skips a quadrant product whenever the product of the quadrants' norms is
+ * below tau: an ancestor's norms bound its leaves', so the pairs the
+ * recursion keeps are exactly those passing the leaf test.  The numeric
+ * phase (either mode) runs unchanged on the plan.  C's pattern holds the
+ * leaves with at least one kept pair.  The dropped pairs bound the error:
+ * ||C - A*B||_F <= sum over dropped pairs of ||A(I,K)||_F ||B(K,J)||_F.
+ * tau = 0 keeps every pair.  Synchronises `stream` four times. */
+int cht_symbolic_multiply_spamm(cht_mat_t A, cht_mat_t B, double tau, void *stream,
+                                cht_plan_t *out, int64_t *nnzb_C, int64_t *npairs);
+
 /* Plan counts; any out-pointer may be NULL. */
 int cht_plan_info(cht_plan_t P, int64_t *nnzb_C, int64_t *npairs);
 

@@ -31,7 +31,7 @@ def build(mutant: int = 0, force: bool = False) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off",
-           "-fPIC", "-shared", f"-DORC_MUTANT={mutant}", src, "-o", tmp]
+           "-fPIC", "-shared", f"-DORC_MUTANT={mutant}", src, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out

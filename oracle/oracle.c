@@ -28,6 +28,7 @@
  */
 #include "oracle.h"
 
+#include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -231,6 +232,63 @@ int orc_multiply(const orc_mat *A, const orc_mat *B, orc_mat **C,
 #pragma omp parallel
 #pragma omp single
     m->root = mul(A->root, B->root, A->depth, A->b, &np, PAR_LEVELS);
+    if (npairs) *npairs = np;
+    *C = m;
+    return 0;
+}
+
+/* ---------------------------------------------------- sparse approximate -- */
+
+/* squared Frobenius norm of a subtree */
+static double fro2(const node *x, int lev, int bs) {
+    if (!x) return 0.0;
+    if (lev == 0) {
+        double s = 0.0;
+        for (size_t e = 0; e < (size_t)bs * bs; ++e) s += x->leaf[e] * x->leaf[e];
+        return s;
+    }
+    double s = 0.0;
+    for (int i = 0; i < 4; ++i) s += fro2(x->q[i], lev - 1, bs);
+    return s;
+}
+
+static node *mul_spamm(const node *a, const node *b, int lev, int bs, double tau,
+                       int64_t *npairs) {
+    if (!a || !b) return NULL;
+    if (sqrt(fro2(a, lev, bs)) * sqrt(fro2(b, lev, bs)) < tau) return NULL;
+    if (lev == 0) {
+        node *c = new_node();
+        c->leaf = (double *)xcalloc((size_t)bs * bs, sizeof(double));
+        leaf_mul(a->leaf, b->leaf, c->leaf, bs);
+        ++*npairs;
+        return c;
+    }
+    node *t[8];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+            for (int k = 0; k < 2; ++k)
+                t[2 * (2 * i + j) + k] =
+                    mul_spamm(a->q[2 * i + k], b->q[2 * k + j], lev - 1, bs, tau, npairs);
+    node *c = new_node();
+    int any = 0;
+    for (int ij = 0; ij < 4; ++ij) {
+        c->q[ij] = add(t[2 * ij], t[2 * ij + 1], lev - 1, bs);
+        any |= c->q[ij] != NULL;
+    }
+    if (!any) {
+        free(c);
+        return NULL;
+    }
+    return c;
+}
+
+int orc_multiply_spamm(const orc_mat *A, const orc_mat *B, double tau,
+                       orc_mat **C, int64_t *npairs) {
+    if (!A || !B || !C || !(tau >= 0.0)) return -1;
+    if (A->n != B->n || A->b != B->b) return -2;
+    orc_mat *m = new_mat(A->n, A->b);
+    int64_t np = 0;
+    m->root = mul_spamm(A->root, B->root, A->depth, A->b, tau, &np);
     if (npairs) *npairs = np;
     *C = m;
     return 0;

@@ -38,6 +38,12 @@ int orc_build(int64_t n, int32_t b, int64_t nblk, const int32_t *brow,
 int orc_multiply(const orc_mat *A, const orc_mat *B, orc_mat **C,
                  int64_t *npairs);
 
+/* Sparse approximate product (SpAMM): the multiply recursion in which a
+ * quadrant product is skipped (nil) whenever ||A_sub||_F * ||B_sub||_F < tau,
+ * tested at every level including the leaves.  tau = 0 is orc_multiply. */
+int orc_multiply_spamm(const orc_mat *A, const orc_mat *B, double tau,
+                       orc_mat **C, int64_t *npairs);
+
 /* Transpose (a new matrix). */
 int orc_transpose(const orc_mat *A, orc_mat **out);
 

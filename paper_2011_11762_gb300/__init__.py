@@ -210,6 +210,15 @@ def cht_symbolic_multiply(A: Matrix, B: Matrix, stream=None) -> Plan:
     return Plan(h, A, B)
 
 
+def cht_symbolic_multiply_spamm(A: Matrix, B: Matrix, tau: float, stream=None) -> Plan:
+    """Sparse approximate plan: pairs with ||A leaf|| ||B leaf|| < tau dropped."""
+    h = _VP()
+    _check(_lib.load().cht_symbolic_multiply_spamm(A.handle, B.handle, float(tau),
+                                                   _stream(stream), ctypes.byref(h), None,
+                                                   None), "cht_symbolic_multiply_spamm")
+    return Plan(h, A, B)
+
+
 def cht_multiply(plan: Plan, A: Matrix, B: Matrix, mode: int = CHT_FP64, nslices: int = 0,
                  out: Matrix | None = None, stream=None, sync: bool = False):
     """C = A*B on the plan's pattern.  Returns (C, err_bound or None); with

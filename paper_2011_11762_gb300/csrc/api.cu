@@ -13,7 +13,9 @@ namespace cht {
 int build_matrix(int64_t n, int32_t b, int64_t nblocks, const int32_t *d_brow,
                  const int32_t *d_bcol, const double *d_vals, cudaStream_t s, cht_mat **out);
 int densify(cht_mat *M, double *d_out, int64_t ld, cudaStream_t s);
-int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out);
+int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
+             const double *normA = nullptr, const double *normB = nullptr, double tau = 0.0);
+int leaf_norms(const double *vals, int64_t n, int b, double *out, cudaStream_t s);
 int backward_lists_from_plan(cht_plan &plan, const Pattern &A, const Pattern &B, cudaStream_t s);
 int backward_lists_recompute(const Pattern &A, const Pattern &B, const Pattern &dC,
                              cudaStream_t s, cht_plan &out);
@@ -285,6 +287,27 @@ int cht_symbolic_multiply(cht_mat_t A, cht_mat_t B, void *stream, cht_plan_t *ou
   CHT_TRY(check_pair(A, B));
   cht_plan *p = nullptr;
   CHT_TRY(symbolic(*A->pat, *B->pat, as_stream(stream), &p));
+  if (nnzb_C) *nnzb_C = p->C->nnz;
+  if (npairs) *npairs = p->npairs;
+  *out = p;
+  return CHT_OK;
+}
+
+int cht_symbolic_multiply_spamm(cht_mat_t A, cht_mat_t B, double tau, void *stream,
+                                cht_plan_t *out, int64_t *nnzb_C, int64_t *npairs) {
+  if (!out || !(tau >= 0.0)) {
+    set_error("null plan out-pointer or invalid threshold");
+    return CHT_ERR_INVALID;
+  }
+  CHT_TRY(check_pair(A, B));
+  cudaStream_t s = as_stream(stream);
+  DevArray<double> na, nb;
+  CHT_TRY(na.alloc(A->pat->nnz, s));
+  CHT_TRY(nb.alloc(B->pat->nnz, s));
+  CHT_TRY(leaf_norms(A->values(), A->pat->nnz, A->pat->b, na.p, s));
+  CHT_TRY(leaf_norms(B->values(), B->pat->nnz, B->pat->b, nb.p, s));
+  cht_plan *p = nullptr;
+  CHT_TRY(symbolic(*A->pat, *B->pat, s, &p, na.p, nb.p, tau));
   if (nnzb_C) *nnzb_C = p->C->nnz;
   if (npairs) *npairs = p->npairs;
   *out = p;

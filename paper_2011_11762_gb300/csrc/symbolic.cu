@@ -139,6 +139,45 @@ __global__ void k_gather2(const int32_t *__restrict__ sidx, int64_t P,
   }
 }
 
+// SpAMM filter: keep pair p iff |A leaf| * |B leaf| >= tau (Frobenius norms).
+__global__ void k_spamm_keep(const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
+                             int64_t P, const double *__restrict__ na,
+                             const double *__restrict__ nb, double tau,
+                             int32_t *__restrict__ keep) {
+  GRID_STRIDE(p, P) keep[p] = (na[pa[p]] * nb[pb[p]] >= tau) ? 1 : 0;
+}
+
+__global__ void k_compact_pairs(const int32_t *__restrict__ keep, const int64_t *__restrict__ pos,
+                                int64_t P, const uint64_t *__restrict__ key,
+                                const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
+                                uint64_t *__restrict__ ko, int32_t *__restrict__ ao,
+                                int32_t *__restrict__ bo, int32_t *__restrict__ io) {
+  GRID_STRIDE(p, P) {
+    if (!keep[p]) continue;
+    const int64_t q = pos[p];
+    ko[q] = key[p];
+    ao[q] = pa[p];
+    bo[q] = pb[p];
+    io[q] = static_cast<int32_t>(q);
+  }
+}
+
+// Frobenius norm of every leaf: one warp per leaf, fixed reduction order.
+__global__ void k_leaf_norms(const double *__restrict__ vals, int64_t n, int bb,
+                             double *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t l = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5; l < n;
+       l += warps) {
+    const double *v = vals + l * bb;
+    double s2 = 0.0;
+    for (int e = lane; e < bb; e += 32) s2 = fma(v[e], v[e], s2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0) out[l] = sqrt(s2);
+  }
+}
+
 __global__ void k_count_units(const int32_t *__restrict__ unit, int64_t P, int32_t *__restrict__ cnt) {
   GRID_STRIDE(p, P) atomicAdd(&cnt[unit[p]], 1);
 }
@@ -181,7 +220,8 @@ __global__ void k_compact3(const int32_t *__restrict__ keep, const int64_t *__re
 // outputs key[P] (sorted), pa[P], pb[P].  Synchronises once to read P.
 static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
                         DevArray<uint64_t> &skey, DevArray<int32_t> &pa, DevArray<int32_t> &pb,
-                        int64_t *P_out) {
+                        int64_t *P_out, const double *normA = nullptr,
+                        const double *normB = nullptr, double tau = 0.0) {
   const int L = A.L;
   DevArray<int32_t> cnt;
   DevArray<int64_t> off;
@@ -213,6 +253,34 @@ static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
                                                           B.rowptr.p, B.rowcol.p, B.rowleaf.p, L,
                                                           key.p, pa0.p, pb0.p, idx.p);
     CHT_TRY(launched("pair_fill"));
+  }
+  if (P > 0 && normA) {
+    // sparse approximate product: drop the pairs below the norm threshold
+    DevArray<int32_t> keep;
+    DevArray<int64_t> pos;
+    CHT_TRY(keep.alloc(P, s));
+    CHT_TRY(pos.alloc(P + 1, s));
+    k_spamm_keep<<<grid_for(P, 256), 256, 0, s>>>(pa0.p, pb0.p, P, normA, normB, tau, keep.p);
+    CHT_TRY(launched("spamm_keep"));
+    CHT_TRY(scan_exclusive(keep.p, pos.p, P, s));
+    int64_t Pk = 0;
+    CHT_TRY(read_i64(pos.p + P, &Pk, s));
+    DevArray<uint64_t> key2;
+    DevArray<int32_t> pa2, pb2, idx2;
+    CHT_TRY(key2.alloc(Pk, s));
+    CHT_TRY(pa2.alloc(Pk, s));
+    CHT_TRY(pb2.alloc(Pk, s));
+    CHT_TRY(idx2.alloc(Pk, s));
+    k_compact_pairs<<<grid_for(P, 256), 256, 0, s>>>(keep.p, pos.p, P, key.p, pa0.p, pb0.p,
+                                                     key2.p, pa2.p, pb2.p, idx2.p);
+    CHT_TRY(launched("compact_pairs"));
+    key = std::move(key2);
+    pa0 = std::move(pa2);
+    pb0 = std::move(pb2);
+    idx = std::move(idx2);
+    P = Pk;
+  }
+  if (P > 0) {
     CHT_TRY(radix_sort_pairs(key.p, idx.p, skey.p, sidx.p, P, 3 * L, s));
     k_pair_gather<<<grid_for(P, 256), 256, 0, s>>>(sidx.p, P, pa0.p, pb0.p, pa.p, pb.p);
     CHT_TRY(launched("pair_gather"));
@@ -237,7 +305,14 @@ int schedule_units(const int64_t *seg, int64_t n, int32_t *order, cudaStream_t s
   return radix_sort_pairs(key.p, idx.p, skey.p, order, n, 32, s);
 }
 
-int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out) {
+int leaf_norms(const double *vals, int64_t n, int b, double *out, cudaStream_t s) {
+  if (n <= 0) return CHT_OK;
+  k_leaf_norms<<<grid_for(n * 32, 256), 256, 0, s>>>(vals, n, b * b, out);
+  return launched("leaf_norms");
+}
+
+int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
+             const double *normA, const double *normB, double tau) {
   const int L = A.L;
   if (3 * L > 63) {
     set_error("leaf grid of %lld per side is too large for 64-bit pair keys", (long long)A.G);
@@ -255,7 +330,7 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out)
   DevArray<uint64_t> skey;
   DevArray<int32_t> pa, pb;
   int64_t P = 0;
-  CHT_TRY(make_triples(A, B, s, skey, pa, pb, &P));
+  CHT_TRY(make_triples(A, B, s, skey, pa, pb, &P, normA, normB, tau));
   plan->npairs = P;
 
   DevArray<int32_t> head;
