@@ -12,8 +12,8 @@ symbolic phase + FP64 numeric phase (one full product); inputs (4 GB) are
 resident in HBM and larger than L2.
 
 Further sections on their own workloads (each reported in the same JSON
-line): the split-precision form, the backward of L = ||A B - T||_F^2, and
-the batched form.
+line): the split-precision form, the sparse approximate product, the
+symmetric square, the backward of L = ||A B - T||_F^2, and the batched form.
 
 ``--impl reference`` times the CPU oracle (the plain recursive quadtree
 multiply) on a bounded sample of the same workload on the host cores.
@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=65536, help="3D-locality workload size")
-    ap.add_argument("--sections", default="split,spamm,backward,batched",
+    ap.add_argument("--sections", default="split,spamm,symsquare,backward,batched",
                     help="extra sections (comma list; '' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -422,6 +422,59 @@ def section_spamm(args, world, cht, torch):
             "ms_per_step": ms, "value": plan.useful_flops * world / (ms * 1e-3) / 1e12,
             "unit": UNIT, "rel_fro_err_vs_exact": err,
             "effective_exact_tflops": full.useful_flops * world / (ms * 1e-3) / 1e12}
+    cht.sync_status()
+    return out
+
+
+def section_symsquare(args, world, cht, torch):
+    """Symmetric square C = A^2 of the symmetric 3D-locality matrix
+    (A + A^T) / 2 (N = 65536, 64x64 leaves): the plan of the upper leaves
+    (I <= J) only, FP64 and split numeric phases, and the mirror that gives
+    the full C; against the full product A*A.  "effective" TFLOP/s divides
+    the full product's work by the time of the symmetric path."""
+    import workloads as w
+    stream = torch.cuda.current_stream()
+    a = w.config2_symmetric(args.n)
+    A = cht.from_block_matrix(a)
+    full = cht.cht_symbolic_multiply(A, A)
+    sym = cht.cht_symbolic_multiply_symsquare(A)
+    Cf, _ = cht.cht_multiply(full, A, A, sync=True)
+    U, _ = cht.cht_multiply(sym, A, A, sync=True)
+    M = cht.cht_mat_mirror_upper(U)
+    same_pattern = bool(M.nblocks == Cf.nblocks and all(
+        torch.equal(x, y) for x, y in zip(M.coords(), Cf.coords())))
+    err = float(torch.linalg.norm((M.values() - Cf.values()).reshape(-1))
+                / torch.linalg.norm(Cf.values().reshape(-1))) if same_pattern else None
+    del M, U, Cf
+    steps, warm = max(1, args.steps // 2), min(args.warmup, 3)
+    out = {"workload": f"symmetric_3d_locality_N{args.n}_b{a.b}",
+           "pairs_full": full.npairs, "pairs_upper": sym.npairs,
+           "mirror_equals_full_pattern": same_pattern, "mirror_rel_fro_err_vs_full": err}
+
+    def run_full():
+        p = cht.cht_symbolic_multiply(A, A)
+        cht.cht_multiply(p, A, A)
+
+    def run_sym(mode, mirror):
+        def f():
+            p = cht.cht_symbolic_multiply_symsquare(A)
+            u, _ = cht.cht_multiply(p, A, A, mode=mode)
+            if mirror:
+                cht.cht_mat_mirror_upper(u)
+        return f
+
+    ms_full = _time_steps(torch, stream, run_full, steps, warm)
+    out["full_fp64"] = {"ms_per_step": ms_full,
+                        "value": full.useful_flops * world / (ms_full * 1e-3) / 1e12,
+                        "unit": UNIT}
+    for name, mode, mirror in (("upper_fp64", cht.CHT_FP64, False),
+                               ("upper_fp64_plus_mirror", cht.CHT_FP64, True),
+                               ("upper_split", cht.CHT_SPLIT_BF16, False)):
+        ms = _time_steps(torch, stream, run_sym(mode, mirror), steps, warm)
+        out[name] = {"ms_per_step": ms,
+                     "value": sym.useful_flops * world / (ms * 1e-3) / 1e12, "unit": UNIT,
+                     "effective_full_tflops": full.useful_flops * world / (ms * 1e-3) / 1e12,
+                     "speedup_vs_full_fp64": ms_full / ms}
     cht.sync_status()
     return out
 

@@ -154,6 +154,22 @@ int cht_symbolic_multiply(cht_mat_t A, cht_mat_t B, void *stream,
 int cht_symbolic_multiply_spamm(cht_mat_t A, cht_mat_t B, double tau, void *stream,
                                 cht_plan_t *out, int64_t *nnzb_C, int64_t *npairs);
 
+/* Symmetric square (paper, Section 2.2: "symmetric matrix square"): the plan
+ * of C = A*A for a symmetric A (A = A^T; not checked) restricted to the
+ * upper triangle, the C leaves (I, J) with I <= J -- C is symmetric, so they
+ * determine it, at about half the work.  Run the numeric phase with
+ * cht_multiply(plan, A, A, ...); cht_mat_mirror_upper then gives the full C.
+ * Synchronises `stream` four times. */
+int cht_symbolic_multiply_symsquare(cht_mat_t A, void *stream, cht_plan_t *out,
+                                    int64_t *nnzb_C, int64_t *npairs);
+
+/* The full symmetric matrix whose upper-triangle leaves (I <= J) are those of
+ * U: leaf (J, I) of the result is leaf (I, J) of U transposed.  Every leaf
+ * of U is kept, all-zero or not.  U must hold no leaf below the diagonal
+ * (CHT_ERR_INVALID otherwise, nothing created).  Synchronises `stream`
+ * twice. */
+int cht_mat_mirror_upper(cht_mat_t U, void *stream, cht_mat_t *out);
+
 /* Plan counts; any out-pointer may be NULL. */
 int cht_plan_info(cht_plan_t P, int64_t *nnzb_C, int64_t *npairs);
 

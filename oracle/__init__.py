@@ -39,6 +39,7 @@ def load(mutant: int = 0):
                               _I32P, _I32P, _F64P, ctypes.POINTER(_VP)]
     lib.orc_multiply.argtypes = [_VP, _VP, ctypes.POINTER(_VP), _I64P]
     lib.orc_multiply_spamm.argtypes = [_VP, _VP, ctypes.c_double, ctypes.POINTER(_VP), _I64P]
+    lib.orc_multiply_upper.argtypes = [_VP, _VP, ctypes.POINTER(_VP), _I64P]
     lib.orc_transpose.argtypes = [_VP, ctypes.POINTER(_VP)]
     lib.orc_restrict.argtypes = [_VP, _VP, ctypes.POINTER(_VP)]
     lib.orc_backward.argtypes = [_VP, _VP, _VP, ctypes.POINTER(_VP),
@@ -120,6 +121,14 @@ class OMatrix:
         h = _VP()
         np_ = ctypes.c_int64(0)
         _check(self._lib.orc_multiply_spamm(self._h, other._h, float(tau), ctypes.byref(h),
+                                            ctypes.byref(np_)))
+        return OMatrix(h, self._lib), int(np_.value)
+
+    def multiply_upper(self, other: "OMatrix"):
+        """(C, npairs) for the leaves (I, J), I <= J, of self * other."""
+        h = _VP()
+        np_ = ctypes.c_int64(0)
+        _check(self._lib.orc_multiply_upper(self._h, other._h, ctypes.byref(h),
                                             ctypes.byref(np_)))
         return OMatrix(h, self._lib), int(np_.value)
 

@@ -294,6 +294,52 @@ int orc_multiply_spamm(const orc_mat *A, const orc_mat *B, double tau,
     return 0;
 }
 
+/* ------------------------------------------------------- upper triangle -- */
+
+/* The leaves (I, J), I <= J, of a*b for a node on the diagonal of C: the
+ * quadrants 11 and 22 are again on the diagonal, quadrant 12 lies wholly
+ * above it (every product), quadrant 21 wholly below it (skipped). */
+static node *mul_upper(const node *a, const node *b, int lev, int bs,
+                       int64_t *npairs) {
+    if (!a || !b) return NULL;
+    if (lev == 0) return mul(a, b, 0, bs, npairs, 0);
+    node *t[8] = {0};
+    for (int i = 0; i < 2; ++i)
+        for (int j = i; j < 2; ++j)
+            for (int k = 0; k < 2; ++k) {
+                const node *ak = a->q[2 * i + k], *bk = b->q[2 * k + j];
+#if ORC_MUTANT == 5
+                t[2 * (2 * i + j) + k] = mul_upper(ak, bk, lev - 1, bs, npairs);
+#else
+                t[2 * (2 * i + j) + k] = i == j ? mul_upper(ak, bk, lev - 1, bs, npairs)
+                                                : mul(ak, bk, lev - 1, bs, npairs, 0);
+#endif
+            }
+    node *c = new_node();
+    int any = 0;
+    for (int ij = 0; ij < 4; ++ij) {
+        c->q[ij] = add(t[2 * ij], t[2 * ij + 1], lev - 1, bs);
+        any |= c->q[ij] != NULL;
+    }
+    if (!any) {
+        free(c);
+        return NULL;
+    }
+    return c;
+}
+
+int orc_multiply_upper(const orc_mat *A, const orc_mat *B, orc_mat **C,
+                       int64_t *npairs) {
+    if (!A || !B || !C) return -1;
+    if (A->n != B->n || A->b != B->b) return -2;
+    orc_mat *m = new_mat(A->n, A->b);
+    int64_t np = 0;
+    m->root = mul_upper(A->root, B->root, A->depth, A->b, &np);
+    if (npairs) *npairs = np;
+    *C = m;
+    return 0;
+}
+
 /* ------------------------------------------------ transpose / restrict -- */
 
 static node *transpose_rec(const node *x, int lev, int bs) {

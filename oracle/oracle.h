@@ -44,6 +44,13 @@ int orc_multiply(const orc_mat *A, const orc_mat *B, orc_mat **C,
 int orc_multiply_spamm(const orc_mat *A, const orc_mat *B, double tau,
                        orc_mat **C, int64_t *npairs);
 
+/* The upper triangle of C = A*B: its leaves (I, J) with I <= J, by the
+ * multiply recursion in which a quadrant of C that lies wholly below the
+ * diagonal is not formed.  For symmetric A and B = A this is the symmetric
+ * square (paper, Section 2.2), whose lower leaves are the transposes. */
+int orc_multiply_upper(const orc_mat *A, const orc_mat *B, orc_mat **C,
+                       int64_t *npairs);
+
 /* Transpose (a new matrix). */
 int orc_transpose(const orc_mat *A, orc_mat **out);
 

@@ -219,6 +219,24 @@ def cht_symbolic_multiply_spamm(A: Matrix, B: Matrix, tau: float, stream=None) -
     return Plan(h, A, B)
 
 
+def cht_symbolic_multiply_symsquare(A: Matrix, stream=None) -> Plan:
+    """Plan of the upper triangle (leaf rows <= leaf columns) of A*A for a
+    symmetric A; multiply with cht_multiply(plan, A, A)."""
+    h = _VP()
+    _check(_lib.load().cht_symbolic_multiply_symsquare(A.handle, _stream(stream),
+                                                       ctypes.byref(h), None, None),
+           "cht_symbolic_multiply_symsquare")
+    return Plan(h, A, A)
+
+
+def cht_mat_mirror_upper(U: Matrix, stream=None) -> Matrix:
+    """The full symmetric matrix from its upper-triangle leaves."""
+    h = _VP()
+    _check(_lib.load().cht_mat_mirror_upper(U.handle, _stream(stream), ctypes.byref(h)),
+           "cht_mat_mirror_upper")
+    return Matrix(h)
+
+
 def cht_multiply(plan: Plan, A: Matrix, B: Matrix, mode: int = CHT_FP64, nslices: int = 0,
                  out: Matrix | None = None, stream=None, sync: bool = False):
     """C = A*B on the plan's pattern.  Returns (C, err_bound or None); with

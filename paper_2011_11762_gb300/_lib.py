@@ -27,6 +27,8 @@ SIGNATURES = {
     "cht_symbolic_multiply": (ctypes.c_int, [_VP, _VP, _VP, _PVP, _PI64, _PI64]),
     "cht_symbolic_multiply_spamm": (ctypes.c_int, [_VP, _VP, ctypes.c_double, _VP, _PVP,
                                                    _PI64, _PI64]),
+    "cht_symbolic_multiply_symsquare": (ctypes.c_int, [_VP, _VP, _PVP, _PI64, _PI64]),
+    "cht_mat_mirror_upper": (ctypes.c_int, [_VP, _VP, _PVP]),
     "cht_plan_info": (ctypes.c_int, [_VP, _PI64, _PI64]),
     "cht_plan_arrays": (ctypes.c_int, [_VP, _PVP, _PVP, _PVP, _PVP, _PVP, _PVP]),
     "cht_plan_free": (ctypes.c_int, [_VP]),

@@ -11,10 +11,13 @@ namespace cht {
 
 // Implemented in the other translation units.
 int build_matrix(int64_t n, int32_t b, int64_t nblocks, const int32_t *d_brow,
-                 const int32_t *d_bcol, const double *d_vals, cudaStream_t s, cht_mat **out);
+                 const int32_t *d_bcol, const double *d_vals, cudaStream_t s, cht_mat **out,
+                 bool drop_zero);
+int mirror_upper(cht_mat *U, cudaStream_t s, cht_mat **out);
 int densify(cht_mat *M, double *d_out, int64_t ld, cudaStream_t s);
 int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
-             const double *normA = nullptr, const double *normB = nullptr, double tau = 0.0);
+             const double *normA = nullptr, const double *normB = nullptr, double tau = 0.0,
+             bool upper_only = false);
 int leaf_norms(const double *vals, int64_t n, int b, double *out, cudaStream_t s);
 int backward_lists_from_plan(cht_plan &plan, const Pattern &A, const Pattern &B, cudaStream_t s);
 int backward_lists_recompute(const Pattern &A, const Pattern &B, const Pattern &dC,
@@ -223,7 +226,7 @@ int cht_mat_from_blocks(int64_t n, int32_t b, int64_t nblocks, const int32_t *d_
     return CHT_ERR_UNSUPPORTED;
   }
   cht_mat *m = nullptr;
-  CHT_TRY(build_matrix(n, b, nblocks, d_brow, d_bcol, d_vals, as_stream(stream), &m));
+  CHT_TRY(build_matrix(n, b, nblocks, d_brow, d_bcol, d_vals, as_stream(stream), &m, true));
   *out = m;
   return CHT_OK;
 }
@@ -311,6 +314,31 @@ int cht_symbolic_multiply_spamm(cht_mat_t A, cht_mat_t B, double tau, void *stre
   if (nnzb_C) *nnzb_C = p->C->nnz;
   if (npairs) *npairs = p->npairs;
   *out = p;
+  return CHT_OK;
+}
+
+int cht_symbolic_multiply_symsquare(cht_mat_t A, void *stream, cht_plan_t *out,
+                                    int64_t *nnzb_C, int64_t *npairs) {
+  if (!out || !A) {
+    set_error("null matrix or plan out-pointer");
+    return CHT_ERR_INVALID;
+  }
+  cht_plan *p = nullptr;
+  CHT_TRY(symbolic(*A->pat, *A->pat, as_stream(stream), &p, nullptr, nullptr, 0.0, true));
+  if (nnzb_C) *nnzb_C = p->C->nnz;
+  if (npairs) *npairs = p->npairs;
+  *out = p;
+  return CHT_OK;
+}
+
+int cht_mat_mirror_upper(cht_mat_t U, void *stream, cht_mat_t *out) {
+  if (!U || !out) {
+    set_error("null matrix or out-pointer");
+    return CHT_ERR_INVALID;
+  }
+  cht_mat *m = nullptr;
+  CHT_TRY(mirror_upper(U, as_stream(stream), &m));
+  *out = m;
   return CHT_OK;
 }
 

@@ -30,7 +30,7 @@ __global__ void k_make_keys(const int32_t *__restrict__ brow, const int32_t *__r
 // all-zero test of the leaf's values.
 __global__ void k_dup_and_zero(const uint64_t *__restrict__ skeys, const int32_t *__restrict__ sidx,
                                const double *__restrict__ vals, int64_t n, int bb,
-                               int32_t *__restrict__ keep, int *__restrict__ err) {
+                               int32_t *__restrict__ keep, int *__restrict__ err, bool drop_zero) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
   for (int64_t i = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5; i < n;
@@ -40,7 +40,7 @@ __global__ void k_dup_and_zero(const uint64_t *__restrict__ skeys, const int32_t
     bool nz = false;
     for (int e = lane; e < bb; e += 32) nz |= (v[e] != 0.0);
     nz = __any_sync(0xffffffffu, nz);
-    if (lane == 0) keep[i] = nz ? 1 : 0;
+    if (lane == 0) keep[i] = (nz || !drop_zero) ? 1 : 0;
   }
 }
 
@@ -160,9 +160,88 @@ int build_pattern_index(Pattern &p, cudaStream_t s) {
   return CHT_OK;
 }
 
-// Builds a matrix from a device leaf list; see cht_mat_from_blocks.
+// Lower-triangle mirror: leaf l (I <= J) is emitted as (I, J) and, off the
+// diagonal, also as (J, I) with transposed values; pos[l] = output slot.
+__global__ void k_mirror(const int32_t *__restrict__ brow, const int32_t *__restrict__ bcol,
+                         const double *__restrict__ vals, const int64_t *__restrict__ pos,
+                         int64_t n, int b, int32_t *__restrict__ orow, int32_t *__restrict__ ocol,
+                         double *__restrict__ ovals) {
+  const int bb = b * b;
+  for (int64_t l = blockIdx.x; l < n; l += gridDim.x) {
+    const int32_t I = brow[l], J = bcol[l];
+    const int64_t q = pos[l];
+    if (threadIdx.x == 0) {
+      orow[q] = I;
+      ocol[q] = J;
+      if (I != J) {
+        orow[q + 1] = J;
+        ocol[q + 1] = I;
+      }
+    }
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) {
+      const double v = vals[l * bb + e];
+      ovals[q * bb + e] = v;
+      if (I != J) ovals[(q + 1) * bb + (e % b) * b + e / b] = v;
+    }
+  }
+}
+
+__global__ void k_mirror_count(const int32_t *__restrict__ brow, const int32_t *__restrict__ bcol,
+                               int64_t n, int32_t *__restrict__ cnt, int *__restrict__ err) {
+  for (int64_t l = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; l < n;
+       l += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t I = brow[l], J = bcol[l];
+    if (I > J) atomicOr(err, 1);
+    cnt[l] = I == J ? 1 : (I < J ? 2 : 0);
+  }
+}
+
 int build_matrix(int64_t n, int32_t b, int64_t nblocks, const int32_t *d_brow,
-                 const int32_t *d_bcol, const double *d_vals, cudaStream_t s, cht_mat **out) {
+                 const int32_t *d_bcol, const double *d_vals, cudaStream_t s, cht_mat **out,
+                 bool drop_zero);
+
+// The full symmetric matrix whose upper triangle (I <= J) U holds.
+int mirror_upper(cht_mat *U, cudaStream_t s, cht_mat **out) {
+  const Pattern &p = *U->pat;
+  const int64_t n = p.nnz;
+  DevArray<int32_t> cnt, orow, ocol;
+  DevArray<int64_t> pos;
+  DevArray<double> ovals;
+  DevArray<int> err;
+  CHT_TRY(cnt.alloc(n, s));
+  CHT_TRY(pos.alloc(n + 1, s));
+  CHT_TRY(err.alloc(1, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+  if (n > 0) {
+    k_mirror_count<<<grid_for(n, 256), 256, 0, s>>>(p.brow.p, p.bcol.p, n, cnt.p, err.p);
+    CHT_TRY(launched("mirror_count"));
+  }
+  CHT_TRY(scan_exclusive(cnt.p, pos.p, n, s));
+  int64_t total = 0;
+  int herr = 0;
+  CHT_CUDA_TRY(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CHT_CUDA_TRY(cudaMemcpyAsync(&total, pos.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CHT_CUDA_TRY(cudaStreamSynchronize(s));
+  if (herr) {
+    set_error("mirror of an upper triangle: a leaf lies below the diagonal");
+    return CHT_ERR_INVALID;
+  }
+  CHT_TRY(orow.alloc(total, s));
+  CHT_TRY(ocol.alloc(total, s));
+  CHT_TRY(ovals.alloc(static_cast<size_t>(total) * p.b * p.b, s));
+  if (n > 0) {
+    k_mirror<<<grid_for(n, 1), 256, 0, s>>>(p.brow.p, p.bcol.p, U->values(), pos.p, n, p.b,
+                                            orow.p, ocol.p, ovals.p);
+    CHT_TRY(launched("mirror"));
+  }
+  return build_matrix(p.n, p.b, total, orow.p, ocol.p, ovals.p, s, out, false);
+}
+
+// Builds a matrix from a device leaf list; see cht_mat_from_blocks.  With
+// drop_zero false every given leaf is stored, all-zero or not.
+int build_matrix(int64_t n, int32_t b, int64_t nblocks, const int32_t *d_brow,
+                 const int32_t *d_bcol, const double *d_vals, cudaStream_t s, cht_mat **out,
+                 bool drop_zero) {
   auto pat = std::make_shared<Pattern>();
   pat->n = n;
   pat->b = b;
@@ -189,7 +268,7 @@ int build_matrix(int64_t n, int32_t b, int64_t nblocks, const int32_t *d_brow,
     CHT_TRY(launched("make_keys"));
     CHT_TRY(radix_sort_pairs(keys.p, idx.p, skeys.p, sidx.p, nblocks, 2 * pat->L, s));
     k_dup_and_zero<<<grid_for(nblocks * 32, 256), 256, 0, s>>>(skeys.p, sidx.p, d_vals, nblocks,
-                                                               bb, keep.p, err.p);
+                                                               bb, keep.p, err.p, drop_zero);
     CHT_TRY(launched("dup_and_zero"));
   }
   CHT_TRY(scan_exclusive(keep.p, pos.p, nblocks, s));

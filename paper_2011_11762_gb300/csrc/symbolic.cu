@@ -162,6 +162,15 @@ __global__ void k_compact_pairs(const int32_t *__restrict__ keep, const int64_t 
   }
 }
 
+// Symmetric-square filter: keep pair p iff its C leaf (I, J) has I <= J.
+__global__ void k_upper_keep(const uint64_t *__restrict__ key, int64_t P, int L,
+                             int32_t *__restrict__ keep) {
+  GRID_STRIDE(p, P) {
+    const uint64_t m = key[p] >> L;
+    keep[p] = morton_row(m) <= morton_col(m) ? 1 : 0;
+  }
+}
+
 // Frobenius norm of every leaf: one warp per leaf, fixed reduction order.
 __global__ void k_leaf_norms(const double *__restrict__ vals, int64_t n, int bb,
                              double *__restrict__ out) {
@@ -221,7 +230,8 @@ __global__ void k_compact3(const int32_t *__restrict__ keep, const int64_t *__re
 static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
                         DevArray<uint64_t> &skey, DevArray<int32_t> &pa, DevArray<int32_t> &pb,
                         int64_t *P_out, const double *normA = nullptr,
-                        const double *normB = nullptr, double tau = 0.0) {
+                        const double *normB = nullptr, double tau = 0.0,
+                        bool upper_only = false) {
   const int L = A.L;
   DevArray<int32_t> cnt;
   DevArray<int64_t> off;
@@ -254,14 +264,20 @@ static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
                                                           key.p, pa0.p, pb0.p, idx.p);
     CHT_TRY(launched("pair_fill"));
   }
-  if (P > 0 && normA) {
-    // sparse approximate product: drop the pairs below the norm threshold
+  if (P > 0 && (normA || upper_only)) {
+    // sparse approximate product: drop the pairs below the norm threshold;
+    // symmetric square: drop the pairs of C leaves below the diagonal
     DevArray<int32_t> keep;
     DevArray<int64_t> pos;
     CHT_TRY(keep.alloc(P, s));
     CHT_TRY(pos.alloc(P + 1, s));
-    k_spamm_keep<<<grid_for(P, 256), 256, 0, s>>>(pa0.p, pb0.p, P, normA, normB, tau, keep.p);
-    CHT_TRY(launched("spamm_keep"));
+    if (normA) {
+      k_spamm_keep<<<grid_for(P, 256), 256, 0, s>>>(pa0.p, pb0.p, P, normA, normB, tau, keep.p);
+      CHT_TRY(launched("spamm_keep"));
+    } else {
+      k_upper_keep<<<grid_for(P, 256), 256, 0, s>>>(key.p, P, L, keep.p);
+      CHT_TRY(launched("upper_keep"));
+    }
     CHT_TRY(scan_exclusive(keep.p, pos.p, P, s));
     int64_t Pk = 0;
     CHT_TRY(read_i64(pos.p + P, &Pk, s));
@@ -312,7 +328,7 @@ int leaf_norms(const double *vals, int64_t n, int b, double *out, cudaStream_t s
 }
 
 int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
-             const double *normA, const double *normB, double tau) {
+             const double *normA, const double *normB, double tau, bool upper_only) {
   const int L = A.L;
   if (3 * L > 63) {
     set_error("leaf grid of %lld per side is too large for 64-bit pair keys", (long long)A.G);
@@ -330,7 +346,7 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   DevArray<uint64_t> skey;
   DevArray<int32_t> pa, pb;
   int64_t P = 0;
-  CHT_TRY(make_triples(A, B, s, skey, pa, pb, &P, normA, normB, tau));
+  CHT_TRY(make_triples(A, B, s, skey, pa, pb, &P, normA, normB, tau, upper_only));
   plan->npairs = P;
 
   DevArray<int32_t> head;

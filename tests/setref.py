@@ -35,6 +35,22 @@ def pair_count(pa: set, pb: set) -> int:
     return sum(ca[k] * rb.get(k, 0) for k in ca)
 
 
+def upper_pair_count(pa: set, pb: set) -> int:
+    """The pairs (I, K) x (K, J) with I <= J: for every K, the rows I of
+    column K of pa against the columns J of row K of pb."""
+    rows, cols = defaultdict(list), defaultdict(list)
+    for i, k in pa:
+        rows[k].append(i)
+    for k, j in pb:
+        cols[k].append(j)
+    total = 0
+    for k, ri in rows.items():
+        cj = np.sort(np.asarray(cols.get(k, []), dtype=np.int64))
+        if cj.size:
+            total += int(np.sum(cj.size - np.searchsorted(cj, np.asarray(ri), side="left")))
+    return total
+
+
 def pairs_per_c_leaf(pa: set, pb: set) -> dict:
     """{(I, J): sorted list of K} for every contributing triple (I, K, J)."""
     by_row = defaultdict(list)

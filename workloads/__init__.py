@@ -29,6 +29,8 @@ from .structures import (  # noqa: F401
     random_blocks,
     values_on_pattern,
     reblock,
+    symmetrize,
+    config2_symmetric,
     batched_products,
     config1,
     config2,

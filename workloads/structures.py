@@ -250,6 +250,20 @@ def reblock(m: BlockMatrix, b_new: int) -> BlockMatrix:
                        (uniq % g_new).astype(np.int32), vals)
 
 
+def symmetrize(m: BlockMatrix) -> BlockMatrix:
+    """(M + M^T) / 2 on the union of M's leaf pattern and its transpose, in
+    row-major leaf order: a symmetric input for the symmetric square."""
+    g = m.grid
+    b = m.b
+    key = m.brow.astype(np.int64) * g + m.bcol.astype(np.int64)
+    tkey = m.bcol.astype(np.int64) * g + m.brow.astype(np.int64)
+    allk = np.unique(np.concatenate([key, tkey]))
+    vals = np.zeros((allk.shape[0], b, b), dtype=np.float64)
+    vals[np.searchsorted(allk, key)] += 0.5 * m.vals
+    vals[np.searchsorted(allk, tkey)] += 0.5 * np.transpose(m.vals, (0, 2, 1))
+    return BlockMatrix(m.n, b, (allk // g).astype(np.int32), (allk % g).astype(np.int32), vals)
+
+
 # --------------------------------------------------------------------------
 # The five workloads
 # --------------------------------------------------------------------------
@@ -267,6 +281,12 @@ def config2(n: int = 65536, b: int = 64, cutoff: float = 6.0):
     dec = locality_decay(pts, b, pat)
     return (locality_matrix(pts, b, cutoff, SEED_A + 2, pattern=pat, decay=dec),
             locality_matrix(pts, b, cutoff, SEED_B + 2, pattern=pat, decay=dec))
+
+
+def config2_symmetric(n: int = 65536, b: int = 64, cutoff: float = 6.0):
+    """The symmetric 3D-locality matrix (A + A^T) / 2 of workload 2, the
+    input of the symmetric square C = A^2."""
+    return symmetrize(config2(n, b, cutoff)[0])
 
 
 def config3(n: int = 32768, b: int = 32, p: float = 0.01):
