@@ -13,7 +13,8 @@ resident in HBM and larger than L2.
 
 Further sections on their own workloads (each reported in the same JSON
 line): the split-precision form, the sparse approximate product, the
-symmetric square, the backward of L = ||A B - T||_F^2, and the batched form.
+symmetric square, McWeeny purification steps (the second workload), the
+backward of L = ||A B - T||_F^2, and the batched form.
 
 ``--impl reference`` times the CPU oracle (the plain recursive quadtree
 multiply) on a bounded sample of the same workload on the host cores.
@@ -52,7 +53,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=65536, help="3D-locality workload size")
-    ap.add_argument("--sections", default="split,spamm,symsquare,backward,batched",
+    ap.add_argument("--sections", default="split,spamm,symsquare,purify,backward,batched",
                     help="extra sections (comma list; '' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -475,6 +476,57 @@ def section_symsquare(args, world, cht, torch):
                      "value": sym.useful_flops * world / (ms * 1e-3) / 1e12, "unit": UNIT,
                      "effective_full_tflops": full.useful_flops * world / (ms * 1e-3) / 1e12,
                      "speedup_vs_full_fp64": ms_full / ms}
+    cht.sync_status()
+    return out
+
+
+def section_purify(args, world, cht, torch):
+    """McWeeny purification step X <- 3X^2 - 2X^3 with truncation, the
+    second workload: X0 = (hi I - H) / (hi - lo) for the symmetric
+    3D-locality H of the symmetric-square section, [lo, hi] its Gershgorin
+    bounds.  One step = symmetric square, mirror, upper product X^2 X,
+    addition, truncation (Frobenius, eps = 1e-6 ||X||_F), mirror; all on the
+    GPU.  Reported per mode: time per step and the useful TFLOP/s of its two
+    products, for two steps from X0."""
+    import workloads as w
+    from paper_2011_11762_gb300 import purify
+    stream = torch.cuda.current_stream()
+    h = w.config2_symmetric(args.n)
+    lo, hi = w.gershgorin_bounds(h)
+    H = cht.from_block_matrix(h)
+    X0 = cht.cht_add_identity(-1.0 / (hi - lo), H, hi / (hi - lo))
+    del H
+    fro = float(torch.linalg.norm(X0.values().reshape(-1)))
+    eps = 1e-6 * fro
+    out = {"workload": f"mcweeny_symmetric_3d_locality_N{args.n}_b{h.b}",
+           "eps": eps, "leaves_X0": X0.nblocks}
+    for name, mode in (("fp64", cht.CHT_FP64), ("split", cht.CHT_SPLIT_BF16)):
+        X = X0
+        steps = []
+        for it in range(2):
+            start = torch.cuda.Event(enable_timing=True)
+            end = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            start.record(stream)
+            Xn, info = purify.mcweeny_step(X, eps, mode=mode)
+            end.record(stream)
+            torch.cuda.synchronize()
+            ms = start.elapsed_time(end)
+            steps.append({"ms": ms, "pairs": info["pairs"],
+                          "value": info["flops"] * world / (ms * 1e-3) / 1e12, "unit": UNIT,
+                          "leaves_upper_before_truncation": info["leaves_upper"],
+                          "leaves_upper_kept": info["leaves_upper_kept"],
+                          "removed_fro": info["removed"]})
+            X = Xn
+        if name == "fp64":
+            Xf = X
+        else:
+            num = torch.linalg.norm((X.values() - Xf.values()).reshape(-1)) \
+                if X.nblocks == Xf.nblocks else None
+            out["split_vs_fp64_rel_fro_after_2_steps"] = (
+                float(num / torch.linalg.norm(Xf.values().reshape(-1)))
+                if num is not None else "patterns differ")
+        out[name] = steps
     cht.sync_status()
     return out
 

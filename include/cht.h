@@ -163,12 +163,66 @@ int cht_symbolic_multiply_spamm(cht_mat_t A, cht_mat_t B, double tau, void *stre
 int cht_symbolic_multiply_symsquare(cht_mat_t A, void *stream, cht_plan_t *out,
                                     int64_t *nnzb_C, int64_t *npairs);
 
-/* The full symmetric matrix whose upper-triangle leaves (I <= J) are those of
- * U: leaf (J, I) of the result is leaf (I, J) of U transposed.  Every leaf
- * of U is kept, all-zero or not.  U must hold no leaf below the diagonal
+/* The plan of the upper-triangle leaves (I <= J) of C = A*B, for products
+ * known to be symmetric though A and B differ (paper, Section 2.2 lists
+ * symmetric multiplication; e.g. X^2 * X in a purification step, where the
+ * factors are commuting symmetric matrices).  Nothing about symmetry is
+ * checked.  cht_symbolic_multiply_symsquare(A) is this call with B = A.
+ * Synchronises `stream` four times. */
+int cht_symbolic_multiply_upper(cht_mat_t A, cht_mat_t B, void *stream, cht_plan_t *out,
+                                int64_t *nnzb_C, int64_t *npairs);
+
+/* The full symmetric matrix whose upper triangle is that of U, at element
+ * level: leaf (J, I), I < J, of the result is leaf (I, J) of U transposed,
+ * and a diagonal leaf (I, I) keeps the entries (r, c), r <= c, of U's and
+ * takes its entries r > c from (c, r), so the result is exactly symmetric
+ * even where U's diagonal leaves are not (rounding in a product).  Every
+ * leaf of U is kept, all-zero or not.  U must hold no leaf below the diagonal
  * (CHT_ERR_INVALID otherwise, nothing created).  Synchronises `stream`
  * twice. */
 int cht_mat_mirror_upper(cht_mat_t U, void *stream, cht_mat_t *out);
+
+/* ------------------------------------------------------------------------
+ * Matrix addition and truncation (paper, Section 2.2: "matrix addition",
+ * including the addition of a scaled identity, and "truncation", the
+ * removal of small elements with error control).  These are the building
+ * blocks, with the product, of purification-style iterations such as
+ * X <- 3X^2 - 2X^3.
+ * ---------------------------------------------------------------------- */
+
+/* *out = alpha*A + beta*B on the union of the two leaf patterns (Morton
+ * order).  A leaf stored in both is alpha*a + beta*b elementwise, each
+ * product and the sum rounded separately (no fused multiply-add), so results
+ * are reproducible bit for bit; a leaf stored in one operand only is that
+ * operand's scaled leaf.  Every union leaf is stored, even one that cancels
+ * to zero (truncation is a separate call).  CHT_ERR_SHAPE if n or b differ.
+ * Synchronises `stream` once. */
+int cht_add(double alpha, cht_mat_t A, double beta, cht_mat_t B, void *stream,
+            cht_mat_t *out);
+
+/* *out = alpha*A + beta*I: cht_add with B the identity, whose stored leaves
+ * are the G diagonal leaves (I, I) (1 on their diagonal, 0 elsewhere).
+ * Synchronises `stream` once. */
+int cht_add_identity(double alpha, cht_mat_t A, double beta, void *stream, cht_mat_t *out);
+
+typedef enum {
+  CHT_TRUNC_FRO = 0, /* removed part has Frobenius norm <= eps (greedy,     */
+                     /* smallest leaves first)                               */
+  CHT_TRUNC_MAX = 1  /* removed leaves have every |entry| <= eps            */
+} cht_trunc_kind;
+
+/* Truncation at leaf granularity: *out holds the leaves of M that are kept,
+ * values unchanged, in Morton order; a removed leaf becomes nil.
+ *  CHT_TRUNC_FRO: leaves sorted by squared Frobenius norm, ascending, ties
+ *    in Morton order; with S_r the prefix sums of the sorted squared norms,
+ *    the leaves before the first rank r with S_r > eps^2 are removed.
+ *    *removed (may be NULL) = sqrt(S) of the removed leaves, <= eps.
+ *  CHT_TRUNC_MAX: a leaf is removed iff its largest magnitude is <= eps;
+ *    *removed = the largest removed magnitude (max-norm error).
+ * eps = 0 removes exactly the all-zero leaves.  CHT_ERR_INVALID for eps < 0,
+ * NaN eps or an unknown kind.  Synchronises `stream` once. */
+int cht_truncate(cht_mat_t M, double eps, int kind, void *stream, cht_mat_t *out,
+                 double *removed);
 
 /* Plan counts; any out-pointer may be NULL. */
 int cht_plan_info(cht_plan_t P, int64_t *nnzb_C, int64_t *npairs);

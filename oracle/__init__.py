@@ -40,6 +40,12 @@ def load(mutant: int = 0):
     lib.orc_multiply.argtypes = [_VP, _VP, ctypes.POINTER(_VP), _I64P]
     lib.orc_multiply_spamm.argtypes = [_VP, _VP, ctypes.c_double, ctypes.POINTER(_VP), _I64P]
     lib.orc_multiply_upper.argtypes = [_VP, _VP, ctypes.POINTER(_VP), _I64P]
+    lib.orc_mirror_upper.argtypes = [_VP, ctypes.POINTER(_VP)]
+    lib.orc_add.argtypes = [ctypes.c_double, _VP, ctypes.c_double, _VP, ctypes.POINTER(_VP)]
+    lib.orc_add_identity.argtypes = [ctypes.c_double, _VP, ctypes.c_double,
+                                     ctypes.POINTER(_VP)]
+    lib.orc_truncate.argtypes = [_VP, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_VP),
+                                 ctypes.POINTER(ctypes.c_double)]
     lib.orc_transpose.argtypes = [_VP, ctypes.POINTER(_VP)]
     lib.orc_restrict.argtypes = [_VP, _VP, ctypes.POINTER(_VP)]
     lib.orc_backward.argtypes = [_VP, _VP, _VP, ctypes.POINTER(_VP),
@@ -131,6 +137,33 @@ class OMatrix:
         _check(self._lib.orc_multiply_upper(self._h, other._h, ctypes.byref(h),
                                             ctypes.byref(np_)))
         return OMatrix(h, self._lib), int(np_.value)
+
+    def mirror_upper(self) -> "OMatrix":
+        """The symmetric matrix whose upper-triangle leaves are self's."""
+        h = _VP()
+        _check(self._lib.orc_mirror_upper(self._h, ctypes.byref(h)))
+        return OMatrix(h, self._lib)
+
+    def add(self, alpha: float, other: "OMatrix", beta: float) -> "OMatrix":
+        """alpha * self + beta * other on the union pattern."""
+        h = _VP()
+        _check(self._lib.orc_add(float(alpha), self._h, float(beta), other._h, ctypes.byref(h)))
+        return OMatrix(h, self._lib)
+
+    def add_identity(self, alpha: float, beta: float) -> "OMatrix":
+        """alpha * self + beta * I."""
+        h = _VP()
+        _check(self._lib.orc_add_identity(float(alpha), self._h, float(beta), ctypes.byref(h)))
+        return OMatrix(h, self._lib)
+
+    def truncate(self, eps: float, kind: int = 0):
+        """(T, removed): leaf truncation with Frobenius (kind 0) or max-norm
+        (kind 1) error control."""
+        h = _VP()
+        rem = ctypes.c_double(0.0)
+        _check(self._lib.orc_truncate(self._h, float(eps), int(kind), ctypes.byref(h),
+                                      ctypes.byref(rem)))
+        return OMatrix(h, self._lib), float(rem.value)
 
     def __matmul__(self, other: "OMatrix") -> "OMatrix":
         return self.multiply(other)[0]

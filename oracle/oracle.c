@@ -96,6 +96,24 @@ static int cmp_i64(const void *x, const void *y) {
     return (a > b) - (a < b);
 }
 
+/* Store leaf (I, J) with values v (transposed if trans) in m. */
+static void insert_leaf(orc_mat *m, int64_t I, int64_t J, const double *v, int trans) {
+    const int bs = m->b;
+    node **slot = &m->root;
+    for (int lev = m->depth;; --lev) {
+        if (!*slot) *slot = new_node();
+        if (lev == 0) break;
+        int qi = (int)((I >> (lev - 1)) & 1);
+        int qj = (int)((J >> (lev - 1)) & 1);
+        slot = &(*slot)->q[2 * qi + qj];
+    }
+    double *leaf = (double *)xcalloc((size_t)bs * bs, sizeof(double));
+    for (int r = 0; r < bs; ++r)
+        for (int c = 0; c < bs; ++c)
+            leaf[(size_t)r * bs + c] = trans ? v[(size_t)c * bs + r] : v[(size_t)r * bs + c];
+    (*slot)->leaf = leaf;
+}
+
 int orc_build(int64_t n, int32_t b, int64_t nblk, const int32_t *brow,
               const int32_t *bcol, const double *vals, orc_mat **out) {
     if (!out || n <= 0 || b <= 0 || n % b || nblk < 0) return -1;
@@ -126,16 +144,7 @@ int orc_build(int64_t n, int32_t b, int64_t nblk, const int32_t *brow,
         for (size_t e = 0; e < lsz; ++e)
             if (v[e] != 0.0) { nonzero = 1; break; }
         if (!nonzero) continue; /* identically zero: nil */
-        node **slot = &m->root;
-        for (int lev = m->depth;; --lev) {
-            if (!*slot) *slot = new_node();
-            if (lev == 0) break;
-            int qi = (int)((brow[i] >> (lev - 1)) & 1);
-            int qj = (int)((bcol[i] >> (lev - 1)) & 1);
-            slot = &(*slot)->q[2 * qi + qj];
-        }
-        (*slot)->leaf = (double *)xcalloc(lsz, sizeof(double));
-        memcpy((*slot)->leaf, v, lsz * sizeof(double));
+        insert_leaf(m, brow[i], bcol[i], v, 0);
     }
     *out = m;
     return 0;
@@ -300,7 +309,7 @@ int orc_multiply_spamm(const orc_mat *A, const orc_mat *B, double tau,
  * quadrants 11 and 22 are again on the diagonal, quadrant 12 lies wholly
  * above it (every product), quadrant 21 wholly below it (skipped). */
 static node *mul_upper(const node *a, const node *b, int lev, int bs,
-                       int64_t *npairs) {
+                       int64_t *npairs, int par) {
     if (!a || !b) return NULL;
     if (lev == 0) return mul(a, b, 0, bs, npairs, 0);
     node *t[8] = {0};
@@ -308,13 +317,21 @@ static node *mul_upper(const node *a, const node *b, int lev, int bs,
         for (int j = i; j < 2; ++j)
             for (int k = 0; k < 2; ++k) {
                 const node *ak = a->q[2 * i + k], *bk = b->q[2 * k + j];
+                node **slot = &t[2 * (2 * i + j) + k];
 #if ORC_MUTANT == 5
-                t[2 * (2 * i + j) + k] = mul_upper(ak, bk, lev - 1, bs, npairs);
+#pragma omp task firstprivate(ak, bk, slot) if (par > 0)
+                *slot = mul_upper(ak, bk, lev - 1, bs, npairs, par - 1);
 #else
-                t[2 * (2 * i + j) + k] = i == j ? mul_upper(ak, bk, lev - 1, bs, npairs)
-                                                : mul(ak, bk, lev - 1, bs, npairs, 0);
+                if (i == j) {
+#pragma omp task firstprivate(ak, bk, slot) if (par > 0)
+                    *slot = mul_upper(ak, bk, lev - 1, bs, npairs, par - 1);
+                } else {
+#pragma omp task firstprivate(ak, bk, slot) if (par > 0)
+                    *slot = mul(ak, bk, lev - 1, bs, npairs, par - 1);
+                }
 #endif
             }
+#pragma omp taskwait
     node *c = new_node();
     int any = 0;
     for (int ij = 0; ij < 4; ++ij) {
@@ -334,7 +351,9 @@ int orc_multiply_upper(const orc_mat *A, const orc_mat *B, orc_mat **C,
     if (A->n != B->n || A->b != B->b) return -2;
     orc_mat *m = new_mat(A->n, A->b);
     int64_t np = 0;
-    m->root = mul_upper(A->root, B->root, A->depth, A->b, &np);
+#pragma omp parallel
+#pragma omp single
+    m->root = mul_upper(A->root, B->root, A->depth, A->b, &np, PAR_LEVELS);
     if (npairs) *npairs = np;
     *C = m;
     return 0;
@@ -408,6 +427,184 @@ int orc_backward(const orc_mat *A, const orc_mat *B, const orc_mat *dC,
     rc |= orc_restrict(p, B, dB);
     orc_free(p);
     orc_free(at);
+    return rc;
+}
+
+/* ------------------------------------------------------------ addition -- */
+
+/* alpha*x + beta*y as a new tree on the union of the two patterns (paper,
+ * Section 2.2, matrix addition).  A leaf present on one side only is that
+ * side's scaled copy; a leaf present on both is alpha*x + beta*y elementwise
+ * (two products, then one sum).  idn != 0 makes y the identity: y is not read,
+ * and the leaf (I, I) of y, for every leaf row I < grid, holds 1 on its
+ * diagonal and 0 elsewhere. */
+static node *add_rec(double alpha, const node *x, double beta, const node *y, int idn,
+                     int lev, int bs, int64_t I, int64_t grid) {
+    const int ydiag = idn && I < grid; /* this node carries identity leaves */
+    if (!x && !y && !ydiag) return NULL;
+    node *c = new_node();
+    if (lev == 0) {
+        size_t lsz = (size_t)bs * bs;
+        c->leaf = (double *)xcalloc(lsz, sizeof(double));
+        for (int r = 0; r < bs; ++r)
+            for (int q = 0; q < bs; ++q) {
+                size_t e = (size_t)r * bs + q;
+                int have_y = idn ? ydiag : y != NULL;
+                double yv = idn ? (r == q ? 1.0 : 0.0) : (y ? y->leaf[e] : 0.0);
+#if ORC_MUTANT == 6
+                if (x && have_y) c->leaf[e] = alpha * x->leaf[e] + beta * yv;
+                else if (x) c->leaf[e] = x->leaf[e];
+                else c->leaf[e] = beta * yv;
+#else
+                if (x && have_y) c->leaf[e] = alpha * x->leaf[e] + beta * yv;
+                else if (x) c->leaf[e] = alpha * x->leaf[e];
+                else c->leaf[e] = beta * yv;
+#endif
+            }
+        return c;
+    }
+    const int64_t half = (int64_t)1 << (lev - 1);
+    for (int qi = 0; qi < 2; ++qi)
+        for (int qj = 0; qj < 2; ++qj) {
+            const int k = 2 * qi + qj;
+            /* identity leaves lie only in the diagonal quadrants */
+            const int sub_idn = idn && qi == qj;
+            c->q[k] = add_rec(alpha, x ? x->q[k] : NULL, beta,
+                              idn ? NULL : (y ? y->q[k] : NULL), sub_idn, lev - 1, bs,
+                              I + qi * half, grid);
+        }
+    if (!c->q[0] && !c->q[1] && !c->q[2] && !c->q[3]) {
+        free(c);
+        return NULL;
+    }
+    return c;
+}
+
+int orc_add(double alpha, const orc_mat *A, double beta, const orc_mat *B, orc_mat **out) {
+    if (!A || !B || !out) return -1;
+    if (A->n != B->n || A->b != B->b) return -2;
+    orc_mat *m = new_mat(A->n, A->b);
+    m->root = add_rec(alpha, A->root, beta, B->root, 0, A->depth, A->b, 0, A->grid);
+    *out = m;
+    return 0;
+}
+
+int orc_add_identity(double alpha, const orc_mat *A, double beta, orc_mat **out) {
+    if (!A || !out) return -1;
+    orc_mat *m = new_mat(A->n, A->b);
+    m->root = add_rec(alpha, A->root, beta, NULL, 1, A->depth, A->b, 0, A->grid);
+    *out = m;
+    return 0;
+}
+
+/* ---------------------------------------------------------- truncation -- */
+
+typedef struct {
+    double key;  /* squared Frobenius norm, or largest magnitude */
+    int64_t pos; /* position in Morton order (ties: earlier first) */
+} leaf_key;
+
+static int cmp_leaf_key(const void *x, const void *y) {
+    const leaf_key *a = (const leaf_key *)x, *b = (const leaf_key *)y;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return (a->pos > b->pos) - (a->pos < b->pos);
+}
+
+int orc_truncate(const orc_mat *M, double eps, int kind, orc_mat **out, double *removed) {
+    if (!M || !out || !(eps >= 0.0) || (kind != 0 && kind != 1)) return -1;
+    const int64_t nl = orc_nleaves(M);
+    const size_t lsz = (size_t)M->b * M->b;
+    int32_t *br = (int32_t *)xcalloc(nl ? nl : 1, sizeof(int32_t));
+    int32_t *bc = (int32_t *)xcalloc(nl ? nl : 1, sizeof(int32_t));
+    double *v = (double *)xcalloc((nl ? nl : 1) * lsz, sizeof(double));
+    orc_extract(M, br, bc, v);
+    leaf_key *k = (leaf_key *)xcalloc(nl ? nl : 1, sizeof(leaf_key));
+    char *drop = (char *)xcalloc(nl ? nl : 1, 1);
+    double rem = 0.0;
+    for (int64_t l = 0; l < nl; ++l) {
+        double s = 0.0;
+        for (size_t e = 0; e < lsz; ++e) {
+            double a = v[(size_t)l * lsz + e];
+            if (kind == 0) s += a * a;
+            else if (fabs(a) > s) s = fabs(a);
+        }
+        k[l].key = s;
+        k[l].pos = l;
+    }
+    if (kind == 0) {
+        /* Frobenius-norm control: remove the leaves of smallest norm, in
+         * ascending order, while the removed squared norm stays <= eps^2 */
+        qsort(k, (size_t)nl, sizeof(leaf_key), cmp_leaf_key);
+        double acc = 0.0;
+        for (int64_t r = 0; r < nl; ++r) {
+#if ORC_MUTANT == 7
+            double next = acc + k[nl - 1 - r].key;
+            if (!(next <= eps * eps)) break;
+            acc = next;
+            drop[k[nl - 1 - r].pos] = 1;
+#else
+            double next = acc + k[r].key;
+            if (!(next <= eps * eps)) break;
+            acc = next;
+            drop[k[r].pos] = 1;
+#endif
+        }
+        rem = sqrt(acc);
+    } else {
+        /* max-norm control: remove every leaf whose entries are all <= eps */
+        for (int64_t l = 0; l < nl; ++l)
+            if (k[l].key <= eps) {
+                drop[l] = 1;
+                if (k[l].key > rem) rem = k[l].key;
+            }
+    }
+    int64_t w = 0;
+    for (int64_t l = 0; l < nl; ++l) {
+        if (drop[l]) continue;
+        br[w] = br[l];
+        bc[w] = bc[l];
+        memmove(v + (size_t)w * lsz, v + (size_t)l * lsz, lsz * sizeof(double));
+        ++w;
+    }
+    int rc = orc_build(M->n, M->b, w, br, bc, v, out);
+    if (removed) *removed = rem;
+    free(br);
+    free(bc);
+    free(v);
+    free(k);
+    free(drop);
+    return rc;
+}
+
+/* --------------------------------------------------------------- mirror -- */
+
+int orc_mirror_upper(const orc_mat *U, orc_mat **out) {
+    if (!U || !out) return -1;
+    const int64_t nl = orc_nleaves(U);
+    const size_t lsz = (size_t)U->b * U->b;
+    int32_t *br = (int32_t *)xcalloc(nl ? nl : 1, sizeof(int32_t));
+    int32_t *bc = (int32_t *)xcalloc(nl ? nl : 1, sizeof(int32_t));
+    double *v = (double *)xcalloc((nl ? nl : 1) * lsz, sizeof(double));
+    orc_extract(U, br, bc, v);
+    int rc = 0;
+    for (int64_t l = 0; l < nl; ++l)
+        if (br[l] > bc[l]) rc = -1;
+    if (rc == 0) {
+        orc_mat *m = new_mat(U->n, U->b);
+        const int bs = U->b;
+        for (int64_t l = 0; l < nl; ++l) {
+            double *x = v + (size_t)l * lsz;
+            if (br[l] == bc[l]) /* diagonal leaf: upper triangle mirrored */
+                for (int r = 0; r < bs; ++r)
+                    for (int c = 0; c < r; ++c) x[(size_t)r * bs + c] = x[(size_t)c * bs + r];
+            insert_leaf(m, br[l], bc[l], x, 0);
+            if (br[l] != bc[l]) insert_leaf(m, bc[l], br[l], x, 1);
+        }
+        *out = m;
+    }
+    free(br);
+    free(bc);
+    free(v);
     return rc;
 }
 

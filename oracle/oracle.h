@@ -51,6 +51,31 @@ int orc_multiply_spamm(const orc_mat *A, const orc_mat *B, double tau,
 int orc_multiply_upper(const orc_mat *A, const orc_mat *B, orc_mat **C,
                        int64_t *npairs);
 
+/* alpha*A + beta*B on the union of the patterns (paper, Section 2.2).  A leaf
+ * on both sides is alpha*a + beta*b elementwise (two products, one sum,
+ * no fused multiply-add); a leaf on one side only is alpha*a or beta*b.
+ * Every leaf of the union is kept, even if it cancels to zero. */
+int orc_add(double alpha, const orc_mat *A, double beta, const orc_mat *B, orc_mat **out);
+
+/* alpha*A + beta*I (paper, Section 2.2, addition of a scaled identity): as
+ * orc_add with B the identity, whose leaves are the diagonal leaves (I, I). */
+int orc_add_identity(double alpha, const orc_mat *A, double beta, orc_mat **out);
+
+/* Truncation (paper, Section 2.2: removal of small elements with error
+ * control), at leaf granularity.  kind 0 (Frobenius): sort the leaves by
+ * squared Frobenius norm, ascending (ties in Morton order), and remove them
+ * in that order while the running sum of removed squared norms stays
+ * <= eps^2; *removed = sqrt of that sum, so ||M - out||_F = *removed <= eps.
+ * kind 1 (max norm): remove every leaf whose largest magnitude is <= eps;
+ * *removed = the largest removed magnitude.  removed may be NULL. */
+int orc_truncate(const orc_mat *M, double eps, int kind, orc_mat **out, double *removed);
+
+/* The symmetric matrix whose upper triangle (element level) is U's: leaf
+ * (J, I), I < J, is U's leaf (I, J) transposed; a diagonal leaf keeps its
+ * entries on and above its diagonal and mirrors them below.  Every leaf of
+ * U is kept, all-zero or not.  -1 if U has a leaf below the diagonal. */
+int orc_mirror_upper(const orc_mat *U, orc_mat **out);
+
 /* Transpose (a new matrix). */
 int orc_transpose(const orc_mat *A, orc_mat **out);
 

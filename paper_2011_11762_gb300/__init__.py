@@ -229,12 +229,52 @@ def cht_symbolic_multiply_symsquare(A: Matrix, stream=None) -> Plan:
     return Plan(h, A, A)
 
 
+def cht_symbolic_multiply_upper(A: Matrix, B: Matrix, stream=None) -> Plan:
+    """Plan of the upper-triangle leaves (I <= J) of A*B (for a product known
+    to be symmetric); multiply with cht_multiply(plan, A, B)."""
+    h = _VP()
+    _check(_lib.load().cht_symbolic_multiply_upper(A.handle, B.handle, _stream(stream),
+                                                   ctypes.byref(h), None, None),
+           "cht_symbolic_multiply_upper")
+    return Plan(h, A, B)
+
+
 def cht_mat_mirror_upper(U: Matrix, stream=None) -> Matrix:
     """The full symmetric matrix from its upper-triangle leaves."""
     h = _VP()
     _check(_lib.load().cht_mat_mirror_upper(U.handle, _stream(stream), ctypes.byref(h)),
            "cht_mat_mirror_upper")
     return Matrix(h)
+
+
+CHT_TRUNC_FRO = 0
+CHT_TRUNC_MAX = 1
+
+
+def cht_add(alpha: float, A: Matrix, beta: float, B: Matrix, stream=None) -> Matrix:
+    """alpha*A + beta*B on the union of the leaf patterns."""
+    h = _VP()
+    _check(_lib.load().cht_add(float(alpha), A.handle, float(beta), B.handle, _stream(stream),
+                               ctypes.byref(h)), "cht_add")
+    return Matrix(h)
+
+
+def cht_add_identity(alpha: float, A: Matrix, beta: float, stream=None) -> Matrix:
+    """alpha*A + beta*I."""
+    h = _VP()
+    _check(_lib.load().cht_add_identity(float(alpha), A.handle, float(beta), _stream(stream),
+                                        ctypes.byref(h)), "cht_add_identity")
+    return Matrix(h)
+
+
+def cht_truncate(M: Matrix, eps: float, kind: int = CHT_TRUNC_FRO, stream=None):
+    """(T, removed): M without its small leaves; removed = the Frobenius
+    (CHT_TRUNC_FRO) or max-norm (CHT_TRUNC_MAX) size of what was removed."""
+    h = _VP()
+    rem = ctypes.c_double(0.0)
+    _check(_lib.load().cht_truncate(M.handle, float(eps), int(kind), _stream(stream),
+                                    ctypes.byref(h), ctypes.byref(rem)), "cht_truncate")
+    return Matrix(h), rem.value
 
 
 def cht_multiply(plan: Plan, A: Matrix, B: Matrix, mode: int = CHT_FP64, nslices: int = 0,

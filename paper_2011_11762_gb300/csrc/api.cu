@@ -14,6 +14,10 @@ int build_matrix(int64_t n, int32_t b, int64_t nblocks, const int32_t *d_brow,
                  const int32_t *d_bcol, const double *d_vals, cudaStream_t s, cht_mat **out,
                  bool drop_zero);
 int mirror_upper(cht_mat *U, cudaStream_t s, cht_mat **out);
+int add_matrices(double alpha, cht_mat *A, double beta, cht_mat *B, cudaStream_t s,
+                 cht_mat **out);
+int truncate_matrix(cht_mat *M, double eps, int kind, cudaStream_t s, cht_mat **out,
+                    double *removed);
 int densify(cht_mat *M, double *d_out, int64_t ld, cudaStream_t s);
 int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
              const double *normA = nullptr, const double *normB = nullptr, double tau = 0.0,
@@ -331,6 +335,21 @@ int cht_symbolic_multiply_symsquare(cht_mat_t A, void *stream, cht_plan_t *out,
   return CHT_OK;
 }
 
+int cht_symbolic_multiply_upper(cht_mat_t A, cht_mat_t B, void *stream, cht_plan_t *out,
+                                int64_t *nnzb_C, int64_t *npairs) {
+  if (!out) {
+    set_error("null plan out-pointer");
+    return CHT_ERR_INVALID;
+  }
+  CHT_TRY(check_pair(A, B));
+  cht_plan *p = nullptr;
+  CHT_TRY(symbolic(*A->pat, *B->pat, as_stream(stream), &p, nullptr, nullptr, 0.0, true));
+  if (nnzb_C) *nnzb_C = p->C->nnz;
+  if (npairs) *npairs = p->npairs;
+  *out = p;
+  return CHT_OK;
+}
+
 int cht_mat_mirror_upper(cht_mat_t U, void *stream, cht_mat_t *out) {
   if (!U || !out) {
     set_error("null matrix or out-pointer");
@@ -338,6 +357,45 @@ int cht_mat_mirror_upper(cht_mat_t U, void *stream, cht_mat_t *out) {
   }
   cht_mat *m = nullptr;
   CHT_TRY(mirror_upper(U, as_stream(stream), &m));
+  *out = m;
+  return CHT_OK;
+}
+
+int cht_add(double alpha, cht_mat_t A, double beta, cht_mat_t B, void *stream,
+            cht_mat_t *out) {
+  if (!A || !B || !out) {
+    set_error("null matrix or out-pointer");
+    return CHT_ERR_INVALID;
+  }
+  cht_mat *m = nullptr;
+  CHT_TRY(add_matrices(alpha, A, beta, B, as_stream(stream), &m));
+  *out = m;
+  return CHT_OK;
+}
+
+int cht_add_identity(double alpha, cht_mat_t A, double beta, void *stream, cht_mat_t *out) {
+  if (!A || !out) {
+    set_error("null matrix or out-pointer");
+    return CHT_ERR_INVALID;
+  }
+  cht_mat *m = nullptr;
+  CHT_TRY(add_matrices(alpha, A, beta, nullptr, as_stream(stream), &m));
+  *out = m;
+  return CHT_OK;
+}
+
+int cht_truncate(cht_mat_t M, double eps, int kind, void *stream, cht_mat_t *out,
+                 double *removed) {
+  if (!M || !out) {
+    set_error("null matrix or out-pointer");
+    return CHT_ERR_INVALID;
+  }
+  if (!(eps >= 0.0) || (kind != CHT_TRUNC_FRO && kind != CHT_TRUNC_MAX)) {
+    set_error("truncation: eps must be >= 0 and kind CHT_TRUNC_FRO or CHT_TRUNC_MAX");
+    return CHT_ERR_INVALID;
+  }
+  cht_mat *m = nullptr;
+  CHT_TRY(truncate_matrix(M, eps, kind, as_stream(stream), &m, removed));
   *out = m;
   return CHT_OK;
 }

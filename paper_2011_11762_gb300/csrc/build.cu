@@ -161,7 +161,8 @@ int build_pattern_index(Pattern &p, cudaStream_t s) {
 }
 
 // Lower-triangle mirror: leaf l (I <= J) is emitted as (I, J) and, off the
-// diagonal, also as (J, I) with transposed values; pos[l] = output slot.
+// diagonal, also as (J, I) with transposed values; a diagonal leaf keeps its
+// upper triangle and mirrors it into its lower one; pos[l] = output slot.
 __global__ void k_mirror(const int32_t *__restrict__ brow, const int32_t *__restrict__ bcol,
                          const double *__restrict__ vals, const int64_t *__restrict__ pos,
                          int64_t n, int b, int32_t *__restrict__ orow, int32_t *__restrict__ ocol,
@@ -179,9 +180,15 @@ __global__ void k_mirror(const int32_t *__restrict__ brow, const int32_t *__rest
       }
     }
     for (int e = threadIdx.x; e < bb; e += blockDim.x) {
-      const double v = vals[l * bb + e];
-      ovals[q * bb + e] = v;
-      if (I != J) ovals[(q + 1) * bb + (e % b) * b + e / b] = v;
+      const int r = e / b, c = e % b;
+      if (I != J) {
+        const double v = vals[l * bb + e];
+        ovals[q * bb + e] = v;
+        ovals[(q + 1) * bb + c * b + r] = v;
+      } else {
+        // diagonal leaf: its upper triangle (r <= c) is kept and mirrored
+        ovals[q * bb + e] = vals[l * bb + (r <= c ? e : c * b + r)];
+      }
     }
   }
 }

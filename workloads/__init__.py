@@ -30,6 +30,7 @@ from .structures import (  # noqa: F401
     values_on_pattern,
     reblock,
     symmetrize,
+    gershgorin_bounds,
     config2_symmetric,
     batched_products,
     config1,

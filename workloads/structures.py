@@ -264,6 +264,24 @@ def symmetrize(m: BlockMatrix) -> BlockMatrix:
     return BlockMatrix(m.n, b, (allk // g).astype(np.int32), (allk % g).astype(np.int32), vals)
 
 
+def gershgorin_bounds(m: BlockMatrix):
+    """(lo, hi) enclosing every eigenvalue of the symmetric matrix m
+    (Gershgorin discs: diagonal entry -+ the off-diagonal absolute row sum).
+    Used to map a matrix's spectrum into [0, 1] before purification."""
+    b = m.b
+    absrow = np.zeros(m.n)
+    diag = np.zeros(m.n)
+    rows = (m.brow.astype(np.int64)[:, None] * b + np.arange(b)[None, :]).reshape(-1)
+    np.add.at(absrow, rows, np.abs(m.vals).sum(axis=2).reshape(-1))
+    on = m.brow == m.bcol
+    if np.any(on):
+        d = np.diagonal(m.vals[on], axis1=1, axis2=2)
+        drows = (m.brow[on].astype(np.int64)[:, None] * b + np.arange(b)[None, :]).reshape(-1)
+        diag[drows] = d.reshape(-1)
+    radius = absrow - np.abs(diag)
+    return float(np.min(diag - radius)), float(np.max(diag + radius))
+
+
 # --------------------------------------------------------------------------
 # The five workloads
 # --------------------------------------------------------------------------
