@@ -14,7 +14,8 @@ resident in HBM and larger than L2.
 Further sections on their own workloads (each reported in the same JSON
 line): the split-precision form, the sparse approximate product, the
 symmetric square, McWeeny purification steps (the second workload), the
-backward of L = ||A B - T||_F^2, and the batched form.
+paper's weak-scaling structures at its first size, the backward of
+L = ||A B - T||_F^2, and the batched form.
 
 ``--impl reference`` times the CPU oracle (the plain recursive quadtree
 multiply) on a bounded sample of the same workload on the host cores.
@@ -53,7 +54,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=65536, help="3D-locality workload size")
-    ap.add_argument("--sections", default="split,spamm,symsquare,purify,backward,batched",
+    ap.add_argument("--sections",
+                    default="split,spamm,symsquare,purify,table1,backward,batched",
                     help="extra sections (comma list; '' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -527,6 +529,46 @@ def section_purify(args, world, cht, torch):
                 float(num / torch.linalg.norm(Xf.values().reshape(-1)))
                 if num is not None else "patterns differ")
         out[name] = steps
+    cht.sync_status()
+    return out
+
+
+def section_table1(args, world, cht, torch):
+    """The paper's weak-scaling structures (Section 3, Table 1) at its first
+    size, N = 100000 (padded to 100032 for 64x64 leaves), band half-width
+    3000: banded, growing block (15716-wide top-left block) and random
+    blocks (one block placed at random; its size doubles the banded flops).
+    Each structure is squared (C = A*A) as in the paper.  Reported: the
+    element-level Tflop of the product (the paper's Tflop row), the leaf
+    pairs, one FP64 step and the mean of two split steps (symbolic +
+    numeric), with both the leaf-level useful TFLOP/s and the element-level
+    rate (paper's flops / time)."""
+    import workloads as w
+    stream = torch.cuda.current_stream()
+    out = {}
+    for kind in ("banded", "growing_block", "random_blocks"):
+        a, blocks, eflops = w.table1_structure(kind, 100000, 64)
+        A = cht.from_block_matrix(a)
+        del a
+        plan = cht.cht_symbolic_multiply(A, A)
+        res = {"element_tflop": eflops / 1e12, "blocks": blocks, "leaves": A.nblocks,
+               "pairs": plan.npairs, "leaf_tflop": plan.useful_flops / 1e12}
+        del plan
+        # FP64 steps take seconds each, so that one is timed cold (the
+        # library is warm from the earlier sections); split: 1 warm-up
+        for name, mode, steps, warm in (("fp64", cht.CHT_FP64, 1, 0),
+                                        ("split", cht.CHT_SPLIT_BF16, 2, 1)):
+            def step(mode=mode):
+                p = cht.cht_symbolic_multiply(A, A)
+                cht.cht_multiply(p, A, A, mode=mode)
+            ms = _time_steps(torch, stream, step, steps, warm)
+            res[name] = {"ms_per_step": ms,
+                         "value": res["leaf_tflop"] * 1e12 * world / (ms * 1e-3) / 1e12,
+                         "unit": UNIT,
+                         "element_level_tflops": eflops * world / (ms * 1e-3) / 1e12}
+        out[kind] = res
+        del A
+    out["workload"] = "table1_N100000_hw3000_b64"
     cht.sync_status()
     return out
 

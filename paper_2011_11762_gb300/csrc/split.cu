@@ -420,6 +420,7 @@ struct SplitProd {
   const int *row_exp;
   const int *col_exp;
   double *C;
+  double *const *cptr;      // per unit: output leaf (null: C + unit * b * b)
   int32_t b;
   int32_t pad;
 };
@@ -790,7 +791,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           sl.cexp[r] = exp16(d.col_exp[static_cast<int64_t>(ccol) * b + r]);
         }
         if (lane == 0) {
-          sl.C = d.C + o * b * b;
+          sl.C = d.cptr ? d.cptr[o] : d.C + o * b * b;
           sl.np = static_cast<int32_t>(p1 - p0);
           sl.b = b;
           sl.u = static_cast<int32_t>(n);
@@ -1005,15 +1006,106 @@ int launch_split(const SplitProd &single, const SplitProd *prods, const int64_t 
   return launched("split_gemm");
 }
 
+// The parts handed between epilogue warps hold (windows * 2^56) in 64 bits,
+// so one unit sums at most 127 windows of leaf pairs.
+int max_unit_pairs(int b) { return 127 * (b == 64 ? Cfg<64>::WINDOW : Cfg<32>::WINDOW); }
+
 int check_segments(const cht_plan *plan) {
-  // the parts handed between epilogue warps hold (windows * 2^56) in 64 bits
-  const int window = plan->b == 64 ? Cfg<64>::WINDOW : Cfg<32>::WINDOW;
-  if ((plan->max_seg + window - 1) / window >= 128) {
-    set_error("split form: a C leaf has %lld leaf pairs (at most %d); use CHT_FP64",
-              (long long)plan->max_seg, 127 * window);
+  if (plan->max_seg > max_unit_pairs(plan->b)) {
+    set_error("split form (batched): a C leaf has %lld leaf pairs (at most %d); use CHT_FP64",
+              (long long)plan->max_seg, max_unit_pairs(plan->b));
     return CHT_ERR_UNSUPPORTED;
   }
   return CHT_OK;
+}
+
+// Long segments: a C leaf with more pairs than one unit may sum is cut into
+// np = ceil(len / maxp) pieces of ceil(len / np) pairs; each piece is a unit
+// whose exact split-form sum goes to a scratch leaf, and the pieces are then
+// added in FP64, in piece order.
+__global__ void k_piece_count(const int64_t *__restrict__ cseg, int64_t nC, int maxp,
+                              int32_t *__restrict__ npiece, int32_t *__restrict__ nscratch) {
+  for (int64_t o = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; o < nC;
+       o += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t len = cseg[o + 1] - cseg[o];
+    const int32_t np = len > maxp ? static_cast<int32_t>((len + maxp - 1) / maxp) : 1;
+    npiece[o] = np;
+    nscratch[o] = np > 1 ? np : 0;
+  }
+}
+
+__global__ void k_piece_fill(const int64_t *__restrict__ cseg, const int32_t *__restrict__ crow,
+                             const int32_t *__restrict__ ccol, int64_t nC,
+                             const int32_t *__restrict__ npiece, const int64_t *__restrict__ vpos,
+                             const int64_t *__restrict__ tpos, double *C, double *scratch, int bb,
+                             int64_t *__restrict__ vseg, int32_t *__restrict__ vrow,
+                             int32_t *__restrict__ vcol, double **__restrict__ vptr) {
+  for (int64_t o = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; o < nC;
+       o += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t p0 = cseg[o], len = cseg[o + 1] - p0;
+    const int32_t np = npiece[o];
+    const int64_t plen = (len + np - 1) / np;
+    for (int32_t q = 0; q < np; ++q) {
+      const int64_t v = vpos[o] + q;
+      const int64_t start = p0 + q * plen;
+      vseg[v] = start < p0 + len ? start : p0 + len;
+      vrow[v] = crow[o];
+      vcol[v] = ccol[o];
+      vptr[v] = np > 1 ? scratch + (tpos[o] + q) * bb : C + o * bb;
+    }
+    if (o == nC - 1) vseg[vpos[o] + np] = cseg[nC];
+  }
+}
+
+__global__ void k_piece_reduce(const int32_t *__restrict__ npiece, const int64_t *__restrict__ tpos,
+                               int64_t nC, const double *__restrict__ scratch, int bb,
+                               double *__restrict__ C) {
+  for (int64_t o = blockIdx.x; o < nC; o += gridDim.x) {
+    const int32_t np = npiece[o];
+    if (np < 2) continue;
+    const double *src = scratch + tpos[o] * bb;
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) {
+      double acc = src[e];
+      for (int32_t q = 1; q < np; ++q) acc += src[static_cast<int64_t>(q) * bb + e];
+      C[o * bb + e] = acc;
+    }
+  }
+}
+
+// The units of one product whose longest segment exceeds one unit's limit.
+struct PieceUnits {
+  DevArray<int32_t> npiece, nscratch, vrow, vcol;
+  DevArray<int64_t> vpos, tpos, vseg;
+  DevArray<double *> vptr;
+  DevArray<double> scratch;
+  int64_t nv = 0;
+};
+
+int make_pieces(const cht_plan *plan, double *Cvals, cudaStream_t s, PieceUnits &pu) {
+  const int64_t nC = plan->C->nnz;
+  const int bb = plan->b * plan->b;
+  CHT_TRY(pu.npiece.alloc(nC, s));
+  CHT_TRY(pu.nscratch.alloc(nC, s));
+  CHT_TRY(pu.vpos.alloc(nC + 1, s));
+  CHT_TRY(pu.tpos.alloc(nC + 1, s));
+  k_piece_count<<<grid_for(nC, 256), 256, 0, s>>>(plan->cseg.p, nC, max_unit_pairs(plan->b),
+                                                  pu.npiece.p, pu.nscratch.p);
+  CHT_TRY(launched("piece_count"));
+  CHT_TRY(scan_exclusive(pu.npiece.p, pu.vpos.p, nC, s));
+  CHT_TRY(scan_exclusive(pu.nscratch.p, pu.tpos.p, nC, s));
+  int64_t nt = 0;
+  CHT_CUDA_TRY(cudaMemcpyAsync(&pu.nv, pu.vpos.p + nC, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CHT_TRY(read_i64(pu.tpos.p + nC, &nt, s));
+  CHT_TRY(pu.vseg.alloc(pu.nv + 1, s));
+  CHT_TRY(pu.vrow.alloc(pu.nv, s));
+  CHT_TRY(pu.vcol.alloc(pu.nv, s));
+  CHT_TRY(pu.vptr.alloc(pu.nv, s));
+  CHT_TRY(pu.scratch.alloc(static_cast<size_t>(nt) * bb, s));
+  k_piece_fill<<<grid_for(nC, 256), 256, 0, s>>>(plan->cseg.p, plan->C->brow.p, plan->C->bcol.p,
+                                                 nC, pu.npiece.p, pu.vpos.p, pu.tpos.p, Cvals,
+                                                 pu.scratch.p, bb, pu.vseg.p, pu.vrow.p,
+                                                 pu.vcol.p, pu.vptr.p);
+  return launched("piece_fill");
 }
 
 struct SplitBatch {
@@ -1036,7 +1128,6 @@ int split_multiply(cht_plan *plan, cht_mat *A, cht_mat *B, int nslices, cudaStre
     set_error("leaf size %d: the split form takes b = 32 or b = 64", b);
     return CHT_ERR_UNSUPPORTED;
   }
-  CHT_TRY(check_segments(plan));
   // elementwise bound relative to 2^(e_r + f_c): K (s + 3) 2^(-s w) with
   // K <= n, plus the FP32 rounding of the low regions (below 2^-50)
   *err_bound = static_cast<double>(plan->n) * (kSB + 3) * 0x1p-48 + 0x1p-50;
@@ -1046,11 +1137,31 @@ int split_multiply(cht_plan *plan, cht_mat *A, cht_mat *B, int nslices, cudaStre
     CHT_TRY(split_operands<64>(A, B, s, op));
   else
     CHT_TRY(split_operands<32>(A, B, s, op));
-  const SplitProd d = make_prod(plan, op, Cvals);
+  SplitProd d = make_prod(plan, op, Cvals);
   DevArray<unsigned long long> counter;
   CHT_TRY(counter.alloc(1, s));
-  if (b == 64) return launch_split<64>(d, nullptr, nullptr, plan->C->nnz, counter.p, s);
-  return launch_split<32>(d, nullptr, nullptr, plan->C->nnz, counter.p, s);
+  int64_t nunits = plan->C->nnz;
+  PieceUnits pu;
+  const bool pieces = plan->max_seg > max_unit_pairs(b);
+  if (pieces) {
+    CHT_TRY(make_pieces(plan, Cvals, s, pu));
+    d.cseg = pu.vseg.p;
+    d.crow = pu.vrow.p;
+    d.ccol = pu.vcol.p;
+    d.cptr = pu.vptr.p;
+    nunits = pu.nv;
+  }
+  if (b == 64)
+    CHT_TRY(launch_split<64>(d, nullptr, nullptr, nunits, counter.p, s));
+  else
+    CHT_TRY(launch_split<32>(d, nullptr, nullptr, nunits, counter.p, s));
+  if (pieces) {
+    const int64_t nC = plan->C->nnz;
+    k_piece_reduce<<<static_cast<unsigned>(std::min<int64_t>(nC, 65535LL * 8)), 256, 0, s>>>(
+        pu.npiece.p, pu.tpos.p, nC, pu.scratch.p, b * b, Cvals);
+    CHT_TRY(launched("piece_reduce"));
+  }
+  return CHT_OK;
 }
 
 int split_batch_prepare(cht_batch *bt, cudaStream_t s) {

@@ -148,3 +148,19 @@ def test_split_timeout_path(lib):
     Co, _ = gu.oracle_product(a, b)
     gu.assert_values_close(C, Co, 1e-12)
     _ = oracle
+
+
+@pytest.mark.parametrize("b,g", [(64, 300), (64, 700), (32, 2100)])
+def test_split_long_segments_are_cut_into_pieces(lib, b, g):
+    # leaf (0, 0) of A*B sums g leaf pairs, more than one unit of the split
+    # kernel sums (254 at b = 64, 1016 at b = 32): it is computed in pieces
+    a, bm = w.dense_line_pair(g * b, b, 1, 91)
+    A, B = gu.upload(lib, a), gu.upload(lib, bm)
+    plan = lib.cht_symbolic_multiply(A, B)
+    OC, npairs = gu.oracle_product(a, bm)
+    assert plan.npairs == npairs
+    Cs, _ = lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
+    gu.assert_same_pattern(Cs, OC)
+    gu.assert_values_close(Cs, OC, 1e-11)
+    _, _, ov = OC.leaves()
+    assert setref.rel_fro(Cs.values()[0].cpu().numpy(), ov[0]) <= 1e-11

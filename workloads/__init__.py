@@ -28,8 +28,15 @@ from .structures import (  # noqa: F401
     locality_matrix,
     random_blocks,
     values_on_pattern,
+    dense_line_pair,
     reblock,
     symmetrize,
+    structure_column_counts,
+    structure_flops,
+    growing_block_size,
+    random_blocks_layout,
+    band_with_blocks,
+    table1_structure,
     gershgorin_bounds,
     config2_symmetric,
     batched_products,

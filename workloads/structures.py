@@ -88,6 +88,131 @@ def banded(n: int, b: int, half_width: int, seed: int) -> BlockMatrix:
 
 
 # --------------------------------------------------------------------------
+# Element-level structures of the paper's weak-scaling sequences (Section 3,
+# Table 1): a band of half-width w united with dense diagonal blocks
+# --------------------------------------------------------------------------
+
+def structure_column_counts(n: int, half_width: int, blocks=()) -> np.ndarray:
+    """Nonzeros of every column of the n x n element structure
+    {(r, c): |r - c| <= w} united with the dense blocks [p, p+s)^2 of
+    ``blocks`` (pairs (p, s), pairwise disjoint).  The structure is
+    symmetric, so row counts are the same."""
+    k = np.arange(n, dtype=np.int64)
+    w = half_width
+    c = np.minimum(k, w) + np.minimum(n - 1 - k, w) + 1
+    for p, sz in blocks:
+        kk = k[p:p + sz]
+        lo = np.minimum(p, np.maximum(kk - w, 0))
+        hi = np.maximum(p + sz - 1, np.minimum(kk + w, n - 1))
+        c[p:p + sz] = hi - lo + 1
+    return c
+
+
+def structure_flops(n: int, half_width: int, blocks=()) -> int:
+    """Element-level flops of the structure times itself,
+    2 sum_k nnz(A[:, k]) nnz(A[k, :]) (the paper's Tflop rows)."""
+    c = structure_column_counts(n, half_width, blocks)
+    sq = c * c  # <= n^2 each; partial sums of 65536 stay below 2^63 for n < 1.1e7
+    return 2 * sum(int(x) for x in np.add.reduceat(sq, np.arange(0, n, 65536)))
+
+
+def _closest_size(flops_of, target: int, hi: int) -> int:
+    lo = 1
+    while lo < hi:  # smallest size reaching the target
+        m = (lo + hi) // 2
+        if flops_of(m) >= target:
+            hi = m
+        else:
+            lo = m + 1
+    best = lo
+    if lo > 1 and abs(flops_of(lo - 1) - target) <= abs(flops_of(lo) - target):
+        best = lo - 1
+    return best
+
+
+def growing_block_size(n: int, half_width: int) -> int:
+    """Size of the dense top-left block for which the band plus the block
+    needs twice the banded flops (the size with the closest flop count)."""
+    target = 2 * structure_flops(n, half_width)
+    return _closest_size(lambda s: structure_flops(n, half_width, [(0, s)]), target, n)
+
+
+def random_blocks_layout(n: int, half_width: int, count: int, seed: int):
+    """``count`` equal dense diagonal blocks at random positions, one in each
+    of ``count`` equal slots of the diagonal, at least ``half_width`` from
+    the slot's ends (so blocks neither overlap nor reach the matrix edge, and
+    the flop count does not depend on the positions).  Their size is the one
+    with the flop count closest to twice the banded flops.  Returns the list
+    of (p, s)."""
+    slot = n // count
+    target = 2 * structure_flops(n, half_width)
+
+    def flops_of(sz):
+        return structure_flops(n, half_width,
+                               [(i * slot + half_width, sz) for i in range(count)])
+
+    sz = _closest_size(flops_of, target, slot - 2 * half_width)
+    if slot - sz - 2 * half_width < 0:
+        raise ValueError("blocks do not fit their slots")
+    rng = np.random.default_rng(seed)
+    offs = rng.integers(0, slot - sz - 2 * half_width + 1, size=count)
+    return [(int(i * slot + half_width + o), int(sz)) for i, o in enumerate(offs)]
+
+
+def band_with_blocks(n: int, b: int, half_width: int, blocks, seed: int) -> BlockMatrix:
+    """The element structure of ``structure_column_counts`` stored in b x b
+    leaves: the dimension is n rounded up to a multiple of b (rows and
+    columns >= n are empty), a leaf is stored iff it holds a structural
+    entry, structural entries are U[-1, 1] and the rest of a stored leaf is
+    zero.  Leaf values are drawn for all stored leaves (row-major leaf order)
+    and then masked."""
+    npad = -(-n // b) * b
+    g = npad // b
+    gn = -(-n // b)  # leaf rows that hold matrix rows
+    wl = (half_width + b - 1) // b
+    keys = set()
+    for i in range(gn):
+        for j in range(max(0, i - wl), min(gn - 1, i + wl) + 1):
+            keys.add(i * g + j)
+    for p, sz in blocks:
+        lo, hi = p // b, (p + sz - 1) // b
+        for i in range(lo, hi + 1):
+            keys.update(i * g + np.arange(lo, hi + 1))
+    key = np.array(sorted(int(k) for k in keys), dtype=np.int64)
+    brow, bcol = (key // g).astype(np.int32), (key % g).astype(np.int32)
+    rng = np.random.default_rng(seed)
+    vals = _uniform_leaves(rng, key.shape[0], b)
+    e = np.arange(b, dtype=np.int64)
+    chunk = 4096
+    for s0 in range(0, key.shape[0], chunk):
+        r = brow[s0:s0 + chunk].astype(np.int64)[:, None, None] * b + e[None, :, None]
+        c = bcol[s0:s0 + chunk].astype(np.int64)[:, None, None] * b + e[None, None, :]
+        m = np.abs(r - c) <= half_width
+        for p, sz in blocks:
+            m |= (r >= p) & (r < p + sz) & (c >= p) & (c < p + sz)
+        m &= (r < n) & (c < n)
+        vals[s0:s0 + chunk] *= m
+    return BlockMatrix(npad, b, brow, bcol, vals)
+
+
+def table1_structure(kind: str, n: int, b: int, half_width: int = 3000, count: int = 1,
+                     seed: int = SEED_A + 6) -> tuple:
+    """One matrix of the paper's weak-scaling sequences: kind 'banded',
+    'growing_block' or 'random_blocks' (``count`` blocks).  Returns
+    (BlockMatrix, blocks, element-level flops of its square)."""
+    if kind == "banded":
+        blocks = []
+    elif kind == "growing_block":
+        blocks = [(0, growing_block_size(n, half_width))]
+    elif kind == "random_blocks":
+        blocks = random_blocks_layout(n, half_width, count, seed + 7)
+    else:
+        raise ValueError(kind)
+    m = band_with_blocks(n, b, half_width, blocks, seed)
+    return m, blocks, structure_flops(n, half_width, blocks)
+
+
+# --------------------------------------------------------------------------
 # 3D locality: jittered cubic lattice ordered along a Morton curve
 # --------------------------------------------------------------------------
 
@@ -217,6 +342,28 @@ def random_blocks(n: int, b: int, p: float, seed: int,
     else:
         vals = _uniform_leaves(rng, brow.shape[0], b)
     return BlockMatrix(n, b, brow, bcol, vals)
+
+
+def dense_line_pair(n: int, b: int, half_width: int, seed: int):
+    """(A, B): A banded (|I - J| <= half_width leaves) plus a full first leaf
+    row, B banded plus a full first leaf column, U[-1, 1] entries.  Leaf
+    (0, 0) of A*B then sums n/b leaf pairs while every other leaf sums a
+    handful: a product with one very long pair segment."""
+    g = n // b
+    out = []
+    for t, sd in ((0, seed), (1, seed + 1)):
+        keys = set()
+        for i in range(g):
+            for j in range(max(0, i - half_width), min(g - 1, i + half_width) + 1):
+                keys.add(i * g + j)
+        for j in range(g):
+            keys.add(j if t == 0 else j * g)
+        key = np.array(sorted(keys), dtype=np.int64)
+        rng = np.random.default_rng(sd)
+        vals = _uniform_leaves(rng, key.shape[0], b)
+        out.append(BlockMatrix(n, b, (key // g).astype(np.int32), (key % g).astype(np.int32),
+                               vals))
+    return out[0], out[1]
 
 
 def values_on_pattern(n: int, b: int, brow, bcol, seed: int) -> BlockMatrix:
