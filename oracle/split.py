@@ -8,21 +8,25 @@ narrow slices so that slice products are exact in a low-precision unit:
 
 1. Row scaling of A: e_r is the exponent with max_k |a_rk| in [2^(e_r-1),
    2^e_r) (frexp); column scaling of B: f_c likewise over column c.
-2. Fixed point with s*w bits: A_int = trunc(a_rk * 2^(s*w - e_r)), so
-   |A_int| < 2^(s*w); the same for B with f_c.
-3. Signed base-2^w digits, most significant first:
-   A_int = sum_{i=1..s} d_i 2^(w(s-i)),  |d_i| <= 2^w - 1,
-   every digit carrying the sign of A_int.  With w <= 8 each digit is exactly
-   representable in bfloat16 (8 significant bits).
-4. C_rc ~= 2^(e_r + f_c - 2sw) sum_{(i,j) in S} 2^(w(2s-i-j)) sum_k d_i,rk g_j,kc
+2. Fixed point with s*w bits: A_int = round(a_rk * 2^(s*w - 1 - e_r))
+   (halves away from zero), so |A_int| <= 2^(s*w - 1); the same for B.
+3. Balanced signed base-2^w digits, most significant first:
+   A_int = sum_{i=1..s} d_i 2^(w(s-i)),  |d_i| <= 2^(w-1),
+   so that a_rk ~= 2^(e_r + 1) sum_i d_i 2^(-w i).  With w <= 8 each digit
+   is exactly representable in bfloat16, and a product of two digits is at
+   most 2^(2w - 2) in magnitude.
+4. C_rc ~= 2^(e_r + f_c + 2) sum_{(i,j) in S} 2^(-w(i+j)) sum_k d_i,rk g_j,kc
    over a chosen set S of slice pairs (usually i + j <= s + 1: the terms
-   with larger i + j are below the truncation error).
+   with larger i + j are below the rounding error).
 
 Everything here is exact (Python integers) except the final conversion of
 each result to FP64.  It is meant for small matrices.
 """
 
 from __future__ import annotations
+
+import math
+from fractions import Fraction
 
 import numpy as np
 
@@ -36,29 +40,44 @@ def row_exponents(x: np.ndarray, axis: int) -> np.ndarray:
 
 
 def fixed_point(x: np.ndarray, exps: np.ndarray, axis: int, s: int, w: int) -> np.ndarray:
-    """trunc(x * 2^(s*w - e)) as exact integers (object array)."""
+    """round(x * 2^(s*w - 1 - e)) (halves away from zero) as exact integers,
+    e the line exponent; |result| <= 2^(s*w - 1) because |x| < 2^e."""
     shape = [1, 1]
     shape[1 - axis] = -1
-    e = exps.reshape(shape)
-    scaled = np.ldexp(x, (s * w - e).astype(np.int64))  # exact: a power-of-two scaling
-    t = np.trunc(scaled)
+    e = np.broadcast_to(exps.reshape(shape), x.shape)
     out = np.empty(x.shape, dtype=object)
-    for idx, v in np.ndenumerate(t):
-        out[idx] = int(v)
+    half = Fraction(1, 2)
+    for idx, v in np.ndenumerate(x):
+        q = Fraction(float(v)) * Fraction(2) ** (s * w - 1 - int(e[idx]))
+        m = math.floor(abs(q) + half)
+        out[idx] = -m if q < 0 else m
     return out
 
 
 def digits(xi: np.ndarray, s: int, w: int) -> list:
-    """Signed base-2^w digits d_1 (most significant) .. d_s of integers."""
+    """Balanced base-2^w digits d_1 (most significant) .. d_s of integers
+    with |x| <= 2^(s*w - 1): the digits of |x| are taken from the least
+    significant one in [-(2^(w-1) - 1), 2^(w-1)], then the sign of x is
+    applied, so every |d_i| <= 2^(w-1) (the most significant one absorbs the
+    remainder and stays in that range)."""
     base = 1 << w
-    out = []
-    mags = np.vectorize(lambda v: abs(v), otypes=[object])(xi)
-    signs = np.vectorize(lambda v: -1 if v < 0 else 1, otypes=[object])(xi)
-    for i in range(1, s + 1):
-        sh = w * (s - i)
-        d = np.vectorize(lambda m: (m >> sh) % base, otypes=[object])(mags)
-        out.append((d * signs).astype(np.int64))
-    return out
+    lo = (base >> 1) - 1
+
+    def split(v):
+        m = abs(v)
+        ds = []
+        for _ in range(s):
+            t = (m + lo) % base - lo
+            ds.append(t)
+            m = (m - t) >> w
+        assert m == 0, "integer out of range for s balanced digits"
+        sg = -1 if v < 0 else 1
+        return [sg * t for t in reversed(ds)]
+
+    per = np.empty(xi.shape + (s,), dtype=np.int64)
+    for idx, v in np.ndenumerate(xi):
+        per[idx] = split(int(v))
+    return [per[..., i] for i in range(s)]
 
 
 def slice_pairs(s: int, extra: bool = False) -> list:
@@ -91,7 +110,8 @@ def split_product(a: np.ndarray, b: np.ndarray, s: int, w: int, pairs=None,
     out = np.empty((m, n), dtype=np.float64)
     for r in range(m):
         for c in range(n):
-            out[r, c] = _to_double(acc[r, c], int(e[r]) + int(f[c]) - w * top)
+            # a = 2^(e+1) sum_i d_i 2^(-w i), likewise b: weight 2^(e+f+2)
+            out[r, c] = _to_double(acc[r, c], int(e[r]) + int(f[c]) + 2 - w * top)
     return out, e, f
 
 
@@ -99,7 +119,6 @@ def _to_double(v: int, exp2: int) -> float:
     """v * 2^exp2 rounded once to the nearest double."""
     if v == 0:
         return 0.0
-    from fractions import Fraction
     q = Fraction(v) * (Fraction(2) ** exp2)
     return float(q)  # Fraction -> float rounds to nearest (ties to even)
 
@@ -108,11 +127,14 @@ def error_bound(a: np.ndarray, b: np.ndarray, s: int, w: int, kdim=None) -> np.n
     """Elementwise a-priori bound on |C_split - A B| for split_product with
     the pairs i + j <= s + 1:
        |C - C~|_rc <= 2^(e_r + f_c) * K * (s + 3) * 2^(-s*w)
-    with K the inner dimension (truncation of each operand contributes
-    < 2^(-s*w) relative to its line maximum < 2^e; each dropped slice pair
-    i + j = s + 1 + q contributes at most K 2^(-w(s - 1 + q)) (1 - 2^-w)^2
-    relative, and summing over q and over the at most s pairs per q stays
-    below (s + 1) K 2^(-s*w))."""
+    with K the inner dimension.  Per term a_rk b_kc, with a = 2^(e+1) (X + dx)
+    and b = 2^(f+1) (Y + dy), |X|, |Y| <= 1/2 and |dx|, |dy| <= 2^(-s*w-1)
+    (rounding): the representation error is below 2^(e+f+2) 2^(-s*w-1) (1 +
+    2^(-s*w)) = 2^(e+f) 2 2^(-s*w) (1 + 2^(-s*w)), and each dropped slice
+    pair i + j = s + 1 + q (at most s of them, j fixing i) is at most
+    2^(e+f+2) 2^(2w-2) 2^(-w(s+1+q)) = 2^(e+f) 2^(-w(s-1+q)), which sums over
+    q >= 1 to below 2^(e+f) s 2^(-s*w) / (1 - 2^-w); together below
+    2^(e+f) (s + 3) 2^(-s*w) per term."""
     e = row_exponents(a, axis=1).astype(np.float64)
     f = row_exponents(b, axis=0).astype(np.float64)
     K = a.shape[1] if kdim is None else kdim

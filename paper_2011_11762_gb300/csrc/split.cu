@@ -3,14 +3,17 @@
 // (kind::f16, FP32 accumulation in TMEM), and an integer recombination.
 //
 // Splitting (error-free transformation in the style of Ozaki, Ogita, Oishi
-// and Rump, Numer. Algorithms 59, 2012): with e_r the exponent of the largest
-// |a| in global row r of A (max < 2^e_r) and f_c that of column c of B,
-//     a_rk = 2^e_r * sum_i d_i 2^(-8i),   b_kc = 2^f_c * sum_j g_j 2^(-8j)
-// up to truncation after the last digit, with signed integer digits
-// |d|, |g| <= 255 (exact in bfloat16).  Then
-//     C_rc = 2^(e_r + f_c) * sum_t S_t 2^(-8t),   S_t = sum_{i+j=t} sum_k d_i g_j,
+// and Rump, Numer. Algorithms 59, 2012): with e_r the frexp exponent of the
+// largest |a| in global row r of A (max < 2^e_r) and f_c that of column c of
+// B, X = round(a_rk 2^(47 - e_r)) has |X| <= 2^47 and balanced signed base-256
+// digits, so
+//     a_rk = 2^(e_r+1) * sum_i d_i 2^(-8i),   b_kc = 2^(f_c+1) * sum_j g_j 2^(-8j)
+// up to the rounding after the last digit, with |d|, |g| <= 128 (exact in
+// bfloat16; a digit product is at most 2^14).  The line exponents are stored
+// as e_r + 1 and f_c + 1.  Then
+//     C_rc = 2^(e_r + f_c + 2) * sum_t S_t 2^(-8t),   S_t = sum_{i+j=t} sum_k d_i g_j,
 // and every S_t is an integer.  Slice pairs with i + j > 7 are dropped (their
-// weight is below the 48-bit truncation).
+// weight is below the 48-bit rounding).
 //
 // Tensor-core mapping (one CTA per C leaf at a time; b = 64 shown, b = 32 in
 // brackets): the A operand of an MMA stacks 2 [4] consecutive slices of the
@@ -22,8 +25,8 @@
 //
 // Exactness: regions r = 0, 1 (diagonals 2..5 and the parts above them)
 // carry the high bits and must be exact.  An FP32 accumulator is exact while
-// every partial sum stays below 2^24, which holds for a window of 2 [8] leaf
-// pairs: 2 blocks * 64 * 2 * 255^2 < 2^24 [1 * 32 * 8 * 255^2 < 2^24].  After
+// every partial sum stays at most 2^24, which holds for a window of 8 [32]
+// leaf pairs: 2 blocks * 64 * 8 * 2^14 = 2^24 [1 * 32 * 32 * 2^14 = 2^24].  After
 // each window the epilogue warps read these regions and add them, converted
 // to integers, into int64 accumulators; the next window restarts them.
 // Region 2 (weight <= 2^-32 of the leading diagonal) accumulates over the
@@ -61,13 +64,13 @@ struct Cfg;
 template <>
 struct Cfg<64> {
   // N is the MMA width: two B slices side by side (2 b columns)
-  static constexpr int N = 128, PARTS = 2, SA = 6, KSTEPS = 4, STAGES = 2, WINDOW = 2;
+  static constexpr int N = 128, PARTS = 2, SA = 6, KSTEPS = 4, STAGES = 2, WINDOW = 8;
   static constexpr int NBLK = 6;
   static constexpr int TMEM_COLS = 512;
 };
 template <>
 struct Cfg<32> {
-  static constexpr int N = 64, PARTS = 4, SA = 8, KSTEPS = 2, STAGES = 3, WINDOW = 8;
+  static constexpr int N = 64, PARTS = 4, SA = 8, KSTEPS = 2, STAGES = 3, WINDOW = 32;
   static constexpr int NBLK = 4;
   static constexpr int TMEM_COLS = 256;
 };
@@ -227,7 +230,9 @@ __device__ inline int exp_of(double x) {
   return (64 - __clzll(static_cast<long long>(mant))) - 1074;
 }
 
-// Magnitude of trunc(|x| * 2^(nbits - e)) and the sign of x.
+// Magnitude of round(|x| * 2^(nbits - e)) (halves rounded up) and the sign of
+// x; e is a stored line exponent (frexp exponent + 1), so the result is at
+// most 2^(nbits - 1).
 __device__ inline unsigned long long fixed_mag(double x, int e, int nbits, bool *neg) {
   const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
   *neg = (bits >> 63) != 0;
@@ -242,9 +247,22 @@ __device__ inline unsigned long long fixed_mag(double x, int e, int nbits, bool 
   }
   if (!mant || e == kNoExp) return 0;
   const int sh = ex + nbits - e;
-  if (sh >= 0) return mant << sh;  // sh <= nbits - 53
-  if (sh <= -64) return 0;
-  return mant >> (-sh);
+  if (sh >= 0) return mant << sh;  // exact; sh <= nbits - 54
+  if (sh <= -55) return 0;         // |x| 2^(nbits-e) < 2^53 2^-55 < 1/2
+  return (mant + (1ULL << (-sh - 1))) >> (-sh);
+}
+
+// Balanced base-256 digits of a magnitude m <= 2^(8n - 1), least significant
+// first: each in [-127, 128], so with the sign applied |digit| <= 128.
+template <int NDIG>
+__device__ inline void balanced_digits(unsigned long long m, bool neg, int (&out)[NDIG]) {
+#pragma unroll
+  for (int i = NDIG - 1; i >= 0; --i) {
+    const int t = static_cast<int>((m + 127ULL) & 0xffULL) - 127;
+    out[i] = neg ? -t : t;
+    m = t >= 0 ? (m - static_cast<unsigned long long>(t)) >> kW
+               : (m + static_cast<unsigned long long>(-t)) >> kW;
+  }
 }
 
 __device__ inline uint32_t pack_bf16x2(int lo, int hi) {
@@ -294,7 +312,7 @@ __device__ inline double scaled_i128_to_double(__int128 v, int e2) {
 
 // ------------------------------------------------------------ pre-kernels --
 
-// Row exponents of A: warp per (leaf, row).
+// Row exponents of A (stored as frexp exponent + 1): warp per (leaf, row).
 __global__ void k_row_exp(const double *__restrict__ vals, const int32_t *__restrict__ brow,
                           int64_t nleaves, int b, int *__restrict__ row_exp) {
   const int lane = threadIdx.x & 31;
@@ -309,11 +327,12 @@ __global__ void k_row_exp(const double *__restrict__ vals, const int32_t *__rest
     for (int k = lane; k < b; k += 32) e = max(e, exp_of(row[k]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-    if (lane == 0 && e != kNoExp) atomicMax(&row_exp[static_cast<int64_t>(brow[leaf]) * b + r], e);
+    if (lane == 0 && e != kNoExp)
+      atomicMax(&row_exp[static_cast<int64_t>(brow[leaf]) * b + r], e + 1);
   }
 }
 
-// Column exponents of B: thread per (leaf, column).
+// Column exponents of B (frexp exponent + 1): thread per (leaf, column).
 __global__ void k_col_exp(const double *__restrict__ vals, const int32_t *__restrict__ bcol,
                           int64_t nleaves, int b, int *__restrict__ col_exp) {
   const int64_t total = nleaves * b;
@@ -324,7 +343,7 @@ __global__ void k_col_exp(const double *__restrict__ vals, const int32_t *__rest
     const double *col = vals + leaf * b * b + c;
     int e = kNoExp;
     for (int k = 0; k < b; ++k) e = max(e, exp_of(col[static_cast<int64_t>(k) * b]));
-    if (e != kNoExp) atomicMax(&col_exp[static_cast<int64_t>(bcol[leaf]) * b + c], e);
+    if (e != kNoExp) atomicMax(&col_exp[static_cast<int64_t>(bcol[leaf]) * b + c], e + 1);
   }
 }
 
@@ -348,11 +367,10 @@ __global__ void k_split_a(const double *__restrict__ vals, const int32_t *__rest
     for (int k = 0; k < 8; ++k) {
       bool neg;
       const unsigned long long mag = fixed_mag(src[k], e, SA * kW, &neg);
+      int dk[SA];
+      balanced_digits<SA>(mag, neg, dk);
 #pragma unroll
-      for (int i = 0; i < SA; ++i) {
-        const int di = static_cast<int>((mag >> (kW * (SA - 1 - i))) & 0xff);
-        d[i][k] = neg ? -di : di;
-      }
+      for (int i = 0; i < SA; ++i) d[i][k] = dk[i];
     }
     uint8_t *base = out + leaf * SA * TILE + sw128_offset(r, c);
 #pragma unroll
@@ -387,11 +405,10 @@ __global__ void k_split_b(const double *__restrict__ vals, const int32_t *__rest
     for (int k = 0; k < 8; ++k) {
       bool neg;
       const unsigned long long mag = fixed_mag(src[static_cast<int64_t>(k) * B], f, kSB * kW, &neg);
+      int gk[kSB];
+      balanced_digits<kSB>(mag, neg, gk);
 #pragma unroll
-      for (int j = 0; j < kSB; ++j) {
-        const int gj = static_cast<int>((mag >> (kW * (kSB - 1 - j))) & 0xff);
-        g[j][k] = neg ? -gj : gj;
-      }
+      for (int j = 0; j < kSB; ++j) g[j][k] = gk[j];
     }
     uint8_t *base = out + leaf * kSB * TILE + sw128_offset(n, c);
 #pragma unroll

@@ -28,12 +28,28 @@ def test_digits_reconstruct_fixed_point(s, w):
     back = sum(d[i].astype(object) * (1 << (w * (s - 1 - i))) for i in range(s))
     assert np.all(back == ai)
     for di in d:
-        assert np.all(np.abs(di) <= (1 << w) - 1)
-    # truncation toward zero: |x 2^(sw - e) - A_int| < 1 with matching signs
-    scaled = np.ldexp(a, (s * w - e)[:, None])
+        assert np.all(np.abs(di) <= 1 << (w - 1))
+    # rounding to nearest: |x 2^(sw - 1 - e) - A_int| <= 1/2, signs agree,
+    # and |A_int| <= 2^(sw - 1)
+    scaled = np.ldexp(a, (s * w - 1 - e)[:, None])
     diff = scaled - ai.astype(np.float64)
-    assert np.all(np.abs(diff) < 1.0)
+    assert np.all(np.abs(diff) <= 0.5 * (1 + 1e-15) + np.spacing(np.abs(scaled)))
     assert np.all((ai.astype(np.float64) == 0) | (np.sign(ai.astype(np.float64)) == np.sign(a)))
+    assert all(abs(int(v)) <= 1 << (s * w - 1) for v in ai.ravel())
+
+
+def test_balanced_digits_of_the_extremes():
+    # the largest magnitude 2^(sw - 1) and values around digit boundaries
+    s, w = 3, 8
+    vals = np.array([1 << 23, -(1 << 23), 127, 128, 129, -127, -128, -129, 255, 256,
+                     (1 << 23) - 1, -((1 << 23) - 1), 0], dtype=object)
+    d = sp.digits(vals, s, w)
+    for k, v in enumerate(vals):
+        ds = [int(d[i][k]) for i in range(s)]
+        assert sum(t << (w * (s - 1 - i)) for i, t in enumerate(ds)) == v
+        assert all(abs(t) <= 128 for t in ds)
+    with pytest.raises(AssertionError):
+        sp.digits(np.array([(1 << 23) + (1 << 16)], dtype=object), s, w)
 
 
 def test_digits_are_bfloat16_exact():
