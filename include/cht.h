@@ -252,7 +252,7 @@ int cht_plan_free(cht_plan_t P);
  * reproducible run to run.  No atomics touch C.
  * CHT_SPLIT_BF16: nslices = 0 or 6 (6 digits of 8 bits per operand, 48
  * bits); inputs must be finite; b = 32 or 64.  One work unit sums at most
- * 1016 (b = 64) or 4064 (b = 32) leaf pairs exactly; a C leaf with more is
+ * 1016 (b = 64) or 4000 (b = 32) leaf pairs exactly; a C leaf with more is
  * cut into equal pieces whose sums are added in FP64 in piece order (still
  * reproducible; scratch of one leaf per piece).  The bound returned is
  * relative to 2^(e_r + f_c), the powers of two just above the largest |A|
@@ -319,7 +319,7 @@ int cht_multiply_backward(cht_plan_t plan, cht_mat_t A, cht_mat_t B,
  * allocation, no synchronisation), so it may be captured in a CUDA graph.
  * cht_batch_output gives a non-owning view of C_i (valid while the batch
  * lives; do not free it).  In CHT_SPLIT_BF16 mode every C leaf of every
- * product may have at most 1016 (b = 64) or 4064 (b = 32) leaf pairs (else
+ * product may have at most 1016 (b = 64) or 4000 (b = 32) leaf pairs (else
  * CHT_ERR_UNSUPPORTED from cht_batch_create): a batched launch does not
  * cut long segments into pieces.
  * ---------------------------------------------------------------------- */

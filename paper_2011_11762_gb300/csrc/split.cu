@@ -32,7 +32,9 @@
 // Region 2 (weight <= 2^-32 of the leading diagonal) accumulates over the
 // whole C leaf in FP32 and is read once.  The final value
 //     T = sum_parts (2^8 Q_p + rnd(2^8 (R6 2^-8 + R7 2^-16))) 2^(-8p)
-// is an integer in units of 2^-48 and becomes a double by bit assembly; no
+// is an integer in units of 2^-48 of 2^(e_r + f_c + 2); every part and the
+// sum are at most K (128/255)^2 2^48 < 2^63 for the unit sizes allowed, so
+// the recombination is int64 and the double comes from bit assembly; no
 // FP64 arithmetic is used (FP64 is the slowest unit on GB300).
 //
 // Roles (320 threads): warp 0 = bulk-copy producer, warp 1 = TMEM owner and
@@ -275,22 +277,20 @@ __host__ __device__ inline int sw128_offset(int r, int c) {
   return (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
 }
 
-// v * 2^e2 rounded to nearest-even, from a 128-bit integer, with integer ops.
-__device__ inline double scaled_i128_to_double(__int128 v, int e2) {
+// v * 2^e2 rounded to nearest-even with 64-bit integer operations, |v| < 2^63.
+// Outside the normal range of doubles (never for finite inputs of moderate
+// range) it falls back to a conversion and ldexp.
+__device__ inline double scaled_i64_to_double(long long v, int e2) {
   if (v == 0) return 0.0;
   const unsigned long long sgn = v < 0 ? (1ULL << 63) : 0ULL;
-  const unsigned __int128 m = v < 0 ? static_cast<unsigned __int128>(0) - static_cast<unsigned __int128>(v)
-                                    : static_cast<unsigned __int128>(v);
-  const unsigned long long hi = static_cast<unsigned long long>(m >> 64);
-  const unsigned long long lo = static_cast<unsigned long long>(m);
-  int top = hi ? 127 - __clzll(static_cast<long long>(hi)) : 63 - __clzll(static_cast<long long>(lo));
+  const unsigned long long m = v < 0 ? 0ULL - static_cast<unsigned long long>(v)
+                                     : static_cast<unsigned long long>(v);
+  int top = 63 - __clzll(static_cast<long long>(m));
   unsigned long long mant;
   const int sh = top - 52;
   if (sh > 0) {
-    const unsigned __int128 one = 1;
-    const unsigned __int128 rem = m & ((one << sh) - 1);
-    const unsigned __int128 half = one << (sh - 1);
-    mant = static_cast<unsigned long long>(m >> sh);
+    const unsigned long long rem = m & ((1ULL << sh) - 1ULL), half = 1ULL << (sh - 1);
+    mant = m >> sh;
     if (rem > half || (rem == half && (mant & 1ULL))) {
       ++mant;
       if (mant >> 53) {
@@ -299,13 +299,10 @@ __device__ inline double scaled_i128_to_double(__int128 v, int e2) {
       }
     }
   } else {
-    mant = lo << (-sh);
+    mant = m << (-sh);
   }
   const int biased = top + e2 + 1023;
-  if (biased <= 0 || biased >= 2047) {  // outside the normal range: rare path
-    const double hd = ldexp(static_cast<double>(hi), 64 + e2) + ldexp(static_cast<double>(lo), e2);
-    return sgn ? -hd : hd;
-  }
+  if (biased <= 0 || biased >= 2047) return ldexp(static_cast<double>(v), e2);
   return __longlong_as_double(static_cast<long long>(
       sgn | (static_cast<unsigned long long>(biased) << 52) | (mant & ((1ULL << 52) - 1))));
 }
@@ -639,49 +636,58 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
       return (v + (1LL << (sh - 1))) >> sh;
     };
     if (B == 64) {
-      // part 1 hands its values to part 0, which converts and stores
-      if (part > 0) {
+      // the two parts of an element meet in the exchange buffer: part 0
+      // converts the first half of this thread's columns, part 1 the second,
+      // each handing the other half of its values over (column-major buffer:
+      // a warp's lanes, one row each, hit consecutive words)
+      constexpr int H = E / 2;
+      if (part == 0) {
 #pragma unroll
-        for (int cc = 0; cc < E; ++cc) xb[row * B + c0 + cc] = part_value(cc);
+        for (int cc = 0; cc < H; ++cc) xb[(c0 + H + cc) * B + row] = part_value(H + cc);
+      } else {
+#pragma unroll
+        for (int cc = 0; cc < H; ++cc) xb[(c0 + cc) * B + row] = part_value(cc);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(c.ep_bar);
       if (!wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag)) return false;
       ++epb;
-      if (part == 0) {
-        const int er = sl.rexp[row];
-        double *dst = sl.C + static_cast<int64_t>(row) * B + c0;
+      const int er = sl.rexp[row];
+      const int cb = c0 + (part == 0 ? 0 : H);
+      double *dst = sl.C + static_cast<int64_t>(row) * B + cb;
 #pragma unroll
-        for (int cc = 0; cc < E; cc += 2) {
-          const __int128 t0 = static_cast<__int128>(part_value(cc)) + xb[row * B + c0 + cc];
-          const __int128 t1 = static_cast<__int128>(part_value(cc + 1)) + xb[row * B + c0 + cc + 1];
-          const int f0 = sl.cexp[c0 + cc], f1 = sl.cexp[c0 + cc + 1];
-          double2 out;
-          out.x = (er == kNoExp16 || f0 == kNoExp16) ? 0.0 : scaled_i128_to_double(t0, er + f0 - 48);
-          out.y = (er == kNoExp16 || f1 == kNoExp16) ? 0.0 : scaled_i128_to_double(t1, er + f1 - 48);
-          *reinterpret_cast<double2 *>(dst + cc) = out;
-        }
+      for (int cc = 0; cc < H; cc += 2) {
+        const long long v0 = part == 0 ? part_value(cc) : part_value(H + cc);
+        const long long v1 = part == 0 ? part_value(cc + 1) : part_value(H + cc + 1);
+        const long long t0 = v0 + xb[(cb + cc) * B + row];
+        const long long t1 = v1 + xb[(cb + cc + 1) * B + row];
+        const int f0 = sl.cexp[cb + cc], f1 = sl.cexp[cb + cc + 1];
+        double2 out;
+        out.x = (er == kNoExp16 || f0 == kNoExp16) ? 0.0 : scaled_i64_to_double(t0, er + f0 - 48);
+        out.y = (er == kNoExp16 || f1 == kNoExp16) ? 0.0 : scaled_i64_to_double(t1, er + f1 - 48);
+        *reinterpret_cast<double2 *>(dst + cc) = out;
       }
     } else {
       // every part into the buffer, then all 256 threads convert 4 elements
+      // column-major per part (lanes = rows: no bank conflicts)
 #pragma unroll
       for (int cc = 0; cc < E; ++cc)
-        xb[(static_cast<int64_t>(part) * B + row) * B + c0 + cc] = part_value(cc);
+        xb[(static_cast<int64_t>(part) * B + c0 + cc) * B + row] = part_value(cc);
       __syncwarp();
       if (lane == 0) mbar_arrive(c.ep_bar);
       if (!wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag)) return false;
       ++epb;
-      const int e0 = (threadIdx.x - 64) * 4;  // epilogue thread index * 4
-      const int r = e0 / B, col = e0 % B;
+      const int et = threadIdx.x - 64;  // epilogue thread index
+      const int r = et % B, col = (et / B) * 4;
       const int er = sl.rexp[r];
       double o4[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        __int128 t = 0;
+        long long t = 0;
 #pragma unroll
-        for (int p = 0; p < PARTS; ++p) t += xb[(static_cast<int64_t>(p) * B + r) * B + col + j];
+        for (int p = 0; p < PARTS; ++p) t += xb[(static_cast<int64_t>(p) * B + col + j) * B + r];
         const int f = sl.cexp[col + j];
-        o4[j] = (er == kNoExp16 || f == kNoExp16) ? 0.0 : scaled_i128_to_double(t, er + f - 48);
+        o4[j] = (er == kNoExp16 || f == kNoExp16) ? 0.0 : scaled_i64_to_double(t, er + f - 48);
       }
       double *dst = sl.C + static_cast<int64_t>(r) * B + col;
       *reinterpret_cast<double2 *>(dst) = make_double2(o4[0], o4[1]);
@@ -1025,7 +1031,10 @@ int launch_split(const SplitProd &single, const SplitProd *prods, const int64_t 
 
 // The parts handed between epilogue warps hold (windows * 2^56) in 64 bits,
 // so one unit sums at most 127 windows of leaf pairs.
-int max_unit_pairs(int b) { return 127 * (b == 64 ? Cfg<64>::WINDOW : Cfg<32>::WINDOW); }
+// The final sum of a C element, in units of 2^-48 of 2^(e_r + f_c + 2), is at
+// most K * (128/255)^2 * 2^48 with K = b * pairs, so it stays below 2^63 in
+// int64 for K <= 65024 (b = 64) and K <= 128000 (b = 32).
+int max_unit_pairs(int b) { return b == 64 ? 127 * Cfg<64>::WINDOW : 4000; }
 
 int check_segments(const cht_plan *plan) {
   if (plan->max_seg > max_unit_pairs(plan->b)) {

@@ -153,7 +153,7 @@ def test_split_timeout_path(lib):
 @pytest.mark.parametrize("b,g", [(64, 1100), (64, 2100), (32, 4100)])
 def test_split_long_segments_are_cut_into_pieces(lib, b, g):
     # leaf (0, 0) of A*B sums g leaf pairs, more than one unit of the split
-    # kernel sums (1016 at b = 64, 4064 at b = 32): it is computed in pieces
+    # kernel sums (1016 at b = 64, 4000 at b = 32): it is computed in pieces
     a, bm = w.dense_line_pair(g * b, b, 1, 91)
     A, B = gu.upload(lib, a), gu.upload(lib, bm)
     plan = lib.cht_symbolic_multiply(A, B)
