@@ -529,6 +529,26 @@ def section_purify(args, world, cht, torch):
                 float(num / torch.linalg.norm(Xf.values().reshape(-1)))
                 if num is not None else "patterns differ")
         out[name] = steps
+    # the addition and the truncation alone, on the step's own operands:
+    # bytes = leaves read + leaves written (8 b^2 each), over the call's time
+    # (which includes their union / sort and selection work)
+    p1 = cht.cht_symbolic_multiply_symsquare(X0)
+    x2u, _ = cht.cht_multiply(p1, X0, X0, mode=cht.CHT_SPLIT_BF16)
+    x2 = cht.cht_mat_mirror_upper(x2u)
+    p2 = cht.cht_symbolic_multiply_upper(x2, X0)
+    x3u, _ = cht.cht_multiply(p2, x2, X0, mode=cht.CHT_SPLIT_BF16)
+    del p1, p2, x2
+    leaf_bytes = 8 * x2u.b * x2u.b
+    yu = cht.cht_add(3.0, x2u, -2.0, x3u)
+    ms_add = _time_steps(torch, stream, lambda: cht.cht_add(3.0, x2u, -2.0, x3u), 3, 1)
+    tu, _ = cht.cht_truncate(yu, eps / math.sqrt(2.0))
+    ms_tr = _time_steps(torch, stream, lambda: cht.cht_truncate(yu, eps / math.sqrt(2.0)), 3, 1)
+    add_bytes = (x2u.nblocks + x3u.nblocks + yu.nblocks) * leaf_bytes
+    tr_bytes = (yu.nblocks + 2 * tu.nblocks) * leaf_bytes
+    out["add"] = {"ms": ms_add, "bytes": add_bytes, "GB/s": add_bytes / (ms_add * 1e-3) / 1e9,
+                  "leaves_in": [x2u.nblocks, x3u.nblocks], "leaves_out": yu.nblocks}
+    out["truncate"] = {"ms": ms_tr, "bytes": tr_bytes, "GB/s": tr_bytes / (ms_tr * 1e-3) / 1e9,
+                       "leaves_in": yu.nblocks, "leaves_out": tu.nblocks}
     cht.sync_status()
     return out
 

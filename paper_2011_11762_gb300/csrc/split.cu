@@ -67,21 +67,31 @@ template <>
 struct Cfg<64> {
   // N is the MMA width: two B slices side by side (2 b columns)
   static constexpr int N = 128, PARTS = 2, SA = 6, KSTEPS = 4, STAGES = 2, WINDOW = 8;
-  static constexpr int NBLK = 6;
   static constexpr int TMEM_COLS = 512;
 };
 template <>
 struct Cfg<32> {
   static constexpr int N = 64, PARTS = 4, SA = 8, KSTEPS = 2, STAGES = 3, WINDOW = 32;
-  static constexpr int NBLK = 4;
   static constexpr int TMEM_COLS = 256;
 };
 
 // MMA blocks (first stacked A slice u, first B slice j; both odd), 1-based.
 // Block (u, j) computes A_{u+p} B_{j+q} for every part p and q in {0, 1}
 // into TMEM region (u + j - 2) / 2.
-__constant__ int8_t c_blk64[6][2] = {{1, 1}, {1, 3}, {3, 1}, {1, 5}, {3, 3}, {5, 1}};
-__constant__ int8_t c_blk32[4][2] = {{1, 1}, {1, 3}, {1, 5}, {5, 1}};
+template <int B>
+struct Blocks;
+template <>
+struct Blocks<64> {
+  static constexpr int NBLK = 6;  // (1,1) (1,3) (3,1) (1,5) (3,3) (5,1)
+  __device__ static constexpr int u(int i) { return i <= 1 || i == 3 ? 1 : i == 5 ? 5 : 3; }
+  __device__ static constexpr int j(int i) { return i == 0 || i == 2 || i == 5 ? 1 : i == 3 ? 5 : 3; }
+};
+template <>
+struct Blocks<32> {
+  static constexpr int NBLK = 4;  // (1,1) (1,3) (1,5) (5,1)
+  __device__ static constexpr int u(int i) { return i == 3 ? 5 : 1; }
+  __device__ static constexpr int j(int i) { return i == 0 || i == 3 ? 1 : i == 1 ? 3 : 5; }
+};
 
 template <int B>
 struct Smem {
@@ -490,22 +500,50 @@ __device__ inline int16_t exp16(int e) {
   return e == kNoExp ? kNoExp16 : static_cast<int16_t>(max(-32000, min(32000, e)));
 }
 
-// MMA issuer: all slice-product blocks of one C leaf, window by window.
-template <int B, int S>
-__device__ bool mma_unit(int64_t np, uint32_t &k, uint32_t &win, const Ctl &c) {
+// The MMA blocks of one leaf pair from stage (sa: A slices, sb: B slices).
+// which = 0: all blocks; 1: the blocks of region 2 only; 2: regions 0, 1.
+template <int B>
+__device__ __forceinline__ void issue_blocks(uint32_t sa, uint32_t sb, uint32_t tmem,
+                                             bool (&fresh)[kRegions], int which) {
   using CF = Cfg<B>;
   using SM = Smem<B>;
   constexpr int N = CF::N;
   constexpr uint32_t IDESC = make_idesc(128, N);
+#pragma unroll
+  for (int bi = 0; bi < Blocks<B>::NBLK; ++bi) {
+    const int bu = Blocks<B>::u(bi), bj = Blocks<B>::j(bi);
+    const int r = (bu + bj - 2) >> 1;  // region 0..2
+    if ((which == 1 && r != 2) || (which == 2 && r == 2)) continue;
+    const uint64_t ad = sw128_desc(sa + (bu - 1) * SM::TILE);
+    const uint64_t bd = sw128_desc(sb + (bj - 1) * SM::TILE);  // slices j, j+1
+    const uint32_t dt = tmem + static_cast<uint32_t>(r * N);
+#pragma unroll
+    for (int kk = 0; kk < CF::KSTEPS; ++kk) {
+      const uint32_t acc = (fresh[r] && kk == 0) ? 0u : 1u;
+      tc_mma(dt, ad + 2 * kk, bd + 2 * kk, IDESC, acc);
+    }
+    fresh[r] = false;
+  }
+}
+
+// MMA issuer: all slice-product blocks of one C leaf, window by window.
+// Region 2 is not read between windows, so from the second window of a unit
+// on, the first pair's region-2 blocks go out before the wait for the
+// epilogue to release the exact regions: they cover that hand-off.
+template <int B, int S>
+__device__ bool mma_unit(int64_t np, uint32_t &k, uint32_t &win, const Ctl &c) {
+  using CF = Cfg<B>;
+  using SM = Smem<B>;
   bool fresh[kRegions];
 #pragma unroll
   for (int r = 0; r < kRegions; ++r) fresh[r] = true;
   for (int64_t w0 = 0; w0 < np; w0 += CF::WINDOW, ++win) {
-    // the epilogue must have read the regions of the previous window
-    if (!wait_or_abort(c.acc_empty, (win & 1u) ^ 1u, c.wait_ns, c.abort_flag)) return false;
-    tc_fence_after();
-#pragma unroll
-    for (int r = 0; r < kExactRegions; ++r) fresh[r] = true;
+    const bool ahead = w0 != 0;
+    if (!ahead) {
+      // the epilogue must have read every region of the previous unit
+      if (!wait_or_abort(c.acc_empty, (win & 1u) ^ 1u, c.wait_ns, c.abort_flag)) return false;
+      tc_fence_after();
+    }
     const int64_t w1 = min(np, w0 + CF::WINDOW);
     for (int64_t i = w0; i < w1; ++i, ++k) {
       const uint32_t st = k % S, ph = (k / S) & 1u;
@@ -513,20 +551,18 @@ __device__ bool mma_unit(int64_t np, uint32_t &k, uint32_t &win, const Ctl &c) {
       tc_fence_after();
       const uint32_t sa = smem_addr(c.stage_base + st * c.stage_bytes);
       const uint32_t sb = sa + SM::A_BYTES;
-#pragma unroll
-      for (int bi = 0; bi < CF::NBLK; ++bi) {
-        const int bu = (B == 64) ? c_blk64[bi][0] : c_blk32[bi][0];
-        const int bj = (B == 64) ? c_blk64[bi][1] : c_blk32[bi][1];
-        const int r = (bu + bj - 2) >> 1;  // region 0..2
-        const uint64_t ad = sw128_desc(sa + (bu - 1) * SM::TILE);
-        const uint64_t bd = sw128_desc(sb + (bj - 1) * SM::TILE);  // slices j, j+1
-        const uint32_t dt = c.tmem + static_cast<uint32_t>(r * N);
-#pragma unroll
-        for (int kk = 0; kk < CF::KSTEPS; ++kk) {
-          const uint32_t acc = (fresh[r] && kk == 0) ? 0u : 1u;
-          tc_mma(dt, ad + 2 * kk, bd + 2 * kk, IDESC, acc);
+      if (i == w0) {
+        if (ahead) {
+          issue_blocks<B>(sa, sb, c.tmem, fresh, 1);
+          // the epilogue must have read the exact regions of the last window
+          if (!wait_or_abort(c.acc_empty, (win & 1u) ^ 1u, c.wait_ns, c.abort_flag)) return false;
+          tc_fence_after();
         }
-        fresh[r] = false;
+#pragma unroll
+        for (int r = 0; r < kExactRegions; ++r) fresh[r] = true;
+        issue_blocks<B>(sa, sb, c.tmem, fresh, ahead ? 2 : 0);
+      } else {
+        issue_blocks<B>(sa, sb, c.tmem, fresh, 0);
       }
       tc_commit(&c.empty[st]);  // frees the stage when these MMAs finish
     }
