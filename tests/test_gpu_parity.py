@@ -248,3 +248,24 @@ def test_full_size_3d_locality_sampled(lib):
         assert present
         got = vals[c].cpu().numpy()
         assert setref.rel_fro(got, ref) <= FP64_TOL
+
+
+def test_dense_torch_cross_check(lib):
+    # the whole product against a dense FP64 matmul (cuBLAS) of the densified
+    # operands: N = 8192, 3D locality
+    torch = pytest.importorskip("torch")
+    a, b = w.config2(8192)
+    A, B = gu.upload(lib, a), gu.upload(lib, b)
+    plan = lib.cht_symbolic_multiply(A, B)
+    C, _ = lib.cht_multiply(plan, A, B, sync=True)
+    ref = torch.matmul(A.to_dense(), B.to_dense())
+    got = C.to_dense()
+    rel = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
+    assert rel <= FP64_TOL, rel
+    # outside C's pattern the dense product is exactly zero
+    crow, ccol = (t.long() for t in C.coords())
+    mask = torch.zeros((a.grid, a.grid), dtype=torch.bool, device="cuda")
+    mask[crow, ccol] = True
+    full = torch.kron(mask.to(torch.float64), torch.ones((a.b, a.b), dtype=torch.float64,
+                                                         device="cuda")) != 0
+    assert not bool(ref[~full].any())
