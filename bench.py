@@ -835,6 +835,10 @@ def main():
     a, b = res.pop("host")
     fp64_peak_meas = max(cht.measure_fp64_peak(1), cht.measure_fp64_peak(0))
 
+    e2e = None
+    if not args.no_e2e:
+        e2e = fp64_e2e(args, world, cht, torch, a, b)
+
     extra = {}
     sections = [s for s in args.sections.split(",") if s and s != "none"]
     for sec in sections:
@@ -847,9 +851,6 @@ def main():
         except Exception as e:  # report, do not hide the headline
             extra[sec] = {"status": "error", "error": f"{type(e).__name__}: {e}"}
 
-    e2e = None
-    if not args.no_e2e:
-        e2e = fp64_e2e(args, world, cht, torch, a, b)
 
     cpu = None
     cpu_blas = None

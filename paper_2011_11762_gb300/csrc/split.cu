@@ -573,7 +573,7 @@ __device__ bool mma_unit(int64_t np, uint32_t &k, uint32_t &win, const Ctl &c) {
 
 // Epilogue (one of 8 warps): exact windows into int64, final recombination
 // and the FP64 store of one C leaf.  `xb` is this unit's exchange buffer.
-template <int B>
+template <int B, bool SINGLE_FAST>
 __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *xb,
                          const Ctl &c) {
   using CF = Cfg<B>;
@@ -611,32 +611,45 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
       __syncwarp();
       if (lane == 0) mbar_arrive(c.acc_empty);  // the MMA may go on
     }
+    long long Q[E];
+    // a one-window unit needs no int64 round trip through TMEM (used where
+    // the extra live int64 values do not spill: the 32-leaf-only kernel)
+    const bool single = SINGLE_FAST && first && last;
+    if (single) {
 #pragma unroll
-    for (int ch = 0; ch < E / 8; ++ch) {
-      uint32_t qw[16];
-      if (first) {
+      for (int cc = 0; cc < E; ++cc)
+        Q[cc] = (static_cast<long long>(__float2int_rn(ex[0][cc])) << 24) +
+                (static_cast<long long>(__float2int_rn(ex[1][cc])) << 16) +
+                (static_cast<long long>(__float2int_rn(ex[2][cc])) << 8) +
+                static_cast<long long>(__float2int_rn(ex[3][cc]));
+    } else {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) qw[i] = 0;
-      } else {
-        tmem_ld16u(qbase + 16 * ch, qw);
-        tc_wait_ld();
+      for (int ch = 0; ch < E / 8; ++ch) {
+        uint32_t qw[16];
+        if (first) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) qw[i] = 0;
+        } else {
+          tmem_ld16u(qbase + 16 * ch, qw);
+          tc_wait_ld();
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int cc = ch * 8 + e;
+          long long qv = static_cast<long long>(
+              (static_cast<unsigned long long>(qw[2 * e + 1]) << 32) | qw[2 * e]);
+          qv += (static_cast<long long>(__float2int_rn(ex[0][cc])) << 24) +
+                (static_cast<long long>(__float2int_rn(ex[1][cc])) << 16) +
+                (static_cast<long long>(__float2int_rn(ex[2][cc])) << 8) +
+                static_cast<long long>(__float2int_rn(ex[3][cc]));
+          qw[2 * e] = static_cast<uint32_t>(qv);
+          qw[2 * e + 1] = static_cast<uint32_t>(static_cast<unsigned long long>(qv) >> 32);
+        }
+        tmem_st16u(qbase + 16 * ch, qw);
       }
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int cc = ch * 8 + e;
-        long long qv = static_cast<long long>((static_cast<unsigned long long>(qw[2 * e + 1]) << 32) |
-                                              qw[2 * e]);
-        qv += (static_cast<long long>(__float2int_rn(ex[0][cc])) << 24) +
-              (static_cast<long long>(__float2int_rn(ex[1][cc])) << 16) +
-              (static_cast<long long>(__float2int_rn(ex[2][cc])) << 8) +
-              static_cast<long long>(__float2int_rn(ex[3][cc]));
-        qw[2 * e] = static_cast<uint32_t>(qv);
-        qw[2 * e + 1] = static_cast<uint32_t>(static_cast<unsigned long long>(qv) >> 32);
-      }
-      tmem_st16u(qbase + 16 * ch, qw);
+      tc_wait_st();
+      if (!last) continue;
     }
-    tc_wait_st();
-    if (!last) continue;
     {
       float v[E];
       tmem_ld<E>(lane_base + static_cast<uint32_t>(2 * N + c0), v);
@@ -648,16 +661,17 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
 #pragma unroll
       for (int cc = 0; cc < E; ++cc) rl[cc] = fmaf(v[cc], 0x1p-16f, rl[cc]);
     }
-    long long Q[E];
+    if (!single) {
 #pragma unroll
-    for (int ch = 0; ch < E / 8; ++ch) {
-      uint32_t qw[16];
-      tmem_ld16u(qbase + 16 * ch, qw);
-      tc_wait_ld();
+      for (int ch = 0; ch < E / 8; ++ch) {
+        uint32_t qw[16];
+        tmem_ld16u(qbase + 16 * ch, qw);
+        tc_wait_ld();
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
-        Q[ch * 8 + e] = static_cast<long long>(
-            (static_cast<unsigned long long>(qw[2 * e + 1]) << 32) | qw[2 * e]);
+        for (int e = 0; e < 8; ++e)
+          Q[ch * 8 + e] = static_cast<long long>(
+              (static_cast<unsigned long long>(qw[2 * e + 1]) << 32) | qw[2 * e]);
+      }
     }
     tc_fence_before();
     __syncwarp();
@@ -946,9 +960,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       int64_t *xb = c.xbuf + (KC::NXB == 2 ? (n & 1u) * (KC::XBUF / 8) : 0);
       bool ok;
       if constexpr (MAXB == 64)
-        ok = b == 64 ? epi_unit<64>(sl, win, epb, xb, c) : epi_unit<32>(sl, win, epb, xb, c);
+        ok = b == 64 ? epi_unit<64, false>(sl, win, epb, xb, c)
+                     : epi_unit<32, false>(sl, win, epb, xb, c);
       else
-        ok = epi_unit<32>(sl, win, epb, xb, c);
+        ok = epi_unit<32, true>(sl, win, epb, xb, c);
       if (!ok) {
         fail();
         break;
