@@ -319,23 +319,31 @@ __device__ inline double scaled_i64_to_double(long long v, int e2) {
 
 // ------------------------------------------------------------ pre-kernels --
 
-// Row exponents of A (stored as frexp exponent + 1): warp per (leaf, row).
+// Row exponents of A (stored as frexp exponent + 1): B/16 consecutive
+// threads per (leaf, row), 16 consecutive values (eight 16-byte loads) each.
+template <int B>
 __global__ void k_row_exp(const double *__restrict__ vals, const int32_t *__restrict__ brow,
-                          int64_t nleaves, int b, int *__restrict__ row_exp) {
-  const int lane = threadIdx.x & 31;
-  const int64_t total = nleaves * b;
-  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t w = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5; w < total;
-       w += warps) {
-    const int64_t leaf = w / b;
-    const int r = static_cast<int>(w % b);
-    const double *row = vals + leaf * b * b + static_cast<int64_t>(r) * b;
+                          int64_t nleaves, int *__restrict__ row_exp) {
+  constexpr int TPR = B / 16;  // threads per row (a power of two dividing 32)
+  const int64_t total = nleaves * B * TPR;
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t leaf = t / (B * TPR);
+    const int r = static_cast<int>((t / TPR) % B), part = static_cast<int>(t % TPR);
+    const double2 *src =
+        reinterpret_cast<const double2 *>(vals + leaf * B * B + static_cast<int64_t>(r) * B + part * 16);
     int e = kNoExp;
-    for (int k = lane; k < b; k += 32) e = max(e, exp_of(row[k]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-    if (lane == 0 && e != kNoExp)
-      atomicMax(&row_exp[static_cast<int64_t>(brow[leaf]) * b + r], e + 1);
+    for (int k = 0; k < 8; ++k) {
+      const double2 v = src[k];
+      e = max(e, max(exp_of(v.x), exp_of(v.y)));
+    }
+    // the row's threads are consecutive lanes of one warp (total is a
+    // multiple of 32, so every lane of a live warp takes part)
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if (part == 0 && e != kNoExp)
+      atomicMax(&row_exp[static_cast<int64_t>(brow[leaf]) * B + r], e + 1);
   }
 }
 
@@ -368,12 +376,20 @@ __global__ void k_split_a(const double *__restrict__ vals, const int32_t *__rest
     const int64_t leaf = t / (B * CH);
     const int r = static_cast<int>((t / CH) % B), c = static_cast<int>(t % CH);
     const int e = row_exp[static_cast<int64_t>(brow[leaf]) * B + r];
-    const double *src = vals + leaf * B * B + static_cast<int64_t>(r) * B + c * 8;
+    const double2 *src =
+        reinterpret_cast<const double2 *>(vals + leaf * B * B + static_cast<int64_t>(r) * B + c * 8);
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double2 v = src[k];
+      x[2 * k] = v.x;
+      x[2 * k + 1] = v.y;
+    }
     int d[SA][8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       bool neg;
-      const unsigned long long mag = fixed_mag(src[k], e, SA * kW, &neg);
+      const unsigned long long mag = fixed_mag(x[k], e, SA * kW, &neg);
       int dk[SA];
       balanced_digits<SA>(mag, neg, dk);
 #pragma unroll
@@ -392,41 +408,54 @@ __global__ void k_split_a(const double *__restrict__ vals, const int32_t *__rest
   }
 }
 
-// B slices, stored transposed (tile row n = column n of the leaf, K-major):
-// thread per (leaf, column n, chunk c of 8 K values).
+// B slices, stored transposed (tile row n = column n of the leaf, K-major).
+// One block per leaf: the leaf is staged in shared memory with contiguous
+// 16-byte loads, then thread (column n, chunk c of 8 K values) reads its
+// column from shared memory (consecutive threads: consecutive columns, no
+// bank conflicts) and writes its 16-byte chunk of every digit plane.
 template <int B>
-__global__ void k_split_b(const double *__restrict__ vals, const int32_t *__restrict__ bcol,
-                          int64_t nleaves, const int *__restrict__ col_exp,
-                          uint8_t *__restrict__ out) {
+__global__ void __launch_bounds__(256) k_split_b(const double *__restrict__ vals,
+                                                 const int32_t *__restrict__ bcol,
+                                                 int64_t nleaves, const int *__restrict__ col_exp,
+                                                 uint8_t *__restrict__ out) {
   constexpr int CH = B / 8;
   constexpr int TILE = B * 128;
-  const int64_t total = nleaves * CH * B;
-  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
-       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t leaf = t / (CH * B);
-    const int c = static_cast<int>((t / B) % CH), n = static_cast<int>(t % B);
-    const int f = col_exp[static_cast<int64_t>(bcol[leaf]) * B + n];
-    const double *src = vals + leaf * B * B + static_cast<int64_t>(c * 8) * B + n;
-    int g[kSB][8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      bool neg;
-      const unsigned long long mag = fixed_mag(src[static_cast<int64_t>(k) * B], f, kSB * kW, &neg);
-      int gk[kSB];
-      balanced_digits<kSB>(mag, neg, gk);
-#pragma unroll
-      for (int j = 0; j < kSB; ++j) g[j][k] = gk[j];
+  __shared__ double tile[B][B + 1];
+  for (int64_t leaf = blockIdx.x; leaf < nleaves; leaf += gridDim.x) {
+    const double2 *src = reinterpret_cast<const double2 *>(vals + leaf * B * B);
+    for (int i = threadIdx.x; i < B * B / 2; i += blockDim.x) {
+      const double2 v = src[i];
+      const int e = 2 * i;
+      tile[e / B][e % B] = v.x;
+      tile[e / B][e % B + 1] = v.y;
     }
-    uint8_t *base = out + leaf * kSB * TILE + sw128_offset(n, c);
+    __syncthreads();
+    const int64_t col0 = static_cast<int64_t>(bcol[leaf]) * B;
+    for (int q = threadIdx.x; q < B * CH; q += blockDim.x) {
+      const int n = q % B, c = q / B;
+      const int f = col_exp[col0 + n];
+      int g[kSB][8];
 #pragma unroll
-    for (int j = 0; j < kSB; ++j) {
-      uint4 v;
-      v.x = pack_bf16x2(g[j][0], g[j][1]);
-      v.y = pack_bf16x2(g[j][2], g[j][3]);
-      v.z = pack_bf16x2(g[j][4], g[j][5]);
-      v.w = pack_bf16x2(g[j][6], g[j][7]);
-      *reinterpret_cast<uint4 *>(base + j * TILE) = v;
+      for (int k = 0; k < 8; ++k) {
+        bool neg;
+        const unsigned long long mag = fixed_mag(tile[c * 8 + k][n], f, kSB * kW, &neg);
+        int gk[kSB];
+        balanced_digits<kSB>(mag, neg, gk);
+#pragma unroll
+        for (int j = 0; j < kSB; ++j) g[j][k] = gk[j];
+      }
+      uint8_t *base = out + leaf * kSB * TILE + sw128_offset(n, c);
+#pragma unroll
+      for (int j = 0; j < kSB; ++j) {
+        uint4 v;
+        v.x = pack_bf16x2(g[j][0], g[j][1]);
+        v.y = pack_bf16x2(g[j][2], g[j][3]);
+        v.z = pack_bf16x2(g[j][4], g[j][5]);
+        v.w = pack_bf16x2(g[j][6], g[j][7]);
+        *reinterpret_cast<uint4 *>(base + j * TILE) = v;
+      }
     }
+    __syncthreads();
   }
 }
 
@@ -1024,8 +1053,8 @@ int split_operands(const cht_mat *A, const cht_mat *Bm, cudaStream_t s, Operands
   const double *av = const_cast<cht_mat *>(A)->values();
   const double *bv = const_cast<cht_mat *>(Bm)->values();
   if (pa.nnz > 0) {
-    k_row_exp<<<grid_for(pa.nnz * B * 32, 256), 256, 0, s>>>(av, pa.brow.p, pa.nnz, B,
-                                                             op.row_exp.p);
+    k_row_exp<B><<<grid_for(pa.nnz * B * (B / 16), 256), 256, 0, s>>>(av, pa.brow.p, pa.nnz,
+                                                                      op.row_exp.p);
     CHT_TRY(launched("row_exp"));
   }
   if (pb.nnz > 0) {
@@ -1038,8 +1067,11 @@ int split_operands(const cht_mat *A, const cht_mat *Bm, cudaStream_t s, Operands
     CHT_TRY(launched("split_a"));
   }
   if (pb.nnz > 0) {
-    k_split_b<B><<<grid_for(pb.nnz * B * (B / 8), 256), 256, 0, s>>>(bv, pb.bcol.p, pb.nnz,
-                                                                   op.col_exp.p, op.b_sl.p);
+    int sms = 0;
+    CHT_TRY(num_sms(&sms));
+    const int64_t nblk = std::min<int64_t>(pb.nnz, static_cast<int64_t>(sms) * 8);
+    k_split_b<B><<<static_cast<unsigned>(nblk), 256, 0, s>>>(bv, pb.bcol.p, pb.nnz, op.col_exp.p,
+                                                              op.b_sl.p);
     CHT_TRY(launched("split_b"));
   }
   return CHT_OK;
