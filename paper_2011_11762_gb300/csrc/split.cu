@@ -40,8 +40,10 @@
 // Roles (320 threads): warp 0 = bulk-copy producer, warp 1 = TMEM owner and
 // MMA issuer (one thread), warps 2..9 = epilogue (two warps per TMEM lane
 // quarter, splitting the columns).  Units are the C leaves in Morton order,
-// dealt round-robin to the persistent CTAs (neighbouring leaves run together,
-// so their A and B slices are shared through L2).  Every wait is bounded.
+// taken two at a time from an atomic counter by the persistent CTAs
+// (neighbouring leaves run together, so their A and B slices are shared
+// through L2).  A C leaf with more pairs than a unit may sum is cut into
+// pieces added afterwards in FP64.  Every wait is bounded.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -1112,11 +1114,10 @@ int launch_split(const SplitProd &single, const SplitProd *prods, const int64_t 
   return launched("split_gemm");
 }
 
-// The parts handed between epilogue warps hold (windows * 2^56) in 64 bits,
-// so one unit sums at most 127 windows of leaf pairs.
-// The final sum of a C element, in units of 2^-48 of 2^(e_r + f_c + 2), is at
-// most K * (128/255)^2 * 2^48 with K = b * pairs, so it stays below 2^63 in
-// int64 for K <= 65024 (b = 64) and K <= 128000 (b = 32).
+// Pairs one unit may sum.  Every window adds at most 2^24 * 2^32 to an int64
+// part (127 windows fit), and the final sum of a C element, in units of 2^-48
+// of 2^(e_r + f_c + 2), is at most K * (128/255)^2 * 2^48 with K = b * pairs,
+// so it stays below 2^63 for K <= 65024 (b = 64) and K <= 128000 (b = 32).
 int max_unit_pairs(int b) { return b == 64 ? 127 * Cfg<64>::WINDOW : 4000; }
 
 int check_segments(const cht_plan *plan) {
