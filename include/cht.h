@@ -318,10 +318,10 @@ int cht_multiply_backward(cht_plan_t plan, cht_mat_t A, cht_mat_t B,
  * launch tables (and may synchronise); cht_batch_run only launches (no
  * allocation, no synchronisation), so it may be captured in a CUDA graph.
  * cht_batch_output gives a non-owning view of C_i (valid while the batch
- * lives; do not free it).  In CHT_SPLIT_BF16 mode every C leaf of every
- * product may have at most 1016 (b = 64) or 4000 (b = 32) leaf pairs (else
- * CHT_ERR_UNSUPPORTED from cht_batch_create): a batched launch does not
- * cut long segments into pieces.
+ * lives; do not free it).  In CHT_SPLIT_BF16 mode a C leaf with more leaf
+ * pairs than one unit sums (1016 at b = 64, 4000 at b = 32) is cut into
+ * pieces as in cht_multiply; cht_batch_create prepares them (scratch of one
+ * leaf per piece) and cht_batch_run adds them after the launch.
  * ---------------------------------------------------------------------- */
 int cht_batch_create(int32_t count, const cht_plan_t *plans,
                      const cht_mat_t *As, const cht_mat_t *Bs, int mode,

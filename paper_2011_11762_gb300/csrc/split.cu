@@ -1120,15 +1120,6 @@ int launch_split(const SplitProd &single, const SplitProd *prods, const int64_t 
 // so it stays below 2^63 for K <= 65024 (b = 64) and K <= 128000 (b = 32).
 int max_unit_pairs(int b) { return b == 64 ? 127 * Cfg<64>::WINDOW : 4000; }
 
-int check_segments(const cht_plan *plan) {
-  if (plan->max_seg > max_unit_pairs(plan->b)) {
-    set_error("split form (batched): a C leaf has %lld leaf pairs (at most %d); use CHT_FP64",
-              (long long)plan->max_seg, max_unit_pairs(plan->b));
-    return CHT_ERR_UNSUPPORTED;
-  }
-  return CHT_OK;
-}
-
 // Long segments: a C leaf with more pairs than one unit may sum is cut into
 // np = ceil(len / maxp) pieces of ceil(len / np) pairs; each piece is a unit
 // whose exact split-form sum goes to a scratch leaf, and the pieces are then
@@ -1218,8 +1209,20 @@ int make_pieces(const cht_plan *plan, double *Cvals, cudaStream_t s, PieceUnits 
   return launched("piece_fill");
 }
 
+// Units (product << 32 | unit) of one product, in order.
+__global__ void k_pack_units(int64_t n, int64_t prod, int64_t off, int64_t *__restrict__ units) {
+  for (int64_t u = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; u < n;
+       u += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    units[off + u] = (prod << 32) | u;
+}
+
 struct SplitBatch {
   std::vector<Operands> ops;
+  std::vector<PieceUnits> pieces;  // per product; used where has_pieces
+  std::vector<char> has_pieces;
+  DevArray<int64_t> units;         // the piece-aware unit list (when any product has pieces)
+  int64_t nunits = 0;
+  bool own_units = false;
   DevArray<SplitProd> prods;
   DevArray<unsigned long long> counter;
   int maxb = 32;
@@ -1282,11 +1285,47 @@ int split_batch_prepare(cht_batch *bt, cudaStream_t s) {
   auto sb = std::make_unique<SplitBatch>();
   std::vector<SplitProd> host(bt->count);
   sb->ops.resize(bt->count);
+  sb->pieces.resize(bt->count);
+  sb->has_pieces.assign(bt->count, 0);
+  bool any = false;
   for (int32_t i = 0; i < bt->count; ++i) {
-    CHT_TRY(check_segments(bt->plans[i]));
+    cht_plan *plan = bt->plans[i];
     CHT_TRY(alloc_operands(*bt->As[i]->pat, *bt->Bs[i]->pat, s, sb->ops[i]));
-    host[i] = make_prod(bt->plans[i], sb->ops[i], bt->views[i]->view_vals);
-    sb->maxb = std::max(sb->maxb, static_cast<int>(bt->plans[i]->b));
+    host[i] = make_prod(plan, sb->ops[i], bt->views[i]->view_vals);
+    sb->maxb = std::max(sb->maxb, static_cast<int>(plan->b));
+    if (plan->max_seg > max_unit_pairs(plan->b)) {
+      // long segments: this product's units become pieces (see make_pieces)
+      PieceUnits &pu = sb->pieces[i];
+      CHT_TRY(make_pieces(plan, bt->views[i]->view_vals, s, pu));
+      host[i].cseg = pu.vseg.p;
+      host[i].crow = pu.vrow.p;
+      host[i].ccol = pu.vcol.p;
+      host[i].cptr = pu.vptr.p;
+      sb->has_pieces[i] = 1;
+      any = true;
+    }
+  }
+  if (any) {
+    // the unit list in terms of pieces: every product's units in order
+    int64_t total = 0;
+    for (int32_t i = 0; i < bt->count; ++i)
+      total += sb->has_pieces[i] ? sb->pieces[i].nv : bt->plans[i]->C->nnz;
+    if (total > 0x7fffffffLL) {
+      set_error("batch has too many work units");
+      return CHT_ERR_UNSUPPORTED;
+    }
+    CHT_TRY(sb->units.alloc(total, s));
+    int64_t off = 0;
+    for (int32_t i = 0; i < bt->count; ++i) {
+      const int64_t n = sb->has_pieces[i] ? sb->pieces[i].nv : bt->plans[i]->C->nnz;
+      if (n > 0) {
+        k_pack_units<<<grid_for(n, 256), 256, 0, s>>>(n, i, off, sb->units.p);
+        CHT_TRY(launched("pack_units"));
+      }
+      off += n;
+    }
+    sb->nunits = total;
+    sb->own_units = true;
   }
   CHT_TRY(sb->prods.alloc(bt->count, s));
   CHT_TRY(sb->counter.alloc(1, s));
@@ -1306,9 +1345,22 @@ int split_batch_run(cht_batch *bt, cudaStream_t s) {
       CHT_TRY(split_operands<32>(bt->As[i], bt->Bs[i], s, sb->ops[i]));
   }
   const SplitProd none{};
+  const int64_t *units = sb->own_units ? sb->units.p : bt->units.p;
+  const int64_t nunits = sb->own_units ? sb->nunits : bt->nunits;
   if (sb->maxb == 64)
-    return launch_split<64>(none, sb->prods.p, bt->units.p, bt->nunits, sb->counter.p, s);
-  return launch_split<32>(none, sb->prods.p, bt->units.p, bt->nunits, sb->counter.p, s);
+    CHT_TRY(launch_split<64>(none, sb->prods.p, units, nunits, sb->counter.p, s));
+  else
+    CHT_TRY(launch_split<32>(none, sb->prods.p, units, nunits, sb->counter.p, s));
+  for (int32_t i = 0; i < bt->count; ++i) {
+    if (!sb->has_pieces[i]) continue;
+    const cht_plan *plan = bt->plans[i];
+    const int64_t nC = plan->C->nnz;
+    k_piece_reduce<<<static_cast<unsigned>(std::min<int64_t>(nC, 65535LL * 8)), 256, 0, s>>>(
+        sb->pieces[i].npiece.p, sb->pieces[i].tpos.p, nC, sb->pieces[i].scratch.p,
+        plan->b * plan->b, bt->views[i]->view_vals);
+    CHT_TRY(launched("piece_reduce"));
+  }
+  return CHT_OK;
 }
 
 void split_batch_release(cht_batch *bt) {

@@ -118,3 +118,35 @@ def test_reblock_preserves_the_matrix(lib):
     assert np.array_equal(M.to_dense().cpu().numpy(), a.to_dense())
     ref = w.reblock(a, 64)
     assert M.nblocks == ref.nblocks
+
+
+def test_split_batch_with_long_segments(lib):
+    # a product whose leaf (0, 0) sums more pairs than one unit may, batched
+    # with ordinary ones: it is computed in pieces inside the batch, and the
+    # batch (also in a graph replay) equals the single products
+    import torch
+    a1, b1 = w.dense_line_pair(1100 * 64, 64, 1, 93)
+    a2, b2 = w.dense_line_pair(4100 * 32, 32, 1, 95)
+    mats = [(gu.upload(lib, a), gu.upload(lib, b), a, b)
+            for a, b in ((a1, b1), (a2, b2), *[(x[1], x[2]) for x in _products(3)])]
+    plans = [lib.cht_symbolic_multiply(A, B) for A, B, _, _ in mats]
+    bt = lib.Batch(plans, [x[0] for x in mats], [x[1] for x in mats], mode=lib.CHT_SPLIT_BF16)
+    bt.run()
+    lib.sync_status()
+    for i, ((A, B, a, b), plan) in enumerate(zip(mats, plans)):
+        single, _ = lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
+        assert bool((bt.output(i).values() == single.values()).all()), i
+        if i < 2:
+            Co, _ = gu.oracle_product(a, b)
+            gu.assert_values_close(bt.output(i), Co, 1e-11)
+    ref = [bt.output(i).values().clone() for i in range(len(plans))]
+    for i in range(len(plans)):
+        bt.output(i).values().fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bt.run()
+    g.replay()
+    torch.cuda.synchronize()
+    lib.sync_status()
+    for i in range(len(plans)):
+        assert bool((bt.output(i).values() == ref[i]).all()), i
