@@ -263,6 +263,23 @@ int cht_multiply(cht_plan_t plan, cht_mat_t A, cht_mat_t B, int mode,
                  double *max_rel_err_est);
 
 /* ------------------------------------------------------------------------
+ * FP64 numeric multiply straight to host memory: the leaf values of C
+ * (Morton order, the layout of cht_mat_leaves on the plan's pattern, nnzb_C
+ * x b x b doubles) are written to h_C, which the caller owns and should have
+ * allocated page-locked (cudaHostAlloc / pinned) for the copies to overlap.
+ * The C leaves are cut into `nchunks` contiguous ranges; each range is one
+ * launch of the FP64 kernel (longest pair segment first inside the range)
+ * and is copied to h_C on an internal stream while the next range computes,
+ * so the device-to-host transfer hides behind the arithmetic.  Values equal
+ * those of cht_multiply(..., CHT_FP64, ...) bit for bit.  Returns after
+ * enqueuing; `stream` is ordered after the last copy (synchronise it before
+ * reading h_C).  Device scratch: C itself, freed in stream order.
+ * CHT_ERR_INVALID for a NULL h_C or nchunks < 1.
+ * ---------------------------------------------------------------------- */
+int cht_multiply_to_host(cht_plan_t plan, cht_mat_t A, cht_mat_t B, void *stream,
+                         double *h_C, int32_t nchunks);
+
+/* ------------------------------------------------------------------------
  * Allocation-free FP64 numeric multiply.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory on the
  * call path -- for example a serving process that reserves its whole device

@@ -290,6 +290,21 @@ def cht_multiply(plan: Plan, A: Matrix, B: Matrix, mode: int = CHT_FP64, nslices
     return C, (err.value if sync else None)
 
 
+def cht_multiply_to_host(plan: Plan, A: Matrix, B: Matrix, out: torch.Tensor,
+                         nchunks: int = 8, stream=None) -> torch.Tensor:
+    """FP64 C = A*B written into the host tensor `out` (float64, shape
+    [nnzb_C, b, b], ideally pinned) while it is computed; the stream is
+    ordered after the last copy."""
+    if out.device.type != "cpu" or out.dtype != torch.float64 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 host tensor")
+    if out.numel() != plan.nnzb_C * A.b * A.b:
+        raise ValueError("out must hold nnzb_C * b * b values")
+    _check(_lib.load().cht_multiply_to_host(plan.handle, A.handle, B.handle, _stream(stream),
+                                            _VP(out.data_ptr()), int(nchunks)),
+           "cht_multiply_to_host")
+    return out
+
+
 def cht_multiply_backward(plan: Plan | None, A: Matrix, B: Matrix, dC: Matrix,
                           recompute_pairs: bool = False, dA: Matrix | None = None,
                           dB: Matrix | None = None, want_dA: bool = True,

@@ -34,6 +34,7 @@ SIGNATURES = {
     "cht_add_identity": (ctypes.c_int, [ctypes.c_double, _VP, ctypes.c_double, _VP, _PVP]),
     "cht_truncate": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int, _VP, _PVP,
                                     ctypes.POINTER(ctypes.c_double)]),
+    "cht_multiply_to_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int32]),
     "cht_plan_info": (ctypes.c_int, [_VP, _PI64, _PI64]),
     "cht_plan_arrays": (ctypes.c_int, [_VP, _PVP, _PVP, _PVP, _PVP, _PVP, _PVP]),
     "cht_plan_free": (ctypes.c_int, [_VP]),

@@ -484,6 +484,34 @@ int cht_multiply(cht_plan_t plan, cht_mat_t A, cht_mat_t B, int mode, int32_t ns
   return CHT_OK;
 }
 
+int cht_multiply_to_host(cht_plan_t plan, cht_mat_t A, cht_mat_t B, void *stream,
+                         double *h_C, int32_t nchunks) {
+  if (!plan || !h_C || nchunks < 1) {
+    set_error("null plan or host buffer, or nchunks < 1");
+    return CHT_ERR_INVALID;
+  }
+  CHT_TRY(check_pair(A, B));
+  if (plan->n != A->pat->n || plan->b != A->pat->b || plan->nA != A->pat->nnz ||
+      plan->nB != B->pat->nnz) {
+    set_error("matrices do not match the plan's operands");
+    return CHT_ERR_SHAPE;
+  }
+  cudaStream_t s = as_stream(stream);
+  const int64_t nC = plan->C->nnz;
+  DevArray<double> cv;
+  CHT_TRY(cv.alloc(static_cast<size_t>(nC) * plan->b * plan->b, s));
+  GemmWork w{};
+  w.X = A->values();
+  w.Y = B->values();
+  w.Z = cv.p;
+  w.px = plan->pa.p;
+  w.py = plan->pb.p;
+  w.seg = plan->cseg.p;
+  w.nunits = nC;
+  w.b = plan->b;
+  return multiply_f64_to_host(w, nchunks, h_C, s);
+}
+
 int cht_multiply_backward(cht_plan_t plan, cht_mat_t A, cht_mat_t B, cht_mat_t dC,
                           int recompute_pairs, void *stream, cht_mat_t *dA, cht_mat_t *dB) {
   CHT_TRY(check_pair(A, B));

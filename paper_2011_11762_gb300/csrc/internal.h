@@ -138,6 +138,9 @@ struct GemmWork {
 };
 // Z[o] = sum_p op(X[px[p]]) op(Y[py[p]]) for every unit; FP64.
 int launch_leafgemm_f64(const GemmWork &w, cudaStream_t s);
+// The same over all w.nunits C leaves (w.order unused) in `nchunks` Morton
+// ranges, each copied to h_out (host) while the next is computed.
+int multiply_f64_to_host(const GemmWork &w, int64_t nchunks, double *h_out, cudaStream_t s);
 
 // One product of a batch, as the batched kernels see it.
 struct ProdDesc {

@@ -327,6 +327,81 @@ int launch_leafgemm_f64(const GemmWork &w, cudaStream_t s) {
   return CHT_ERR_UNSUPPORTED;
 }
 
+namespace {
+
+// Chunk of C leaf u is floor(u * nchunks / nC); inside a chunk the units go
+// longest segment first.  key = chunk << 32 | (2^32 - 1 - segment length).
+__global__ void k_chunk_keys(const int64_t *__restrict__ seg, int64_t nC, int64_t nchunks,
+                             uint64_t *__restrict__ key, int32_t *__restrict__ idx) {
+  for (int64_t u = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; u < nC;
+       u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int64_t len = seg[u + 1] - seg[u];
+    if (len > 0xffffffffLL) len = 0xffffffffLL;
+    const uint64_t chunk = static_cast<uint64_t>(u * nchunks / nC);
+    key[u] = (chunk << 32) | (0xffffffffULL - static_cast<uint64_t>(len));
+    idx[u] = static_cast<int32_t>(u);
+  }
+}
+
+}  // namespace
+
+// C = A*B in FP64 with C going to host memory while it is computed: the C
+// leaves are cut into `nchunks` contiguous Morton ranges, each computed by
+// one launch (longest segment first inside the range) and copied to h_out on
+// a second stream as soon as it is done, so the copies overlap the next
+// ranges' arithmetic.  The caller's stream waits for the last copy.
+int multiply_f64_to_host(const GemmWork &w0, int64_t nchunks, double *h_out, cudaStream_t s) {
+  const int64_t nC = w0.nunits;
+  if (nC <= 0) return CHT_OK;
+  if (nchunks < 1) nchunks = 1;
+  if (nchunks > nC) nchunks = nC;
+  const int64_t bb = static_cast<int64_t>(w0.b) * w0.b;
+  DevArray<uint64_t> key, skey;
+  DevArray<int32_t> idx, sidx;
+  CHT_TRY(key.alloc(nC, s));
+  CHT_TRY(skey.alloc(nC, s));
+  CHT_TRY(idx.alloc(nC, s));
+  CHT_TRY(sidx.alloc(nC, s));
+  {
+    int64_t g = (nC + 255) / 256;
+    if (g > 65535LL * 8) g = 65535LL * 8;
+    k_chunk_keys<<<static_cast<unsigned>(g), 256, 0, s>>>(w0.seg, nC, nchunks, key.p, idx.p);
+    CHT_TRY(launched("chunk_keys"));
+  }
+  CHT_TRY(radix_sort_pairs(key.p, idx.p, skey.p, sidx.p, nC, 32 + bits_for(nchunks + 1), s));
+  cudaStream_t cs = nullptr;
+  CHT_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  int rc = CHT_OK;
+  for (int64_t k = 0; k < nchunks && rc == CHT_OK; ++k) {
+    const int64_t u0 = (k * nC + nchunks - 1) / nchunks;
+    const int64_t u1 = ((k + 1) * nC + nchunks - 1) / nchunks;
+    if (u1 <= u0) continue;
+    GemmWork w = w0;
+    w.order = sidx.p + u0;
+    w.nunits = u1 - u0;
+    rc = launch_leafgemm_f64(w, s);
+    if (rc != CHT_OK) break;
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h_out + u0 * bb, w0.Z + u0 * bb, sizeof(double) * (u1 - u0) * bb,
+                          cudaMemcpyDeviceToHost, cs);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) rc = cuda_fail(e, "chunk copy");
+  }
+  // the caller's stream (and the frees of the scratch above) wait for the copies
+  cudaEvent_t done;
+  cudaError_t e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(done, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, done, 0);
+  cudaEventDestroy(done);
+  cudaStreamDestroy(cs);
+  if (rc == CHT_OK && e != cudaSuccess) rc = cuda_fail(e, "copy stream join");
+  return rc;
+}
+
 int launch_leafgemm_f64_batch(const ProdDesc *d_prods, const int64_t *d_units, int64_t nunits,
                               unsigned long long *d_counter, cudaStream_t s) {
   if (nunits <= 0) return CHT_OK;

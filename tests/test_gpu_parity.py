@@ -269,3 +269,21 @@ def test_dense_torch_cross_check(lib):
     full = torch.kron(mask.to(torch.float64), torch.ones((a.b, a.b), dtype=torch.float64,
                                                          device="cuda")) != 0
     assert not bool(ref[~full].any())
+
+
+@pytest.mark.parametrize("nchunks", [1, 3, 8])
+def test_multiply_to_host_equals_device_product(lib, nchunks):
+    # the chunked product streamed to pinned host memory equals the device
+    # product bit for bit (same kernel, same per-leaf summation order)
+    torch = pytest.importorskip("torch")
+    a, b = w.config2(8192)
+    A, B = gu.upload(lib, a), gu.upload(lib, b)
+    plan = lib.cht_symbolic_multiply(A, B)
+    C, _ = lib.cht_multiply(plan, A, B, sync=True)
+    out = torch.empty((plan.nnzb_C, a.b, a.b), dtype=torch.float64, pin_memory=True)
+    out.fill_(float("nan"))
+    lib.cht_multiply_to_host(plan, A, B, out, nchunks=nchunks)
+    torch.cuda.current_stream().synchronize()
+    assert torch.equal(out, C.values().cpu())
+    with pytest.raises(lib.ChtError):
+        lib.cht_multiply_to_host(plan, A, B, out, nchunks=0)
