@@ -487,11 +487,17 @@ template <>
 struct KCfg<64> {
   static constexpr int STAGES = 2, STAGE = Smem<64>::STAGE, XBUF = Smem<64>::XBUF, NXB = 1;
   static constexpr int TMEM_COLS = 512;
+  static constexpr int CHUNK = 2;  // units taken from the counter at a time
 };
 template <>
 struct KCfg<32> {
   static constexpr int STAGES = 2, STAGE = Smem<32>::STAGE, XBUF = Smem<32>::XBUF, NXB = 2;
-  static constexpr int TMEM_COLS = 256;
+  // two accumulator sets of 256 columns: the MMA of unit n + 1 runs while
+  // the epilogue still reads unit n
+  static constexpr int TMEM_COLS = 512;
+  // 32-leaf products often have one or two pairs per C leaf: the producer
+  // resolves 32 units at once so their metadata loads overlap
+  static constexpr int CHUNK = 32;
 };
 
 // One entry of the per-CTA unit queue: a C leaf and everything the MMA and
@@ -562,7 +568,8 @@ __device__ __forceinline__ void issue_blocks(uint32_t sa, uint32_t sb, uint32_t 
 // on, the first pair's region-2 blocks go out before the wait for the
 // epilogue to release the exact regions: they cover that hand-off.
 template <int B, int S>
-__device__ bool mma_unit(int64_t np, uint32_t &k, uint32_t &win, const Ctl &c) {
+__device__ bool mma_unit(int64_t np, uint32_t &k, uint32_t &win, const Ctl &c, uint32_t tmem,
+                         uint64_t *acc_full, uint64_t *acc_empty) {
   using CF = Cfg<B>;
   using SM = Smem<B>;
   bool fresh[kRegions];
@@ -572,7 +579,7 @@ __device__ bool mma_unit(int64_t np, uint32_t &k, uint32_t &win, const Ctl &c) {
     const bool ahead = w0 != 0;
     if (!ahead) {
       // the epilogue must have read every region of the previous unit
-      if (!wait_or_abort(c.acc_empty, (win & 1u) ^ 1u, c.wait_ns, c.abort_flag)) return false;
+      if (!wait_or_abort(acc_empty, (win & 1u) ^ 1u, c.wait_ns, c.abort_flag)) return false;
       tc_fence_after();
     }
     const int64_t w1 = min(np, w0 + CF::WINDOW);
@@ -584,20 +591,20 @@ __device__ bool mma_unit(int64_t np, uint32_t &k, uint32_t &win, const Ctl &c) {
       const uint32_t sb = sa + SM::A_BYTES;
       if (i == w0) {
         if (ahead) {
-          issue_blocks<B>(sa, sb, c.tmem, fresh, 1);
+          issue_blocks<B>(sa, sb, tmem, fresh, 1);
           // the epilogue must have read the exact regions of the last window
-          if (!wait_or_abort(c.acc_empty, (win & 1u) ^ 1u, c.wait_ns, c.abort_flag)) return false;
+          if (!wait_or_abort(acc_empty, (win & 1u) ^ 1u, c.wait_ns, c.abort_flag)) return false;
           tc_fence_after();
         }
 #pragma unroll
         for (int r = 0; r < kExactRegions; ++r) fresh[r] = true;
-        issue_blocks<B>(sa, sb, c.tmem, fresh, ahead ? 2 : 0);
+        issue_blocks<B>(sa, sb, tmem, fresh, ahead ? 2 : 0);
       } else {
-        issue_blocks<B>(sa, sb, c.tmem, fresh, 0);
+        issue_blocks<B>(sa, sb, tmem, fresh, 0);
       }
       tc_commit(&c.empty[st]);  // frees the stage when these MMAs finish
     }
-    tc_commit(c.acc_full);
+    tc_commit(acc_full);
   }
   return true;
 }
@@ -606,7 +613,8 @@ __device__ bool mma_unit(int64_t np, uint32_t &k, uint32_t &win, const Ctl &c) {
 // and the FP64 store of one C leaf.  `xb` is this unit's exchange buffer.
 template <int B, bool SINGLE_FAST>
 __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *xb,
-                         const Ctl &c) {
+                         const Ctl &c, uint32_t tmem, uint64_t *acc_full,
+                         uint64_t *acc_empty) {
   using CF = Cfg<B>;
   constexpr int N = CF::N, PARTS = CF::PARTS, WINDOW = CF::WINDOW;
   constexpr int E = B / 2;  // columns of the C leaf per epilogue thread
@@ -616,7 +624,7 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
   const int part = (B == 64) ? (q >> 1) : q;
   const int row = (B == 64) ? ((q & 1) * 32 + lane) : lane;
   const int c0 = half * E;
-  const uint32_t lane_base = c.tmem + (static_cast<uint32_t>(32 * q) << 16);
+  const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * q) << 16);
   const int64_t np = sl.np;
   // The int64 accumulators of the exact regions live in TMEM columns beyond
   // the MMA regions (2 columns per element: low, high word), so that the
@@ -625,7 +633,7 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
   float rl[E];  // low region (t = 6), folded: R6 2^-8 + R7 2^-16
   for (int64_t w0 = 0; w0 < np; w0 += WINDOW, ++win) {
     const bool last = w0 + WINDOW >= np, first = w0 == 0;
-    if (!wait_or_abort(c.acc_full, win & 1u, c.wait_ns, c.abort_flag)) return false;
+    if (!wait_or_abort(acc_full, win & 1u, c.wait_ns, c.abort_flag)) return false;
     tc_fence_after();
     // exact regions r = 0, 1 (base diagonal t = 2 + 2r); column half qq of a
     // region holds diagonal t + part + qq, weight 2^(8 (5 - t - qq)) in
@@ -640,7 +648,7 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
     if (!last) {
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(c.acc_empty);  // the MMA may go on
+      if (lane == 0) mbar_arrive(acc_empty);  // the MMA may go on
     }
     long long Q[E];
     // a one-window unit needs no int64 round trip through TMEM (used where
@@ -706,7 +714,7 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
     }
     tc_fence_before();
     __syncwarp();
-    if (lane == 0) mbar_arrive(c.acc_empty);  // the next unit may overwrite TMEM
+    if (lane == 0) mbar_arrive(acc_empty);  // the next unit may overwrite TMEM
     // part value in units of 2^-(8 (5 + part) + 8) = 2^-48 after the shift
     // by 8 * part (rounded); the plan limits the window count so that every
     // part fits 64 bits
@@ -791,6 +799,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                  int64_t wait_ns) {
   using KC = KCfg<MAXB>;
   constexpr int S = KC::STAGES;
+  constexpr int NB = MAXB == 32 ? 2 : 1;  // TMEM accumulator sets
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
   const uint32_t raw_addr = smem_addr(smem_raw);
@@ -806,11 +815,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   c.empty = bars + S;
   c.qfull = bars + 2 * S;
   c.qempty = c.qfull + kQueue;
-  c.acc_full = c.qempty + kQueue;
-  c.acc_empty = c.acc_full + 1;
-  c.drain = c.acc_full + 2;
-  c.ep_bar = c.acc_full + 3;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(c.ep_bar + 1);
+  c.acc_full = c.qempty + kQueue;  // [NB]
+  c.acc_empty = c.acc_full + 2;     // [NB]
+  c.drain = c.acc_full + 4;
+  c.ep_bar = c.acc_full + 5;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(c.ep_bar + 2);
   c.abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   c.wait_ns = wait_ns;
 
@@ -820,14 +829,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&c.full[st], 1);
       mbar_init(&c.empty[st], 1);
     }
+    constexpr int kUnitWarps = kEpiWarps;  // a unit's epilogue: all 8 epilogue warps
     for (int i = 0; i < kQueue; ++i) {
       mbar_init(&c.qfull[i], 1);
-      mbar_init(&c.qempty[i], 1 + kEpiWarps);  // the MMA thread and 8 epilogue warps
+      mbar_init(&c.qempty[i], 1 + kUnitWarps);  // the MMA thread and the epilogue warps
     }
-    mbar_init(c.acc_full, 1);
-    mbar_init(c.acc_empty, kEpiWarps);
+    for (int bf = 0; bf < 2; ++bf) {
+      mbar_init(&c.acc_full[bf], 1);
+      mbar_init(&c.acc_empty[bf], kUnitWarps);
+      mbar_init(&c.ep_bar[bf], kUnitWarps);
+    }
     mbar_init(c.drain, 1);
-    mbar_init(c.ep_bar, kEpiWarps);
     *c.abort_flag = 0;
     fence_mbar_init();
   }
@@ -844,9 +856,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------- producer --
-    // Units are taken kChunk at a time; lanes resolve their metadata, the
-    // line exponents and the pair indices in parallel, lane 0 issues copies.
-    constexpr int kChunk = 2;
+    // Units are taken kChunk at a time.  Lane l resolves unit u0 + l (its
+    // product, C leaf, pair segment, coordinates and the pointers the copies
+    // need) so that those loads overlap; then, unit by unit, the line
+    // exponents and first pair indices of the next unit are loaded while the
+    // current one is staged and its copies are issued.
+    constexpr int kChunk = KCfg<MAXB>::CHUNK;
     uint32_t k = 0;  // pairs issued
     uint32_t n = 0;  // queue position
     bool done = false;
@@ -854,22 +869,68 @@ __global__ void __launch_bounds__(kThreads, 1)
       unsigned long long u0 = 0;
       if (lane == 0) u0 = atomicAdd(next_unit, static_cast<unsigned long long>(kChunk));
       u0 = __shfl_sync(0xffffffffu, u0, 0);
-      int valid_l = 0;
-      long long o_l = 0;
-      int prod_l = 0;
+      int valid_l = 0, b_l = 0, crow_l = 0, ccol_l = 0;
+      long long p0_l = 0, p1_l = 0;
+      const int *re_l = nullptr, *ce_l = nullptr;
+      const int32_t *pa_l = nullptr, *pb_l = nullptr;
+      const uint8_t *as_l = nullptr, *bs_l = nullptr;
+      double *C_l = nullptr;
       if (lane < kChunk) {
         const unsigned long long u = u0 + lane;
         if (u < static_cast<unsigned long long>(nunits)) {
           valid_l = 1;
           const int64_t packed = prods ? units[u] : static_cast<int64_t>(u);
-          o_l = prods ? (packed & 0xffffffffLL) : packed;
-          prod_l = prods ? static_cast<int>(packed >> 32) : 0;
+          const int64_t o = prods ? (packed & 0xffffffffLL) : packed;
+          const SplitProd &dl = prods ? prods[packed >> 32] : single;
+          b_l = dl.b;
+          p0_l = dl.cseg[o];
+          p1_l = dl.cseg[o + 1];
+          crow_l = dl.crow[o];
+          ccol_l = dl.ccol[o];
+          re_l = dl.row_exp;
+          ce_l = dl.col_exp;
+          pa_l = dl.pa;
+          pb_l = dl.pb;
+          as_l = dl.a_slices;
+          bs_l = dl.b_slices;
+          C_l = dl.cptr ? dl.cptr[o] : dl.C + o * dl.b * dl.b;
         }
       }
+      // exponents (rows lane, lane + 32) and the first 32 pair indices of unit j
+      struct Pre {
+        int re0, re1, ce0, ce1, pa, pb;
+      };
+      auto fetch = [&](int j) -> Pre {
+        Pre q{kNoExp, kNoExp, kNoExp, kNoExp, 0, 0};
+        if (!__shfl_sync(0xffffffffu, valid_l, j)) return q;
+        const int b = __shfl_sync(0xffffffffu, b_l, j);
+        const int64_t cr = __shfl_sync(0xffffffffu, crow_l, j), cc = __shfl_sync(0xffffffffu, ccol_l, j);
+        const int *re = reinterpret_cast<const int *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(re_l), j));
+        const int *ce = reinterpret_cast<const int *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(ce_l), j));
+        const int32_t *pa = reinterpret_cast<const int32_t *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(pa_l), j));
+        const int32_t *pb = reinterpret_cast<const int32_t *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(pb_l), j));
+        const long long p0 = __shfl_sync(0xffffffffu, p0_l, j), p1 = __shfl_sync(0xffffffffu, p1_l, j);
+        q.re0 = re[cr * b + lane];
+        q.ce0 = ce[cc * b + lane];
+        if (b == 64) {
+          q.re1 = re[cr * b + lane + 32];
+          q.ce1 = ce[cc * b + lane + 32];
+        }
+        if (p0 + lane < p1) {
+          q.pa = pa[p0 + lane];
+          q.pb = pb[p0 + lane];
+        }
+        return q;
+      };
+      Pre pre = fetch(0);
       for (int j = 0; j < kChunk && !done; ++j) {
         const int valid = __shfl_sync(0xffffffffu, valid_l, j);
-        const int64_t o = __shfl_sync(0xffffffffu, o_l, j);
-        const int prod = __shfl_sync(0xffffffffu, prod_l, j);
+        const Pre cur = pre;
+        if (j + 1 < kChunk) pre = fetch(j + 1);  // lands while this unit is staged
         const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
         const bool ok = wait_or_abort(&c.qempty[qs], qph ^ 1u, c.wait_ns, c.abort_flag);
         if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
@@ -886,16 +947,26 @@ __global__ void __launch_bounds__(kThreads, 1)
           done = true;
           break;
         }
-        const SplitProd d = prods ? prods[prod] : single;
-        const int b = d.b;
-        const int64_t p0 = d.cseg[o], p1 = d.cseg[o + 1];
-        const int32_t crow = d.crow[o], ccol = d.ccol[o];
-        for (int r = lane; r < b; r += 32) {
-          sl.rexp[r] = exp16(d.row_exp[static_cast<int64_t>(crow) * b + r]);
-          sl.cexp[r] = exp16(d.col_exp[static_cast<int64_t>(ccol) * b + r]);
+        const int b = __shfl_sync(0xffffffffu, b_l, j);
+        const int64_t p0 = __shfl_sync(0xffffffffu, p0_l, j), p1 = __shfl_sync(0xffffffffu, p1_l, j);
+        const int32_t *pa = reinterpret_cast<const int32_t *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(pa_l), j));
+        const int32_t *pb = reinterpret_cast<const int32_t *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(pb_l), j));
+        const uint8_t *a_slices = reinterpret_cast<const uint8_t *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(as_l), j));
+        const uint8_t *b_slices = reinterpret_cast<const uint8_t *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(bs_l), j));
+        double *Cp = reinterpret_cast<double *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(C_l), j));
+        sl.rexp[lane] = exp16(cur.re0);
+        sl.cexp[lane] = exp16(cur.ce0);
+        if (b == 64) {
+          sl.rexp[lane + 32] = exp16(cur.re1);
+          sl.cexp[lane + 32] = exp16(cur.ce1);
         }
         if (lane == 0) {
-          sl.C = d.cptr ? d.cptr[o] : d.C + o * b * b;
+          sl.C = Cp;
           sl.np = static_cast<int32_t>(p1 - p0);
           sl.b = b;
           sl.u = static_cast<int32_t>(n);
@@ -907,13 +978,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int b_bytes = b == 64 ? Smem<64>::B_BYTES : Smem<32>::B_BYTES;
         for (int64_t base = p0; base < p1 && !done; base += 32) {
           const int64_t pl = base + lane;
-          const int32_t pa_l = pl < p1 ? d.pa[pl] : 0, pb_l = pl < p1 ? d.pb[pl] : 0;
+          const int32_t pa_v = base == p0 ? cur.pa : (pl < p1 ? pa[pl] : 0);
+          const int32_t pb_v = base == p0 ? cur.pb : (pl < p1 ? pb[pl] : 0);
           const int cnt = static_cast<int>(p1 - base < 32 ? p1 - base : 32);
           for (int i = 0; i < cnt; ++i, ++k) {
             const uint32_t st = k % S, ph = (k / S) & 1u;
             const bool w_ok = wait_or_abort(&c.empty[st], ph ^ 1u, c.wait_ns, c.abort_flag);
-            const int pa_i = __shfl_sync(0xffffffffu, pa_l, i);
-            const int pb_i = __shfl_sync(0xffffffffu, pb_l, i);
+            const int pa_i = __shfl_sync(0xffffffffu, pa_v, i);
+            const int pb_i = __shfl_sync(0xffffffffu, pb_v, i);
             if (!__shfl_sync(0xffffffffu, w_ok ? 1 : 0, 0)) {
               if (lane == 0) fail();
               done = true;
@@ -930,12 +1002,12 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int tile = b * 128;
               const int na = a_bytes / tile, nb = b_bytes / tile;
               if (lane < na)
-                bulk_g2s(sa + lane * tile, d.a_slices + static_cast<int64_t>(pa_i) * a_bytes +
+                bulk_g2s(sa + lane * tile, a_slices + static_cast<int64_t>(pa_i) * a_bytes +
                                                lane * tile,
                          static_cast<uint32_t>(tile), &c.full[st]);
               else if (lane < na + nb)
                 bulk_g2s(sa + a_bytes + (lane - na) * tile,
-                         d.b_slices + static_cast<int64_t>(pb_i) * b_bytes + (lane - na) * tile,
+                         b_slices + static_cast<int64_t>(pb_i) * b_bytes + (lane - na) * tile,
                          static_cast<uint32_t>(tile), &c.full[st]);
             }
           }
@@ -951,7 +1023,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------ MMA issuer --
     if (lane == 0) {
-      uint32_t k = 0, win = 0;
+      uint32_t k = 0, win0 = 0, win1 = 0;  // pairs consumed; windows per accumulator set
       for (uint32_t n = 0;; ++n) {
         const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
         if (!wait_or_abort(&c.qfull[qs], qph, c.wait_ns, c.abort_flag)) {
@@ -963,10 +1035,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (b == 0) break;
         mbar_arrive(&c.qempty[qs]);
         bool ok;
+        const int bf = NB == 2 ? static_cast<int>(n & 1u) : 0;  // accumulator set
+        const uint32_t tm = c.tmem + static_cast<uint32_t>(bf * 256);
+        uint32_t w = bf ? win1 : win0;
         if constexpr (MAXB == 64)
-          ok = b == 64 ? mma_unit<64, S>(np, k, win, c) : mma_unit<32, S>(np, k, win, c);
+          ok = b == 64 ? mma_unit<64, S>(np, k, w, c, tm, &c.acc_full[bf], &c.acc_empty[bf])
+                       : mma_unit<32, S>(np, k, w, c, tm, &c.acc_full[bf], &c.acc_empty[bf]);
         else
-          ok = mma_unit<32, S>(np, k, win, c);
+          ok = mma_unit<32, S>(np, k, w, c, tm, &c.acc_full[bf], &c.acc_empty[bf]);
+        if (bf) win1 = w;
+        else win0 = w;
         if (!ok) {
           fail();
           break;
@@ -978,7 +1056,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // -------------------------------------------------------- epilogue --
-    uint32_t win = 0, epb = 0;
+    uint32_t win0 = 0, win1 = 0, epb = 0;
     for (uint32_t n = 0;; ++n) {
       const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
       if (!wait_or_abort(&c.qfull[qs], qph, c.wait_ns, c.abort_flag)) {
@@ -990,11 +1068,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (b == 0) break;
       int64_t *xb = c.xbuf + (KC::NXB == 2 ? (n & 1u) * (KC::XBUF / 8) : 0);
       bool ok;
+      const int bf = NB == 2 ? static_cast<int>(n & 1u) : 0;
+      const uint32_t tm = c.tmem + static_cast<uint32_t>(bf * 256);
+      uint32_t w = bf ? win1 : win0;
       if constexpr (MAXB == 64)
-        ok = b == 64 ? epi_unit<64, false>(sl, win, epb, xb, c)
-                     : epi_unit<32, false>(sl, win, epb, xb, c);
+        ok = b == 64 ? epi_unit<64, false>(sl, w, epb, xb, c, tm, &c.acc_full[bf],
+                                           &c.acc_empty[bf])
+                     : epi_unit<32, false>(sl, w, epb, xb, c, tm, &c.acc_full[bf],
+                                           &c.acc_empty[bf]);
       else
-        ok = epi_unit<32, true>(sl, win, epb, xb, c);
+        ok = epi_unit<32, true>(sl, w, epb, xb, c, tm, &c.acc_full[bf], &c.acc_empty[bf]);
+      if (bf) win1 = w;
+      else win0 = w;
       if (!ok) {
         fail();
         break;
