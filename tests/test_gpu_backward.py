@@ -175,3 +175,27 @@ def test_backward_with_foreign_dc_pattern(lib):
     gu.assert_values_close(dA, OdA, 1e-13)
     gu.assert_values_close(dB, OdB, 1e-13)
     _ = setref
+
+
+def test_full_size_backward_sampled(lib):
+    # the differentiation workload at its full size (N = 32768, 64x64 leaves,
+    # A banded +-8, B 3D locality): sampled gradient leaves against the
+    # oracle's single-leaf products dA(I,K) = (dC B^T)(I,K), dB(K,J) = (A^T dC)(K,J)
+    a, b = w.config5()
+    A, B = gu.upload(lib, a), gu.upload(lib, b)
+    plan = lib.cht_symbolic_multiply(A, B)
+    C, _ = lib.cht_multiply(plan, A, B, sync=True)
+    crow, ccol = (t.cpu().numpy() for t in C.coords())
+    T = gu.upload(lib, w.values_on_pattern(a.n, a.b, crow, ccol, w.SEED_T + 5))
+    dC = _dc(lib, C, T)
+    dA, dB = lib.cht_multiply_backward(plan, A, B, dC)
+    lib.sync_status()
+    OdC = _oracle_matrix(dC)
+    OA, OB = oracle.OMatrix.from_block_matrix(a), oracle.OMatrix.from_block_matrix(b)
+    OBt, OAt = OB.transpose(), OA.transpose()
+    rng = np.random.default_rng(10)
+    for M, left, right in ((dA, OdC, OBt), (dB, OAt, OdC)):
+        r, c, v = gu.host_leaves(M)
+        for i in list(rng.choice(r.shape[0], 8, replace=False)) + [0, r.shape[0] - 1]:
+            ref, _ = oracle.leaf_product(left, right, int(r[i]), int(c[i]))
+            assert setref.rel_fro(v[i], ref) <= 1e-13, (int(r[i]), int(c[i]))

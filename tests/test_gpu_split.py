@@ -164,3 +164,29 @@ def test_split_long_segments_are_cut_into_pieces(lib, b, g):
     gu.assert_values_close(Cs, OC, 1e-11)
     _, _, ov = OC.leaves()
     assert setref.rel_fro(Cs.values()[0].cpu().numpy(), ov[0]) <= 1e-11
+
+
+def test_full_size_random_sampled(lib):
+    # the random-leaf workload at its full size (N = 32768, 32x32 leaves,
+    # p = 0.01): pattern and pair counts from the set definitions, sampled C
+    # leaves of both forms against the oracle's single-leaf product
+    a, b = w.config3()
+    A, B = gu.upload(lib, a), gu.upload(lib, b)
+    plan = lib.cht_symbolic_multiply(A, B)
+    pa, pb = setref.pattern_set(a.brow, a.bcol), setref.pattern_set(b.brow, b.bcol)
+    assert plan.npairs == setref.pair_count(pa, pb)
+    assert plan.nnzb_C == len(setref.boolean_product(pa, pb))
+    Cd, _ = lib.cht_multiply(plan, A, B, sync=True)
+    Cs, _ = lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
+    arr = plan.arrays()
+    crow, ccol = arr["crow"].numpy(), arr["ccol"].numpy()
+    seglen = np.diff(arr["cseg"].numpy())
+    OA, OB = oracle.OMatrix.from_block_matrix(a), oracle.OMatrix.from_block_matrix(b)
+    vd, vs = Cd.values(), Cs.values()
+    rng = np.random.default_rng(11)
+    picks = list(rng.choice(crow.shape[0], 12, replace=False)) + [int(np.argmax(seglen))]
+    for c in picks:
+        ref, present = oracle.leaf_product(OA, OB, int(crow[c]), int(ccol[c]))
+        assert present
+        assert setref.rel_fro(vd[c].cpu().numpy(), ref) <= 1e-13
+        assert setref.rel_fro(vs[c].cpu().numpy(), ref) <= 1e-11
