@@ -59,7 +59,7 @@ typedef enum {
   CHT_ERR_OOM = -4,         /* an allocation failed                       */
   CHT_ERR_CUDA = -5,        /* a CUDA runtime call failed                 */
   CHT_ERR_TIMEOUT = -6,     /* a bounded device-side wait ran out         */
-  CHT_ERR_UNSUPPORTED = -7  /* valid request this build does not handle   */
+  CHT_ERR_UNSUPPORTED = -7  /* valid request the library does not handle */
 } cht_status;
 
 typedef enum {
