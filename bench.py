@@ -572,7 +572,8 @@ def section_table1(args, world, cht, torch):
     element-level Tflop of the product (the paper's Tflop row), the leaf
     pairs, one FP64 step and the mean of two split steps (symbolic +
     numeric), with both the leaf-level useful TFLOP/s and the element-level
-    rate (paper's flops / time)."""
+    rate (paper's flops / time), and the split result's relative error
+    against the FP64 one."""
     import workloads as w
     stream = torch.cuda.current_stream()
     out = {}
@@ -586,16 +587,21 @@ def section_table1(args, world, cht, torch):
         del plan
         # FP64 steps take seconds each, so that one is timed cold (the
         # library is warm from the earlier sections); split: 1 warm-up
+        last = {}
         for name, mode, steps, warm in (("fp64", cht.CHT_FP64, 1, 0),
                                         ("split", cht.CHT_SPLIT_BF16, 2, 1)):
-            def step(mode=mode):
+            def step(mode=mode, name=name):
                 p = cht.cht_symbolic_multiply(A, A)
-                cht.cht_multiply(p, A, A, mode=mode)
+                last[name], _ = cht.cht_multiply(p, A, A, mode=mode)
             ms = _time_steps(torch, stream, step, steps, warm)
             res[name] = {"ms_per_step": ms,
                          "value": res["leaf_tflop"] * 1e12 * world / (ms * 1e-3) / 1e12,
                          "unit": UNIT,
                          "element_level_tflops": eflops * world / (ms * 1e-3) / 1e12}
+        # the split result against the FP64 one (same plan, same pattern)
+        res["split"]["rel_fro_err_vs_fp64"] = _rel_fro(torch, last["split"].values(),
+                                                       last["fp64"].values())
+        last.clear()
         out[kind] = res
         del A
     out["workload"] = "table1_N100000_hw3000_b64"
