@@ -72,8 +72,10 @@ int orc_truncate(const orc_mat *M, double eps, int kind, orc_mat **out, double *
 
 /* The symmetric matrix whose upper triangle (element level) is U's: leaf
  * (J, I), I < J, is U's leaf (I, J) transposed; a diagonal leaf keeps its
- * entries on and above its diagonal and mirrors them below.  Every leaf of
- * U is kept, all-zero or not.  -1 if U has a leaf below the diagonal. */
+ * entries on and above its diagonal and mirrors them below (paper, Section
+ * 2.2: the symmetric operations, whose results are determined by one
+ * triangle).  Every leaf of U is kept, all-zero or not.  -1 if U has a leaf
+ * below the diagonal. */
 int orc_mirror_upper(const orc_mat *U, orc_mat **out);
 
 /* Transpose (a new matrix). */
