@@ -44,8 +44,6 @@
 // (neighbouring leaves run together, so their A and B slices are shared
 // through L2).  A C leaf with more pairs than a unit may sum is cut into
 // pieces added afterwards in FP64.  Every wait is bounded.
-#include <cuda_bf16.h>
-
 #include <algorithm>
 
 #include "device.cuh"
@@ -267,21 +265,32 @@ __device__ inline unsigned long long fixed_mag(double x, int e, int nbits, bool 
 }
 
 // Balanced base-256 digits of a magnitude m <= 2^(8n - 1), least significant
-// first: each in [-127, 128], so with the sign applied |digit| <= 128.
+// first: t = ((m + 127) mod 256) - 127, m <- (m - t) / 256, so each digit is
+// in [-127, 128] and, with the sign applied, |digit| <= 128.  The recurrence
+// runs on 24-bit chunks of m in 32-bit arithmetic: after the three digits of
+// a chunk the running value is the carry (0 or 1) into the next chunk.
 template <int NDIG>
 __device__ inline void balanced_digits(unsigned long long m, bool neg, int (&out)[NDIG]) {
+  int v = 0, carry = 0;
 #pragma unroll
-  for (int i = NDIG - 1; i >= 0; --i) {
-    const int t = static_cast<int>((m + 127ULL) & 0xffULL) - 127;
-    out[i] = neg ? -t : t;
-    m = t >= 0 ? (m - static_cast<unsigned long long>(t)) >> kW
-               : (m + static_cast<unsigned long long>(-t)) >> kW;
+  for (int g = 0; g < NDIG; ++g) {
+    if (g % 3 == 0) v = static_cast<int>((m >> (kW * g)) & 0xffffffULL) + carry;
+    const int t = ((v + 127) & 0xff) - 127;
+    out[NDIG - 1 - g] = neg ? -t : t;
+    v = (v - t) >> kW;
+    if (g % 3 == 2) carry = v;
   }
 }
 
+// Two integers |t| <= 256 as a bfloat16 pair (both exact in bfloat16).  The
+// float with bits 0x4B400000 + t is 1.5 * 2^23 + t, so subtracting 1.5 * 2^23
+// gives t exactly; its bfloat16 is the upper half of its bits.  Integer adds,
+// one float add and a byte permute replace the slower int-to-float
+// conversions.
 __device__ inline uint32_t pack_bf16x2(int lo, int hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(static_cast<float>(lo), static_cast<float>(hi));
-  return *reinterpret_cast<uint32_t *>(&v);
+  const float fl = __int_as_float(0x4B400000 + lo) - 12582912.0f;
+  const float fh = __int_as_float(0x4B400000 + hi) - 12582912.0f;
+  return __byte_perm(__float_as_uint(fl), __float_as_uint(fh), 0x7632);
 }
 
 // Byte offset of logical 16-byte chunk c of row r in a 128-byte-swizzled tile.
@@ -349,18 +358,21 @@ __global__ void k_row_exp(const double *__restrict__ vals, const int32_t *__rest
   }
 }
 
-// Column exponents of B (frexp exponent + 1): thread per (leaf, column).
+// Column exponents of B (frexp exponent + 1): thread per (leaf, column);
+// consecutive threads read consecutive columns, 16 rows in flight.
+template <int B>
 __global__ void k_col_exp(const double *__restrict__ vals, const int32_t *__restrict__ bcol,
-                          int64_t nleaves, int b, int *__restrict__ col_exp) {
-  const int64_t total = nleaves * b;
+                          int64_t nleaves, int *__restrict__ col_exp) {
+  const int64_t total = nleaves * B;
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
        t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t leaf = t / b;
-    const int c = static_cast<int>(t % b);
-    const double *col = vals + leaf * b * b + c;
+    const int64_t leaf = t / B;
+    const int c = static_cast<int>(t % B);
+    const double *col = vals + leaf * B * B + c;
     int e = kNoExp;
-    for (int k = 0; k < b; ++k) e = max(e, exp_of(col[static_cast<int64_t>(k) * b]));
-    if (e != kNoExp) atomicMax(&col_exp[static_cast<int64_t>(bcol[leaf]) * b + c], e + 1);
+#pragma unroll 16
+    for (int k = 0; k < B; ++k) e = max(e, exp_of(col[static_cast<int64_t>(k) * B]));
+    if (e != kNoExp) atomicMax(&col_exp[static_cast<int64_t>(bcol[leaf]) * B + c], e + 1);
   }
 }
 
@@ -1145,7 +1157,7 @@ int split_operands(const cht_mat *A, const cht_mat *Bm, cudaStream_t s, Operands
     CHT_TRY(launched("row_exp"));
   }
   if (pb.nnz > 0) {
-    k_col_exp<<<grid_for(pb.nnz * B, 256), 256, 0, s>>>(bv, pb.bcol.p, pb.nnz, B, op.col_exp.p);
+    k_col_exp<B><<<grid_for(pb.nnz * B, 256), 256, 0, s>>>(bv, pb.bcol.p, pb.nnz, op.col_exp.p);
     CHT_TRY(launched("col_exp"));
   }
   if (pa.nnz > 0) {
