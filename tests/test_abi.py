@@ -68,6 +68,22 @@ def test_host_only_calls(libpath):
     assert lib.cht_set_allocator(ctypes.c_void_p(1), None, None) == cht.CHT_ERR_INVALID
     assert lib.cht_batch_create(0, None, None, None, 0, 0, None,
                                 ctypes.byref(h)) == cht.CHT_ERR_INVALID
+    # the operations around the product check their arguments on the host too
+    n = ctypes.c_int64()
+    d = ctypes.c_double()
+    inv = cht.CHT_ERR_INVALID
+    assert lib.cht_symbolic_multiply_spamm(None, None, -1.0, None, ctypes.byref(h),
+                                           None, None) == inv
+    assert lib.cht_symbolic_multiply_symsquare(None, None, ctypes.byref(h), ctypes.byref(n),
+                                               ctypes.byref(n)) == inv
+    assert lib.cht_symbolic_multiply_upper(None, None, None, ctypes.byref(h), None, None) == inv
+    assert lib.cht_mat_mirror_upper(None, None, ctypes.byref(h)) == inv
+    assert lib.cht_add(1.0, None, 1.0, None, None, ctypes.byref(h)) == inv
+    assert lib.cht_add_identity(1.0, None, 1.0, None, ctypes.byref(h)) == inv
+    assert lib.cht_truncate(None, 1e-6, cht.CHT_TRUNC_FRO, None, ctypes.byref(h),
+                            ctypes.byref(d)) == inv
+    assert lib.cht_multiply_to_host(None, None, None, None, None, 0) == inv
+    assert b"nchunks" in lib.cht_last_error()
 
 
 def test_product_path_has_no_oracle_dependency():
