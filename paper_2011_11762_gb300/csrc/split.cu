@@ -424,9 +424,19 @@ __global__ void k_split_a(const double *__restrict__ vals, const int32_t *__rest
 
 // B slices, stored transposed (tile row n = column n of the leaf, K-major).
 // One block per leaf: the leaf is staged in shared memory with contiguous
-// 16-byte loads, then thread (column n, chunk c of 8 K values) reads its
-// column from shared memory (consecutive threads: consecutive columns, no
-// bank conflicts) and writes its 16-byte chunk of every digit plane.
+// 16-byte loads; thread (column n, chunk c of 8 K values) reads its column
+// from shared memory (consecutive threads: consecutive columns, no bank
+// conflicts) and writes its 16-byte chunk of every digit plane into a
+// shared-memory image of the leaf's slice tiles, which the block then stores
+// with contiguous 16-byte writes.
+template <int B>
+struct SplitBSmem {
+  static constexpr int IN = B * (B + 1) * 8;  // the staged leaf (padded rows)
+  static constexpr int OUT = kSB * B * 128;   // the slice tiles of one leaf
+  static constexpr int TOTAL = IN + OUT;
+  static_assert(IN % 16 == 0 && OUT % 16 == 0, "16-byte aligned parts");
+};
+
 template <int B>
 __global__ void __launch_bounds__(256) k_split_b(const double *__restrict__ vals,
                                                  const int32_t *__restrict__ bcol,
@@ -434,7 +444,10 @@ __global__ void __launch_bounds__(256) k_split_b(const double *__restrict__ vals
                                                  uint8_t *__restrict__ out) {
   constexpr int CH = B / 8;
   constexpr int TILE = B * 128;
-  __shared__ double tile[B][B + 1];
+  constexpr int OUT = SplitBSmem<B>::OUT;
+  extern __shared__ __align__(16) uint8_t smem_b[];
+  double(*tile)[B + 1] = reinterpret_cast<double(*)[B + 1]>(smem_b);
+  uint8_t *img = smem_b + SplitBSmem<B>::IN;
   for (int64_t leaf = blockIdx.x; leaf < nleaves; leaf += gridDim.x) {
     const double2 *src = reinterpret_cast<const double2 *>(vals + leaf * B * B);
     for (int i = threadIdx.x; i < B * B / 2; i += blockDim.x) {
@@ -443,6 +456,7 @@ __global__ void __launch_bounds__(256) k_split_b(const double *__restrict__ vals
       tile[e / B][e % B] = v.x;
       tile[e / B][e % B + 1] = v.y;
     }
+    // reads of the previous leaf's image ended before every thread got here
     __syncthreads();
     const int64_t col0 = static_cast<int64_t>(bcol[leaf]) * B;
     for (int q = threadIdx.x; q < B * CH; q += blockDim.x) {
@@ -458,7 +472,7 @@ __global__ void __launch_bounds__(256) k_split_b(const double *__restrict__ vals
 #pragma unroll
         for (int j = 0; j < kSB; ++j) g[j][k] = gk[j];
       }
-      uint8_t *base = out + leaf * kSB * TILE + sw128_offset(n, c);
+      uint8_t *base = img + sw128_offset(n, c);
 #pragma unroll
       for (int j = 0; j < kSB; ++j) {
         uint4 v;
@@ -469,7 +483,11 @@ __global__ void __launch_bounds__(256) k_split_b(const double *__restrict__ vals
         *reinterpret_cast<uint4 *>(base + j * TILE) = v;
       }
     }
+    // the image is complete, and the staged leaf is no longer read
     __syncthreads();
+    uint4 *dst = reinterpret_cast<uint4 *>(out + leaf * OUT);
+    const uint4 *from = reinterpret_cast<const uint4 *>(img);
+    for (int i = threadIdx.x; i < OUT / 16; i += blockDim.x) dst[i] = from[i];
   }
 }
 
@@ -1169,8 +1187,11 @@ int split_operands(const cht_mat *A, const cht_mat *Bm, cudaStream_t s, Operands
     int sms = 0;
     CHT_TRY(num_sms(&sms));
     const int64_t nblk = std::min<int64_t>(pb.nnz, static_cast<int64_t>(sms) * 8);
-    k_split_b<B><<<static_cast<unsigned>(nblk), 256, 0, s>>>(bv, pb.bcol.p, pb.nnz, op.col_exp.p,
-                                                              op.b_sl.p);
+    constexpr int smem = SplitBSmem<B>::TOTAL;
+    CHT_CUDA_TRY(cudaFuncSetAttribute(k_split_b<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      smem));
+    k_split_b<B><<<static_cast<unsigned>(nblk), 256, smem, s>>>(bv, pb.bcol.p, pb.nnz,
+                                                                op.col_exp.p, op.b_sl.p);
     CHT_TRY(launched("split_b"));
   }
   return CHT_OK;
