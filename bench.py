@@ -53,7 +53,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=65536, help="3D-locality workload size")
+    ap.add_argument("--n", "--size", dest="n", type=int, default=65536,
+                    help="3D-locality workload size (--size under torchrun, whose own "
+                         "options make --n ambiguous)")
     ap.add_argument("--sections",
                     default="banded,split,spamm,symsquare,purify,table1,backward,batched",
                     help="extra sections (comma list; '' for none)")
