@@ -26,21 +26,22 @@ from . import (CHT_FP64, OPT_SCHEDULE, Batch, cht_mat_from_blocks, cht_multiply,
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "cht", "autotune.json")
 
 
-def reblock(n: int, b: int, brow, bcol, vals, b_new: int):
+def reblock(n: int, b: int, brow, bcol, vals, b_new: int, device="cuda"):
     """The same matrix with leaf size b_new (a multiple of b dividing n):
-    (brow, bcol, vals) of the merged leaves, zero-filled, on the GPU."""
+    (brow, bcol, vals) of the merged leaves, zero-filled, on ``device``
+    (the GPU for the tuner), in row-major order of the new leaves."""
     if b_new == b:
         return brow, bcol, vals
     if b_new % b or n % b_new:
         raise ValueError("b_new must be a multiple of b and divide n")
     f = b_new // b
     g_new = n // b_new
-    brow = torch.as_tensor(brow, device="cuda").long()
-    bcol = torch.as_tensor(bcol, device="cuda").long()
-    vals = torch.as_tensor(vals, device="cuda", dtype=torch.float64)
+    brow = torch.as_tensor(brow, device=device).long()
+    bcol = torch.as_tensor(bcol, device=device).long()
+    vals = torch.as_tensor(vals, device=device, dtype=torch.float64)
     key = (brow // f) * g_new + (bcol // f)
     uniq, inv = torch.unique(key, return_inverse=True)
-    out = torch.zeros((uniq.numel(), f, b, f, b), dtype=torch.float64, device="cuda")
+    out = torch.zeros((uniq.numel(), f, b, f, b), dtype=torch.float64, device=device)
     out[inv, brow % f, :, bcol % f, :] = vals
     return ((uniq // g_new).to(torch.int32), (uniq % g_new).to(torch.int32),
             out.reshape(uniq.numel(), b_new, b_new))
