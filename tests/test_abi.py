@@ -84,6 +84,23 @@ def test_host_only_calls(libpath):
                             ctypes.byref(d)) == inv
     assert lib.cht_multiply_to_host(None, None, None, None, None, 0) == inv
     assert b"nchunks" in lib.cht_last_error()
+    # shape limits of the boundary: leaf size 32..64 in steps of 8, n a
+    # multiple of b, a leaf count that fits int32, 16-byte aligned values, and
+    # at most 2^21 leaves per grid side (the 64-bit Morton pair keys)
+    for n, b, nb in ((4096, 16, 0), (4096, 72, 0), (4096, 36, 0), (4000, 64, 0),
+                     (4096, 64, -1), (4096, 64, 1 << 31), (0, 64, 0), (-64, 64, 0)):
+        assert lib.cht_mat_from_blocks(n, b, nb, None, None, None, None,
+                                       ctypes.byref(h)) == inv, (n, b, nb)
+    dummy = ctypes.c_void_p(64)
+    assert lib.cht_mat_from_blocks(4096, 64, 1, dummy, dummy, ctypes.c_void_p(72), None,
+                                   ctypes.byref(h)) == inv
+    assert b"aligned" in lib.cht_last_error()
+    assert lib.cht_mat_from_blocks(64 * ((1 << 21) + 1), 64, 0, None, None, None, None,
+                                   ctypes.byref(h)) == cht.CHT_ERR_UNSUPPORTED
+    assert b"2^21" in lib.cht_last_error()
+    for code in (cht.CHT_ERR_INVALID, cht.CHT_ERR_SHAPE, cht.CHT_ERR_DUPLICATE,
+                 cht.CHT_ERR_OOM, cht.CHT_ERR_CUDA, cht.CHT_ERR_UNSUPPORTED):
+        assert lib.cht_status_str(code).startswith(b"CHT_ERR_")
 
 
 def test_product_path_has_no_oracle_dependency():
