@@ -91,11 +91,16 @@ int cht_set_allocator(cht_alloc_fn alloc, cht_free_fn free_fn, void *ctx);
  *          (the numeric kernels take b = 32 or b = 64).
  * nblocks  number of leaves given (0 is a valid, empty matrix).
  * d_brow, d_bcol  int32 leaf coordinates, 0 <= coordinate < n / b.
- * d_vals   nblocks * b * b doubles; leaf i is d_vals[i*b*b ...], row-major.
+ * d_vals   nblocks * b * b doubles, 16-byte aligned; leaf i is
+ *          d_vals[i*b*b ...], row-major.
+ * All three arrays are device memory owned by the caller and copied; they
+ * may be freed once the call returns.
  * Leaves may come in any order.  A leaf whose values are all zero is
  * identically zero (nil, Section 2) and is not stored.
- * Errors: CHT_ERR_INVALID (range, sizes), CHT_ERR_DUPLICATE (a coordinate
- * given twice, zero leaves included), CHT_ERR_OOM, CHT_ERR_CUDA.
+ * Errors: CHT_ERR_INVALID (range, sizes, alignment, nblocks >= 2^31),
+ * CHT_ERR_DUPLICATE (a coordinate given twice, zero leaves included),
+ * CHT_ERR_UNSUPPORTED (more than 2^21 leaves per grid side: the pair keys
+ * of the symbolic phase are 64-bit), CHT_ERR_OOM, CHT_ERR_CUDA.
  * Synchronises `stream` once, to validate the input and size the handle.
  * ---------------------------------------------------------------------- */
 int cht_mat_from_blocks(int64_t n, int32_t b, int64_t nblocks,
