@@ -6,6 +6,13 @@ and B's leaf column alone, and exactly one rank owns it, so no reduction is
 needed.  ``partition_units`` cuts the Morton-ordered C leaves into contiguous
 ranges of about equal pair count (contiguous Morton ranges keep each rank's
 A rows and B columns local, the locality the paper's runtime exploits).
+When the operands start distributed (rank r holding a contiguous Morton
+range of each operand's leaves, ``owned_ranges``), the only exchange is
+one-sided and happens before any arithmetic: a rank needs the A and B leaves
+that its C leaves' pairs use (``needed_leaves``), asks each owner for its
+share of them (``exchange_plan``) and receives exactly those.  For banded
+and 3D-locality patterns that is a halo of neighbouring leaves, not the
+whole operand.
 The benchmark's multi-GPU mode runs replicas instead (weak scaling, no
 collective on the data path); the helpers below also serve its timing
 (slowest rank) and totals.
@@ -33,6 +40,41 @@ def partition_units(seg_lengths, nranks: int):
         bounds.append(min(max(cut, bounds[-1]), n))
     bounds.append(n)
     return [(bounds[r], bounds[r + 1]) for r in range(nranks)]
+
+
+def owned_ranges(nleaves: int, nranks: int):
+    """Contiguous [lo, hi) ranges of an operand's Morton-ordered leaves, one
+    per rank, sizes differing by at most one: the initial distribution."""
+    if nranks <= 0:
+        raise ValueError("nranks must be positive")
+    base, extra = divmod(int(nleaves), nranks)
+    out, lo = [], 0
+    for r in range(nranks):
+        hi = lo + base + (1 if r < extra else 0)
+        out.append((lo, hi))
+        lo = hi
+    return out
+
+
+def needed_leaves(cseg, pair_a, pair_b, lo: int, hi: int):
+    """Sorted distinct A-leaf and B-leaf indices (Morton order) used by the
+    pairs of the C leaves [lo, hi): pairs cseg[lo] .. cseg[hi] - 1."""
+    cseg = np.asarray(cseg, dtype=np.int64)
+    s, e = int(cseg[lo]), int(cseg[hi])
+    return (np.unique(np.asarray(pair_a)[s:e]).astype(np.int64),
+            np.unique(np.asarray(pair_b)[s:e]).astype(np.int64))
+
+
+def exchange_plan(needed, ranges):
+    """Split sorted leaf indices by owning rank: {rank: indices owned by it},
+    ranks with nothing to send left out."""
+    needed = np.asarray(needed, dtype=np.int64)
+    starts = np.array([lo for lo, _ in ranges], dtype=np.int64)
+    ends = np.array([hi for _, hi in ranges], dtype=np.int64)
+    if needed.size and (needed[0] < starts.min() or needed[-1] >= ends.max()):
+        raise ValueError("leaf index outside every range")
+    owner = np.searchsorted(ends, needed, side="right")
+    return {int(r): needed[owner == r] for r in np.unique(owner)}
 
 
 def max_over_ranks(x: float, device="cpu") -> float:
