@@ -25,13 +25,6 @@ namespace {
 
 constexpr int kLeafThreads = 256;
 
-unsigned grid_for(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  if (g < 1) g = 1;
-  if (g > 65535LL * 8) g = 65535LL * 8;
-  return static_cast<unsigned>(g);
-}
-
 // ------------------------------------------------------------- addition --
 
 // keys[0..nA) = A's keys, keys[nA..nA+nB) = B's keys (or the diagonal keys

@@ -18,13 +18,6 @@ void split_batch_release(cht_batch *b);
 
 namespace {
 
-unsigned grid_for(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  if (g < 1) g = 1;
-  if (g > 65535LL * 8) g = 65535LL * 8;
-  return static_cast<unsigned>(g);
-}
-
 // Keys (longest segment first) and packed ids for one product's units.
 __global__ void k_batch_units(const int64_t *__restrict__ seg, int64_t n, int64_t prod,
                               int64_t off, int lpt, uint64_t *__restrict__ key,

@@ -100,13 +100,6 @@ __global__ void k_densify(const double *__restrict__ vals, const int32_t *__rest
   }
 }
 
-unsigned grid_for(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  if (g < 1) g = 1;
-  if (g > 65535LL * 8) g = 65535LL * 8;
-  return static_cast<unsigned>(g);
-}
-
 }  // namespace
 
 int bits_for(int64_t G) {

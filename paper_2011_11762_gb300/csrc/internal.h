@@ -112,6 +112,15 @@ int bits_for(int64_t G);
 // Fills brow/bcol and the row and column indexes from the sorted mkey.
 int build_pattern_index(Pattern &p, cudaStream_t s);
 
+// Blocks for a grid-stride loop over n items: ceil(n / threads), at least 1
+// and at most 8 * 65535 (the loops stride by the grid).
+inline unsigned grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 65535LL * 8) g = 65535LL * 8;
+  return static_cast<unsigned>(g);
+}
+
 // ------------------------------------------------------------ scan / sort --
 // out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
 int scan_exclusive(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);

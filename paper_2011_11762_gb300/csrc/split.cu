@@ -1135,13 +1135,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) tmem_dealloc(c.tmem, KC::TMEM_COLS);
 }
 
-unsigned grid_for(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  if (g < 1) g = 1;
-  if (g > 65535LL * 8) g = 65535LL * 8;
-  return static_cast<unsigned>(g);
-}
-
 // Scratch of one operand pair: line exponents and slices.
 struct Operands {
   DevArray<int> row_exp, col_exp;

@@ -15,13 +15,6 @@ namespace cht {
 
 namespace {
 
-unsigned grid_for(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  if (g < 1) g = 1;
-  if (g > 65535LL * 8) g = 65535LL * 8;
-  return static_cast<unsigned>(g);
-}
-
 #define GRID_STRIDE(i, n)                                                              \
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < (n); \
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
