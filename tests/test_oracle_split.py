@@ -109,3 +109,91 @@ def test_zero_rows_and_columns():
     c, e, f = sp.split_product(a, b, 6, 8)
     assert np.all(c[2] == 0.0) and np.all(c[:, 1] == 0.0)
     assert e[2] == 0 and f[1] == 0
+
+
+# ------------------------------------------------------- planted mistakes --
+# Each mutant replaces one step of the split oracle with a plausible mistake
+# (on the CPU, by patching the module); the pins above must catch every one.
+
+def _digits_unbalanced(xi, s, w):
+    # plain base-2^w digits of |x| with the sign applied: up to 2^w - 1
+    base = 1 << w
+    per = np.empty(xi.shape + (s,), dtype=np.int64)
+    for idx, v in np.ndenumerate(xi):
+        m, ds = abs(int(v)), []
+        for _ in range(s):
+            ds.append(m % base)
+            m >>= w
+        sg = -1 if v < 0 else 1
+        per[idx] = [sg * t for t in reversed(ds)]
+    return [per[..., i] for i in range(s)]
+
+
+def _digits_lost_sign(xi, s, w):
+    return [np.abs(d) for d in _ORIG["digits"](xi, s, w)]
+
+
+def _fixed_point_truncating(x, exps, axis, s, w):
+    import math
+    from fractions import Fraction
+    shape = [1, 1]
+    shape[1 - axis] = -1
+    e = np.broadcast_to(exps.reshape(shape), x.shape)
+    out = np.empty(x.shape, dtype=object)
+    for idx, v in np.ndenumerate(x):
+        q = Fraction(float(v)) * Fraction(2) ** (s * w - 1 - int(e[idx]))
+        m = math.floor(abs(q))
+        out[idx] = -m if q < 0 else m
+    return out
+
+
+def _row_exponents_high(x, axis):
+    e = _ORIG["row_exponents"](x, axis)
+    return np.where(np.max(np.abs(x), axis=axis) > 0, e + 1, e)
+
+
+def _slice_pairs_short(s, extra=False):
+    return [(i, j) for i in range(1, s + 1) for j in range(1, s + 1) if i + j <= s]
+
+
+def _to_double_doubled(v, exp2):
+    return _ORIG["_to_double"](v, exp2 + 1)
+
+
+_ORIG = {name: getattr(sp, name) for name in
+         ("digits", "fixed_point", "row_exponents", "slice_pairs", "_to_double")}
+_MUTANTS = {
+    "unbalanced_digits": ("digits", _digits_unbalanced),
+    "lost_digit_sign": ("digits", _digits_lost_sign),
+    "truncating_fixed_point": ("fixed_point", _fixed_point_truncating),
+    "exponent_one_high": ("row_exponents", _row_exponents_high),
+    "dropped_diagonal": ("slice_pairs", _slice_pairs_short),
+    "doubled_scale": ("_to_double", _to_double_doubled),
+}
+
+
+def _split_pins_hold() -> bool:
+    pins = (lambda: test_digits_reconstruct_fixed_point(6, 8),
+            test_balanced_digits_of_the_extremes,
+            test_row_exponent_brackets_the_row_max,
+            test_small_integer_matrices_are_exact,
+            lambda: test_error_within_bound(6, 8),
+            test_converges_to_fp64_product,
+            test_zero_rows_and_columns)
+    for pin in pins:
+        try:
+            pin()
+        except (AssertionError, ValueError, IndexError):
+            return False
+    return True
+
+
+def test_split_pins_hold_unmutated():
+    assert _split_pins_hold()
+
+
+@pytest.mark.parametrize("mutant", list(_MUTANTS))
+def test_split_pins_catch_planted_mistakes(monkeypatch, mutant):
+    name, fn = _MUTANTS[mutant]
+    monkeypatch.setattr(sp, name, fn)
+    assert not _split_pins_hold()
