@@ -90,3 +90,50 @@ def test_step_is_the_composition_of_the_oracle_calls():
     tu, rem = x2u.add(3.0, x3u, -2.0).truncate(eps / np.sqrt(2.0), 0)
     assert pairs == p1 + p2 and removed == rem
     assert np.array_equal(X1.to_dense(), tu.mirror_upper().to_dense())
+
+
+# ------------------------------------------------------- planted mistakes --
+# Plausible mistakes in the step, planted in the oracle on the CPU; the pins
+# against mathematics (the dense polynomial, the truncation bound) catch each.
+# The composition test above is left out: it restates the step.
+
+def _swapped_coefficients(X, eps):
+    x2u, p1 = X.multiply_upper(X)
+    x3u, p2 = x2u.mirror_upper().multiply_upper(X)
+    tu, removed = x2u.add(2.0, x3u, -3.0).truncate(eps / np.sqrt(2.0), 0)
+    return tu.mirror_upper(), removed, p1 + p2
+
+
+def _full_eps_on_the_triangle(X, eps):
+    x2u, p1 = X.multiply_upper(X)
+    x3u, p2 = x2u.mirror_upper().multiply_upper(X)
+    tu, removed = x2u.add(3.0, x3u, -2.0).truncate(eps, 0)
+    return tu.mirror_upper(), removed, p1 + p2
+
+
+def _unmirrored_square(X, eps):
+    x2u, p1 = X.multiply_upper(X)
+    x3u, p2 = x2u.multiply_upper(X)
+    tu, removed = x2u.add(3.0, x3u, -2.0).truncate(eps / np.sqrt(2.0), 0)
+    return tu.mirror_upper(), removed, p1 + p2
+
+
+def _purify_pins_hold() -> bool:
+    try:
+        test_step_without_truncation_is_the_polynomial()
+        for eps in (1e-3, 1e-2, 1e-1):
+            test_truncation_error_within_eps(eps)
+    except AssertionError:
+        return False
+    return True
+
+
+def test_purify_pins_hold_unmutated():
+    assert _purify_pins_hold()
+
+
+@pytest.mark.parametrize("mutant", [_swapped_coefficients, _full_eps_on_the_triangle,
+                                    _unmirrored_square])
+def test_purify_pins_catch_planted_mistakes(monkeypatch, mutant):
+    monkeypatch.setattr(purify, "mcweeny_step", mutant)
+    assert not _purify_pins_hold()
