@@ -264,7 +264,11 @@ static double fro2(const node *x, int lev, int bs) {
 static node *mul_spamm(const node *a, const node *b, int lev, int bs, double tau,
                        int64_t *npairs) {
     if (!a || !b) return NULL;
+#if ORC_MUTANT == 8
+    if (fro2(a, lev, bs) * fro2(b, lev, bs) < tau) return NULL; /* squared norms */
+#else
     if (sqrt(fro2(a, lev, bs)) * sqrt(fro2(b, lev, bs)) < tau) return NULL;
+#endif
     if (lev == 0) {
         node *c = new_node();
         c->leaf = (double *)xcalloc((size_t)bs * bs, sizeof(double));
@@ -594,9 +598,11 @@ int orc_mirror_upper(const orc_mat *U, orc_mat **out) {
         const int bs = U->b;
         for (int64_t l = 0; l < nl; ++l) {
             double *x = v + (size_t)l * lsz;
+#if ORC_MUTANT != 9 /* mutant 9 leaves diagonal leaves as they are */
             if (br[l] == bc[l]) /* diagonal leaf: upper triangle mirrored */
                 for (int r = 0; r < bs; ++r)
                     for (int c = 0; c < r; ++c) x[(size_t)r * bs + c] = x[(size_t)c * bs + r];
+#endif
             insert_leaf(m, br[l], bc[l], x, 0);
             if (br[l] != bc[l]) insert_leaf(m, bc[l], br[l], x, 1);
         }

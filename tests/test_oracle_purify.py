@@ -29,16 +29,27 @@ def test_gershgorin_bounds_enclose_the_spectrum():
     assert lo <= ev.min() and ev.max() <= hi
 
 
-def test_mirror_upper_of_the_oracle():
+def _mirror_pin_holds(mutant: int = 0) -> bool:
     a = w.random_blocks(64, 4, 0.4, 3, dist="uniform")
     up = a.brow <= a.bcol
     u = w.BlockMatrix(a.n, a.b, a.brow[up], a.bcol[up], a.vals[up])
     d = u.to_dense()
     # element-level upper triangle, mirrored
     ref = np.triu(d) + np.triu(d, 1).T
-    assert np.array_equal(oracle.OMatrix.from_block_matrix(u).mirror_upper().to_dense(), ref)
+    got = oracle.OMatrix.from_block_matrix(u, mutant).mirror_upper().to_dense()
+    return bool(np.array_equal(got, ref))
+
+
+def test_mirror_upper_of_the_oracle():
+    assert _mirror_pin_holds()
+    a = w.random_blocks(64, 4, 0.4, 3, dist="uniform")
     with pytest.raises(oracle.OracleError):
         oracle.OMatrix.from_block_matrix(a).mirror_upper()
+
+
+def test_mirror_pin_catches_a_planted_mistake():
+    # mutant 9 leaves the diagonal leaves unmirrored
+    assert not _mirror_pin_holds(9)
 
 
 def test_step_without_truncation_is_the_polynomial():

@@ -99,3 +99,24 @@ def test_monotone_in_tau():
     counts = [A.multiply_spamm(B, t)[1] for t in (0.0, 0.1, 0.5, 1.0, 2.0, 5.0)]
     assert all(x >= y for x, y in zip(counts, counts[1:]))
     assert counts[0] > counts[-1]
+
+
+def _spamm_pins_hold(mutant: int) -> bool:
+    """The pins above, run on an oracle build with one planted mistake."""
+    a, b = _matrices()
+    A = oracle.OMatrix.from_block_matrix(a, mutant)
+    B = oracle.OMatrix.from_block_matrix(b, mutant)
+    prods = _pairs(_leaf_norms(a), _leaf_norms(b))
+    for frac in (0.2, 0.5, 0.8):
+        tau = _safe_tau(prods, frac)
+        S, ns = A.multiply_spamm(B, tau)
+        kept = [p for p in prods if p[3] >= tau]
+        if ns != len(kept) or S.pattern() != {(i, j) for i, _, j, _ in kept}:
+            return False
+    return True
+
+
+def test_spamm_pins_catch_a_planted_mistake():
+    # mutant 8 compares the product of the squared norms with tau
+    assert _spamm_pins_hold(0)
+    assert not _spamm_pins_hold(8)
