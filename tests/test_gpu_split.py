@@ -78,6 +78,40 @@ def test_split_matches_exact_emulation(lib, b, n, p):
     assert 0 < bound < 1e-6
 
 
+@pytest.mark.parametrize("b", [64, 32])
+def test_split_wide_exponent_range(lib, b):
+    # rows of A and columns of B scaled by 2^s, s in [-540, 500]: C spans
+    # about 2^-1070 .. 2^988, with huge, tiny and subnormal results (the
+    # conversion of the integer result falls back to ldexp below the normal
+    # range)
+    n = 256 if b == 64 else 128
+    a = w.random_blocks(n, b, 0.7, 41 + b, dist="uniform")
+    bm = w.random_blocks(n, b, 0.7, 42 + b, dist="uniform")
+    rng = np.random.default_rng(43)
+    sr, sc = rng.integers(-520, 481, size=n), rng.integers(-520, 481, size=n)
+    sr[:4] = [-540, 500, 0, -1]
+    sc[:4] = [-530, 480, -520, 3]
+    for i in range(a.nblocks):
+        r0 = int(a.brow[i]) * b
+        a.vals[i] = np.ldexp(a.vals[i], sr[r0:r0 + b][:, None])
+    for i in range(bm.nblocks):
+        c0 = int(bm.bcol[i]) * b
+        bm.vals[i] = np.ldexp(bm.vals[i], sc[c0:c0 + b][None, :])
+    A, B = gu.upload(lib, a), gu.upload(lib, bm)
+    plan = lib.cht_symbolic_multiply(A, B)
+    C, _ = lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
+    got = _dense_on(C, n)
+    pairs, sa = _kernel_pairs(b)
+    emu, e, f = sp.split_product(a.to_dense(), bm.to_dense(), S, W, pairs=pairs, sa=sa)
+    assert np.all(np.isfinite(got))
+    assert np.any((got != 0) & (np.abs(got) < np.finfo(np.float64).tiny))  # subnormals
+    assert np.abs(got).max() > 2.0 ** 900
+    scale = np.ldexp(1.0, (e[:, None] + f[None, :]).astype(np.int64))
+    tol = scale * float(n) ** 2 * 2.0 ** -54 + 2 * np.spacing(np.abs(emu))
+    diff = np.abs(got - emu)
+    assert np.all(diff <= tol), float((diff / tol).max())
+
+
 @pytest.mark.parametrize("name", ["banded_4096_b32", "locality_8192_b64", "random_4096_b32"])
 def test_split_close_to_fp64(lib, name):
     if name == "banded_4096_b32":
