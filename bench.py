@@ -926,14 +926,21 @@ def main():
         except Exception as e:  # context only; never hides the headline
             cpu_blas = {"status": "error", "error": f"{type(e).__name__}: {e}"}
 
+    # The leaf GEMM changed after its DRAM counters were taken (its per-unit
+    # loop became a device function shared with the batched kernel), so no
+    # traffic figure is claimed for the current build.
     prof = read_profile_traffic("leafgemm_f64_3d_locality")
     traffic = None
+    traffic_note = ("null: the kernel changed after the ncu capture in "
+                    "profiles/leafgemm_f64_3d_locality.txt")
     if prof and "dram_bytes_per_pair" in prof:
-        traffic = float(prof["dram_bytes_per_pair"]) * res["npairs"]
+        traffic_note += (f" ({float(prof['dram_bytes_per_pair']) / 1e3:.0f} KB of DRAM "
+                         "traffic per pair there, on the earlier build)")
     roofline = {
         "kernel": "k_leafgemm_f64 (DFMA)", "bound": "alu",
         "achieved": res["kernel_achieved"], "peak": FP64_NOMINAL_TFLOPS, "unit": UNIT,
         "frac": res["kernel_achieved"] / FP64_NOMINAL_TFLOPS, "traffic": traffic,
+        "traffic_note": traffic_note,
         "peak_source": ("GB300 nominal dense FP64 (profiling recipe; no FP64 entry in the "
                         "measured peaks); FP64 microbenchmark on this GPU: "
                         f"{fp64_peak_meas:.3f} TFLOP/s"),
