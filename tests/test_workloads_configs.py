@@ -93,3 +93,32 @@ def test_random_leaves_density_and_determinism():
     assert np.array_equal(a.brow, a2.brow) and np.array_equal(a.vals, a2.vals)
     # A and B are independent draws
     assert setref.pattern_set(a.brow, a.bcol) != setref.pattern_set(b.brow, b.bcol)
+
+
+def test_batched_products_follow_their_recipe():
+    prods = w.batched_products(count=9, scale=0.125)
+    kinds = [k for k, _, _ in prods]
+    assert kinds == ["banded", "locality", "random"] * 3
+    # the 64 sizes at 1/8 scale (the same draws): multiples of 64 in
+    # [2048, 32768] / 8, log-uniform, so about half below the geometric mean
+    full = w.batched_products(count=64, scale=0.125)
+    sizes = [a.n for _, a, _ in full]
+    assert all(s % 64 == 0 and 256 - 64 <= s <= 4096 for s in sizes)
+    below = sum(s < 1024 for s in sizes)
+    assert 16 <= below <= 48
+    for kind, a, b in prods:
+        assert a.b == 32 and b.b == 32 and a.n == b.n
+        if kind == "banded":
+            assert np.all(np.abs(a.brow.astype(int) - a.bcol.astype(int)) <= 4)
+        elif kind == "locality":
+            # 64-point groups split into 32-leaves: every 2 x 2 block of
+            # 32-leaves of a stored 64-group pair is stored (zero quarters
+            # would have been dropped only if all-zero)
+            s = setref.pattern_set(a.brow, a.bcol)
+            for i, j in list(s)[:50]:
+                I, J = i // 2, j // 2
+                assert {(2 * I + p, 2 * J + q) for p in (0, 1) for q in (0, 1)} <= s
+            assert setref.pattern_set(b.brow, b.bcol) == s
+        else:
+            g = a.n // 32
+            assert abs(a.nblocks - 0.02 * g * g) < 5 * np.sqrt(0.02 * g * g) + 1
