@@ -1,0 +1,323 @@
+"""Host-side model of the split kernel's synchronisation protocol (test
+infrastructure; no GPU).
+
+One CTA of ``k_split_gemm`` runs three roles that talk only through
+mbarriers: the producer warp (unit queue slots and operand stages), the MMA
+thread (slice MMAs into TMEM accumulator regions) and eight epilogue warps
+(exact-window reads, the final read, the exchange buffer).  This module
+replays that protocol with every wait, arrival, copy completion and MMA
+completion as a separate step under a random scheduler, and checks:
+
+- no deadlock: until every role has finished, some step can run;
+- no phase aliasing: when a parity wait passes, the barrier has completed
+  exactly the phase the waiter meant (a waiter a full phase behind would
+  pass or block on the wrong phase);
+- no reuse race: an operand stage is not refilled while MMAs still read it;
+  a TMEM region is not restarted while an epilogue warp has still to read
+  its previous data, nor read while MMAs on it are in flight; a queue slot
+  is not rewritten while a role still reads it; an exchange buffer is not
+  rewritten while a warp still reads it.
+
+``kernel_roles`` mirrors the kernel's producer loop, ``mma_unit`` and
+``epi_unit``: the same barriers, arrival counts, parities and hand-off order
+(exact regions 0 and 1 restart every window of 8 [32] pairs; the low region
+2 accumulates over the unit and is read once; from the second window of a
+unit on, the first pair's region-2 MMAs go out before the wait for the
+epilogue's release).  ``mistakes`` plants one protocol error at a time so
+that the tests can show the checks catch it.
+"""
+
+from __future__ import annotations
+
+import random
+from dataclasses import dataclass, field
+
+QUEUE = 4        # unit queue slots
+EPI_WARPS = 8    # epilogue warps
+REGIONS = 3      # TMEM regions per accumulator set
+
+
+class ProtocolError(AssertionError):
+    pass
+
+
+class Barrier:
+    """An mbarrier: expected arrivals per phase, a transaction byte count and
+    the number of completed phases (whose low bit is the phase parity)."""
+
+    def __init__(self, name: str, count: int):
+        self.name, self.count = name, count
+        self.pending, self.tx, self.completed = count, 0, 0
+
+    def arrive(self, expect_tx: int = 0):
+        self.tx += expect_tx
+        self.pending -= 1
+        if self.pending < 0:
+            raise ProtocolError(f"{self.name}: more arrivals than expected in one phase")
+        self._maybe_complete()
+
+    def complete_tx(self, nbytes: int):
+        self.tx -= nbytes
+        self._maybe_complete()
+
+    def _maybe_complete(self):
+        if self.pending == 0 and self.tx == 0:
+            self.completed += 1
+            self.pending = self.count
+
+    def passes(self, phase: int) -> bool:
+        """try_wait.parity(phase & 1)."""
+        return (self.completed & 1) != (phase & 1)
+
+
+@dataclass
+class Config:
+    nb: int        # TMEM accumulator sets (2 in the 32-leaf kernel)
+    nxb: int       # exchange buffers (2 in the 32-leaf kernel)
+    stages: int    # operand stages
+    windows: dict  # pairs per exact window, by leaf size
+
+
+# the kernel taking 64-leaves (and 32-leaf units of mixed batches), and the
+# 32-leaf-only kernel
+KERNEL_64 = Config(nb=1, nxb=1, stages=2, windows={64: 8, 32: 32})
+KERNEL_32 = Config(nb=2, nxb=2, stages=2, windows={32: 32})
+
+
+@dataclass
+class State:
+    cfg: Config
+    bars: dict = field(default_factory=dict)
+    stage_busy: dict = field(default_factory=dict)     # stage -> pair still read by MMAs
+    readers: dict = field(default_factory=dict)        # (set, region) -> (tag, warps to read)
+    slot_readers: dict = field(default_factory=dict)   # slot -> roles still reading it
+    xb_use: dict = field(default_factory=dict)         # buffer -> (unit, warps still reading)
+    inflight: list = field(default_factory=list)       # issued MMAs and commits, in order
+    copies: list = field(default_factory=list)         # (barrier, bytes) in flight
+
+
+def kernel_roles(st: State, units, mistakes=frozenset()):
+    """Generators for the producer, the MMA thread and the eight epilogue
+    warps.  ``units`` is the list of (leaf size, pairs) this CTA takes.  A
+    generator yields ("wait", barrier, phase) or None (one plain step)."""
+    cfg = st.cfg
+    S = cfg.stages
+    bars = st.bars
+    for i in range(S):
+        bars[f"full{i}"] = Barrier(f"full{i}", 1)
+        bars[f"empty{i}"] = Barrier(f"empty{i}", 1)
+    for i in range(QUEUE):
+        bars[f"qfull{i}"] = Barrier(f"qfull{i}", 1)
+        bars[f"qempty{i}"] = Barrier(f"qempty{i}", 1 + EPI_WARPS)
+    for i in range(cfg.nb):
+        bars[f"acc_full{i}"] = Barrier(f"acc_full{i}", 1)
+        bars[f"acc_empty{i}"] = Barrier(f"acc_empty{i}", EPI_WARPS)
+    bars["ep_bar"] = Barrier("ep_bar", EPI_WARPS)
+    everyone = frozenset(["mma"] + [f"epi{w}" for w in range(EPI_WARPS)])
+    warps = frozenset(f"epi{w}" for w in range(EPI_WARPS))
+    slots = {}
+
+    def wait(name, phase):
+        return ("wait", bars[name], phase)
+
+    def producer():
+        k = 0
+        for n in range(len(units) + 1):
+            qs = n % QUEUE
+            yield wait(f"qempty{qs}", n // QUEUE - 1)
+            if st.slot_readers.get(qs):
+                raise ProtocolError(f"slot {qs} rewritten for unit {n} while "
+                                    f"{sorted(st.slot_readers[qs])} still read it")
+            b, np_ = units[n] if n < len(units) else (0, 0)
+            slots[qs] = (b, np_, n)
+            st.slot_readers[qs] = set(everyone)
+            bars[f"qfull{qs}"].arrive()
+            if b == 0:
+                return
+            yield None
+            for _ in range(np_):
+                s = k % S
+                if "producer_skips_empty_wait" not in mistakes:
+                    yield wait(f"empty{s}", k // S - 1)
+                if s in st.stage_busy:
+                    raise ProtocolError(f"stage {s} refilled for pair {k} while MMAs of "
+                                        f"pair {st.stage_busy[s]} still read it")
+                st.stage_busy[s] = k
+                bars[f"full{s}"].arrive(expect_tx=2)
+                st.copies.extend([(bars[f"full{s}"], 1), (bars[f"full{s}"], 1)])
+                k += 1
+                yield None
+
+    def issue(bf, region, tag, fresh):
+        key = (bf, region)
+        if fresh:
+            old = st.readers.get(key)
+            if old and old[1]:
+                raise ProtocolError(f"TMEM set {bf} region {region} restarted for {tag} while "
+                                    f"{sorted(old[1])} have not read {old[0]}")
+            st.readers[key] = (tag, set(warps))
+        st.inflight.append(("mma", key))
+
+    def mma():
+        k = 0
+        win = [0] * cfg.nb
+        for n in range(len(units) + 1):
+            qs = n % QUEUE
+            yield wait(f"qfull{qs}", n // QUEUE)
+            b, np_, _ = slots[qs]
+            st.slot_readers[qs].discard("mma")
+            if b == 0:
+                return
+            bars[f"qempty{qs}"].arrive()
+            bf = n % cfg.nb
+            W = cfg.windows[b]
+            fresh = [True] * REGIONS
+            for w0 in range(0, np_, W):
+                ahead = w0 != 0
+                if not ahead and "mma_skips_unit_wait" not in mistakes:
+                    yield wait(f"acc_empty{bf}", win[bf] - 1)
+                for i in range(w0, min(np_, w0 + W)):
+                    s = k % S
+                    yield wait(f"full{s}", k // S)
+                    exact_tag, low_tag = (n, win[bf]), (n, "low")
+                    if i == w0 and ahead:
+                        issue(bf, 2, low_tag, fresh[2])
+                        fresh[2] = False
+                        if "mma_skips_window_wait" not in mistakes:
+                            yield wait(f"acc_empty{bf}", win[bf] - 1)
+                    if i == w0:
+                        fresh[0] = fresh[1] = True
+                    for r in range(REGIONS):
+                        if r == 2 and i == w0 and ahead:
+                            continue
+                        issue(bf, r, exact_tag if r < 2 else low_tag, fresh[r])
+                        fresh[r] = False
+                    st.inflight.append(("commit", bars[f"empty{s}"], k))
+                    k += 1
+                    yield None
+                st.inflight.append(("commit", bars[f"acc_full{bf}"], None))
+                win[bf] += 1
+                yield None
+
+    def read(me, bf, region, tag):
+        key = (bf, region)
+        if any(op[0] == "mma" and op[1] == key for op in st.inflight):
+            raise ProtocolError(f"{me} reads TMEM set {bf} region {region} ({tag}) while "
+                                f"MMAs on it are in flight")
+        cur = st.readers.get(key)
+        if cur is None or cur[0] != tag or me not in cur[1]:
+            raise ProtocolError(f"{me} expected {tag} in TMEM set {bf} region {region}, "
+                                f"found {cur and cur[0]}")
+        cur[1].discard(me)
+
+    def epilogue(wid):
+        me = f"epi{wid}"
+        win = [0] * cfg.nb
+        epb = 0
+        for n in range(len(units) + 1):
+            qs = n % QUEUE
+            yield wait(f"qfull{qs}", n // QUEUE)
+            b, np_, _ = slots[qs]
+            if b == 0:
+                st.slot_readers[qs].discard(me)
+                return
+            bf = 0 if "epi_single_accumulator_set" in mistakes else n % cfg.nb
+            W = cfg.windows[b]
+            for w0 in range(0, np_, W):
+                last = w0 + W >= np_
+                yield wait(f"acc_full{bf}", win[bf])
+                for r in (0, 1):
+                    read(me, bf, r, (n, win[bf]))
+                if not last:
+                    bars[f"acc_empty{bf}"].arrive()
+                    win[bf] += 1
+                    yield None
+                    continue
+                early = "epi_releases_before_low_read" in mistakes
+                if early:
+                    bars[f"acc_empty{bf}"].arrive()
+                    yield None
+                read(me, bf, 2, (n, "low"))
+                if not early:
+                    bars[f"acc_empty{bf}"].arrive()
+                win[bf] += 1
+                yield None
+            # the final conversion uses the slot's exponents and C pointer
+            if slots[qs][2] != n:
+                raise ProtocolError(f"{me}: slot {qs} of unit {n} was rewritten for unit "
+                                    f"{slots[qs][2]} while still in use")
+            # exchange: write this warp's values, meet, read the others'
+            xb = n % cfg.nxb
+            use = st.xb_use.get(xb)
+            if use and use[0] != n and use[1]:
+                raise ProtocolError(f"exchange buffer {xb} rewritten by {me} for unit {n} "
+                                    f"while {sorted(use[1])} still read unit {use[0]}")
+            if not use or use[0] != n:
+                st.xb_use[xb] = (n, set(warps))
+            bars["ep_bar"].arrive()
+            yield wait("ep_bar", epb)
+            epb += 1
+            yield None  # reads
+            st.xb_use[xb][1].discard(me)
+            if cfg.nxb == 1 and "no_second_exchange_barrier" not in mistakes:
+                bars["ep_bar"].arrive()
+                yield wait("ep_bar", epb)
+                epb += 1
+            st.slot_readers[qs].discard(me)
+            bars[f"qempty{qs}"].arrive()
+            yield None
+
+    roles = {"producer": producer(), "mma": mma()}
+    for wid in range(EPI_WARPS):
+        roles[f"epi{wid}"] = epilogue(wid)
+    return roles
+
+
+def run(cfg: Config, units, seed: int, mistakes=frozenset(), max_steps: int = 2_000_000):
+    """Replay the protocol under one random schedule; raises ProtocolError on
+    a deadlock, a phase aliasing or a reuse race."""
+    rng = random.Random(seed)
+    st = State(cfg)
+    roles = kernel_roles(st, units, mistakes)
+    waiting, done = {}, set()
+
+    def advance(name):
+        try:
+            waiting[name] = next(roles[name])
+        except StopIteration:
+            done.add(name)
+            waiting.pop(name, None)
+
+    for name in list(roles):
+        advance(name)
+    for _ in range(max_steps):
+        if len(done) == len(roles) and not st.inflight and not st.copies:
+            return
+        runnable = [name for name, req in waiting.items()
+                    if req is None or req[1].passes(req[2])]
+        choices = [("role", name) for name in runnable]
+        if st.copies:
+            choices.append(("copy", None))
+        if st.inflight:
+            choices.append(("tensor", None))
+        if not choices:
+            blocked = {n: (r[1].name, r[2]) for n, r in waiting.items() if r is not None}
+            raise ProtocolError(f"deadlock: {blocked}")
+        kind, name = rng.choice(choices)
+        if kind == "copy":
+            bar, nbytes = st.copies.pop(rng.randrange(len(st.copies)))
+            bar.complete_tx(nbytes)
+        elif kind == "tensor":
+            op = st.inflight.pop(0)  # MMAs and commits complete in issue order
+            if op[0] == "commit":
+                _, bar, pair = op
+                if pair is not None and st.stage_busy.get(pair % cfg.stages) == pair:
+                    del st.stage_busy[pair % cfg.stages]
+                bar.arrive()
+        else:
+            req = waiting[name]
+            if req is not None and req[1].completed != req[2] + 1:
+                raise ProtocolError(f"{name}: waited for phase {req[2]} of {req[1].name}, "
+                                    f"which has completed {req[1].completed} phases")
+            advance(name)
+    raise ProtocolError("step limit reached")

@@ -1,0 +1,74 @@
+"""The split kernel's barrier protocol, replayed on the host under random
+schedules (tests/split_protocol.py): no deadlock, no phase aliasing and no
+reuse race for random unit sequences (one or many exact windows per unit,
+mixed leaf sizes), in both kernel configurations; each planted protocol
+mistake is caught."""
+
+from __future__ import annotations
+
+import random
+
+import pytest
+
+from tests import split_protocol as sp
+
+
+def _units(seed: int, sizes, windows):
+    rng = random.Random(seed)
+    out = []
+    for _ in range(rng.randint(1, 9)):
+        b = rng.choice(sizes)
+        w = windows[b]
+        out.append((b, rng.choice([1, 2, w - 1, w, w + 1, 2 * w, 3 * w + 1,
+                                   rng.randint(1, 3 * w + 2)])))
+    return out
+
+
+CASES = {
+    "kernel64_b64": (sp.KERNEL_64, (64,)),
+    "kernel64_mixed": (sp.KERNEL_64, (64, 32)),
+    "kernel32": (sp.KERNEL_32, (32,)),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_protocol_holds_under_random_schedules(case):
+    cfg, sizes = CASES[case]
+    for seed in range(60):
+        sp.run(cfg, _units(seed, sizes, cfg.windows), seed)
+
+
+def test_protocol_with_no_units_and_one_pair():
+    for cfg, sizes in CASES.values():
+        sp.run(cfg, [], 0)
+        sp.run(cfg, [(sizes[0], 1)], 1)
+
+
+MISTAKES = {
+    # the MMA restarts the exact regions without the epilogue's release
+    "mma_skips_window_wait": ("kernel64_b64", 8),
+    # the MMA starts a unit while the previous unit's data is unread
+    "mma_skips_unit_wait": ("kernel64_b64", 8),
+    # the epilogue releases TMEM before it has read the low region
+    "epi_releases_before_low_read": ("kernel64_b64", 8),
+    # a single exchange buffer without the barrier after the reads
+    "no_second_exchange_barrier": ("kernel64_b64", 8),
+    # the producer refills a stage the MMAs may still read
+    "producer_skips_empty_wait": ("kernel32", 32),
+    # the epilogue reads one accumulator set while the MMA alternates two
+    "epi_single_accumulator_set": ("kernel32", 32),
+}
+
+
+@pytest.mark.parametrize("mistake", list(MISTAKES))
+def test_planted_protocol_mistakes_are_caught(mistake):
+    case, w = MISTAKES[mistake]
+    cfg, sizes = CASES[case]
+    units = [(sizes[0], n) for n in (1, 2 * w + 3, 1, w, 3, 1, 2 * w, 1)]
+    caught = 0
+    for seed in range(300):
+        try:
+            sp.run(cfg, units, seed, mistakes=frozenset([mistake]))
+        except sp.ProtocolError:
+            caught += 1
+    assert caught > 0, mistake
