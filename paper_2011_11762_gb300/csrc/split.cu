@@ -40,9 +40,10 @@
 // Roles (320 threads): warp 0 = bulk-copy producer, warp 1 = TMEM owner and
 // MMA issuer (one thread), warps 2..9 = epilogue (two warps per TMEM lane
 // quarter, splitting the columns).  Units are the C leaves in Morton order,
-// taken two at a time from an atomic counter by the persistent CTAs
-// (neighbouring leaves run together, so their A and B slices are shared
-// through L2).  A C leaf with more pairs than a unit may sum is cut into
+// taken from an atomic counter by the persistent CTAs a chunk at a time (2
+// units in the kernel for 64-leaves, 32 in the 32-leaf kernel), so
+// neighbouring leaves run together and share their A and B slices through
+// L2.  A C leaf with more pairs than a unit may sum is cut into
 // pieces added afterwards in FP64.  Every wait is bounded.
 #include <algorithm>
 
