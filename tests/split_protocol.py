@@ -15,16 +15,21 @@ completion as a separate step under a random scheduler, and checks:
 - no reuse race: an operand stage is not refilled while MMAs still read it;
   a TMEM region is not restarted while an epilogue warp has still to read
   its previous data, nor read while MMAs on it are in flight; a queue slot
-  is not rewritten while a role still reads it; an exchange buffer is not
-  rewritten while a warp still reads it.
+  is not rewritten while a role still uses it; an exchange buffer is not
+  rewritten while a warp still reads it;
+- a clean exit: when the roles end (the CTA then frees TMEM and its shared
+  memory) no copy and no MMA is in flight, also after a wait ran out of time.
 
-``kernel_roles`` mirrors the kernel's producer loop, ``mma_unit`` and
-``epi_unit``: the same barriers, arrival counts, parities and hand-off order
-(exact regions 0 and 1 restart every window of 8 [32] pairs; the low region
-2 accumulates over the unit and is read once; from the second window of a
-unit on, the first pair's region-2 MMAs go out before the wait for the
-epilogue's release).  ``mistakes`` plants one protocol error at a time so
-that the tests can show the checks catch it.
+``kernel_roles`` mirrors the kernel's producer loop, ``mma_unit``,
+``epi_unit`` and their exits: the same barriers, arrival counts, parities and
+hand-off order (exact regions 0 and 1 restart every window of 8 [32] pairs;
+the low region 2 accumulates over the unit and is read once; from the second
+window of a unit on, the first pair's region-2 MMAs go out before the wait
+for the epilogue's release).  A wait that gives up (its budget ran out, or
+another role set the abort flag) returns False, as ``wait_or_abort`` does;
+the producer then waits for its copies in flight and the MMA thread for its
+MMAs (bounded drain waits that ignore the flag).  ``mistakes`` plants one
+protocol error at a time so that the tests can show the checks catch it.
 """
 
 from __future__ import annotations
@@ -90,16 +95,20 @@ class State:
     bars: dict = field(default_factory=dict)
     stage_busy: dict = field(default_factory=dict)     # stage -> pair still read by MMAs
     readers: dict = field(default_factory=dict)        # (set, region) -> (tag, warps to read)
-    slot_readers: dict = field(default_factory=dict)   # slot -> roles still reading it
+    slot_readers: dict = field(default_factory=dict)   # slot -> roles still using it
     xb_use: dict = field(default_factory=dict)         # buffer -> (unit, warps still reading)
     inflight: list = field(default_factory=list)       # issued MMAs and commits, in order
     copies: list = field(default_factory=list)         # (barrier, bytes) in flight
+    abort: bool = False                                # the kernel's abort flag
+    status_timeout: bool = False                       # the device status word
 
 
 def kernel_roles(st: State, units, mistakes=frozenset()):
     """Generators for the producer, the MMA thread and the eight epilogue
     warps.  ``units`` is the list of (leaf size, pairs) this CTA takes.  A
-    generator yields ("wait", barrier, phase) or None (one plain step)."""
+    generator yields ("wait", barrier, phase, abortable) and receives True
+    (the phase completed) or False (it gave up), or yields None (one plain
+    step)."""
     cfg = st.cfg
     S = cfg.stages
     bars = st.bars
@@ -113,32 +122,43 @@ def kernel_roles(st: State, units, mistakes=frozenset()):
         bars[f"acc_full{i}"] = Barrier(f"acc_full{i}", 1)
         bars[f"acc_empty{i}"] = Barrier(f"acc_empty{i}", EPI_WARPS)
     bars["ep_bar"] = Barrier("ep_bar", EPI_WARPS)
+    bars["drain"] = Barrier("drain", 1)
     everyone = frozenset(["mma"] + [f"epi{w}" for w in range(EPI_WARPS)])
     warps = frozenset(f"epi{w}" for w in range(EPI_WARPS))
     slots = {}
 
-    def wait(name, phase):
-        return ("wait", bars[name], phase)
+    def wait(name, phase, abortable=True):
+        return ("wait", bars[name], phase, abortable)
+
+    def fail():
+        st.status_timeout = True
+        st.abort = True
 
     def producer():
         k = 0
+        ok = True
         for n in range(len(units) + 1):
             qs = n % QUEUE
-            yield wait(f"qempty{qs}", n // QUEUE - 1)
+            if not (yield wait(f"qempty{qs}", n // QUEUE - 1)):
+                fail()
+                break
             if st.slot_readers.get(qs):
                 raise ProtocolError(f"slot {qs} rewritten for unit {n} while "
-                                    f"{sorted(st.slot_readers[qs])} still read it")
+                                    f"{sorted(st.slot_readers[qs])} still use it")
             b, np_ = units[n] if n < len(units) else (0, 0)
             slots[qs] = (b, np_, n)
             st.slot_readers[qs] = set(everyone)
             bars[f"qfull{qs}"].arrive()
             if b == 0:
-                return
+                break
             yield None
             for _ in range(np_):
                 s = k % S
                 if "producer_skips_empty_wait" not in mistakes:
-                    yield wait(f"empty{s}", k // S - 1)
+                    ok = yield wait(f"empty{s}", k // S - 1)
+                    if not ok:
+                        fail()
+                        break
                 if s in st.stage_busy:
                     raise ProtocolError(f"stage {s} refilled for pair {k} while MMAs of "
                                         f"pair {st.stage_busy[s]} still read it")
@@ -147,6 +167,12 @@ def kernel_roles(st: State, units, mistakes=frozenset()):
                 st.copies.extend([(bars[f"full{s}"], 1), (bars[f"full{s}"], 1)])
                 k += 1
                 yield None
+            if not ok:
+                break
+        # copies in flight land before shared memory goes away
+        if "producer_no_drain" not in mistakes:
+            for j in range(max(0, k - S), k):
+                yield wait(f"full{j % S}", j // S, abortable=False)
 
     def issue(bf, region, tag, fresh):
         key = (bf, region)
@@ -158,46 +184,61 @@ def kernel_roles(st: State, units, mistakes=frozenset()):
             st.readers[key] = (tag, set(warps))
         st.inflight.append(("mma", key))
 
+    def mma_unit(n, np_, W, bf, win, k):
+        """One unit; returns (ok, pairs consumed)."""
+        fresh = [True] * REGIONS
+        for w0 in range(0, np_, W):
+            ahead = w0 != 0
+            if not ahead and "mma_skips_unit_wait" not in mistakes:
+                if not (yield wait(f"acc_empty{bf}", win[bf] - 1)):
+                    return False, k
+            for i in range(w0, min(np_, w0 + W)):
+                s = k % S
+                if not (yield wait(f"full{s}", k // S)):
+                    return False, k
+                exact_tag, low_tag = (n, win[bf]), (n, "low")
+                if i == w0 and ahead:
+                    issue(bf, 2, low_tag, fresh[2])
+                    fresh[2] = False
+                    if "mma_skips_window_wait" not in mistakes:
+                        if not (yield wait(f"acc_empty{bf}", win[bf] - 1)):
+                            return False, k
+                if i == w0:
+                    fresh[0] = fresh[1] = True
+                for r in range(REGIONS):
+                    if r == 2 and i == w0 and ahead:
+                        continue
+                    issue(bf, r, exact_tag if r < 2 else low_tag, fresh[r])
+                    fresh[r] = False
+                st.inflight.append(("commit", bars[f"empty{s}"], k))
+                k += 1
+                yield None
+            st.inflight.append(("commit", bars[f"acc_full{bf}"], None))
+            win[bf] += 1
+            yield None
+        return True, k
+
     def mma():
         k = 0
         win = [0] * cfg.nb
         for n in range(len(units) + 1):
             qs = n % QUEUE
-            yield wait(f"qfull{qs}", n // QUEUE)
+            if not (yield wait(f"qfull{qs}", n // QUEUE)):
+                fail()
+                break
             b, np_, _ = slots[qs]
             st.slot_readers[qs].discard("mma")
             if b == 0:
-                return
+                break
             bars[f"qempty{qs}"].arrive()
-            bf = n % cfg.nb
-            W = cfg.windows[b]
-            fresh = [True] * REGIONS
-            for w0 in range(0, np_, W):
-                ahead = w0 != 0
-                if not ahead and "mma_skips_unit_wait" not in mistakes:
-                    yield wait(f"acc_empty{bf}", win[bf] - 1)
-                for i in range(w0, min(np_, w0 + W)):
-                    s = k % S
-                    yield wait(f"full{s}", k // S)
-                    exact_tag, low_tag = (n, win[bf]), (n, "low")
-                    if i == w0 and ahead:
-                        issue(bf, 2, low_tag, fresh[2])
-                        fresh[2] = False
-                        if "mma_skips_window_wait" not in mistakes:
-                            yield wait(f"acc_empty{bf}", win[bf] - 1)
-                    if i == w0:
-                        fresh[0] = fresh[1] = True
-                    for r in range(REGIONS):
-                        if r == 2 and i == w0 and ahead:
-                            continue
-                        issue(bf, r, exact_tag if r < 2 else low_tag, fresh[r])
-                        fresh[r] = False
-                    st.inflight.append(("commit", bars[f"empty{s}"], k))
-                    k += 1
-                    yield None
-                st.inflight.append(("commit", bars[f"acc_full{bf}"], None))
-                win[bf] += 1
-                yield None
+            ok, k = yield from mma_unit(n, np_, cfg.windows[b], n % cfg.nb, win, k)
+            if not ok:
+                fail()
+                break
+        # in-flight MMAs finish before TMEM is released
+        if "mma_no_drain" not in mistakes:
+            st.inflight.append(("commit", bars["drain"], None))
+            yield wait("drain", 0, abortable=False)
 
     def read(me, bf, region, tag):
         key = (bf, region)
@@ -210,58 +251,72 @@ def kernel_roles(st: State, units, mistakes=frozenset()):
                                 f"found {cur and cur[0]}")
         cur[1].discard(me)
 
+    def epi_unit(me, n, qs, np_, W, bf, win, epb):
+        """One unit; returns (ok, exchange barrier uses)."""
+        for w0 in range(0, np_, W):
+            last = w0 + W >= np_
+            if not (yield wait(f"acc_full{bf}", win[bf])):
+                return False, epb
+            for r in (0, 1):
+                read(me, bf, r, (n, win[bf]))
+            if not last:
+                bars[f"acc_empty{bf}"].arrive()
+                win[bf] += 1
+                yield None
+                continue
+            early = "epi_releases_before_low_read" in mistakes
+            if early:
+                bars[f"acc_empty{bf}"].arrive()
+                yield None
+            read(me, bf, 2, (n, "low"))
+            if not early:
+                bars[f"acc_empty{bf}"].arrive()
+            win[bf] += 1
+            yield None
+        # the final conversion uses the slot's exponents and C pointer
+        if slots[qs][2] != n:
+            raise ProtocolError(f"{me}: slot {qs} of unit {n} was rewritten for unit "
+                                f"{slots[qs][2]} while still in use")
+        # exchange: write this warp's values, meet, read the others'
+        xb = n % cfg.nxb
+        use = st.xb_use.get(xb)
+        if use and use[0] != n and use[1]:
+            raise ProtocolError(f"exchange buffer {xb} rewritten by {me} for unit {n} "
+                                f"while {sorted(use[1])} still read unit {use[0]}")
+        if not use or use[0] != n:
+            st.xb_use[xb] = (n, set(warps))
+        bars["ep_bar"].arrive()
+        if not (yield wait("ep_bar", epb)):
+            return False, epb
+        epb += 1
+        yield None  # reads
+        st.xb_use[xb][1].discard(me)
+        return True, epb
+
     def epilogue(wid):
         me = f"epi{wid}"
         win = [0] * cfg.nb
         epb = 0
         for n in range(len(units) + 1):
             qs = n % QUEUE
-            yield wait(f"qfull{qs}", n // QUEUE)
+            if not (yield wait(f"qfull{qs}", n // QUEUE)):
+                fail()
+                break
             b, np_, _ = slots[qs]
             if b == 0:
                 st.slot_readers[qs].discard(me)
-                return
+                break
             bf = 0 if "epi_single_accumulator_set" in mistakes else n % cfg.nb
-            W = cfg.windows[b]
-            for w0 in range(0, np_, W):
-                last = w0 + W >= np_
-                yield wait(f"acc_full{bf}", win[bf])
-                for r in (0, 1):
-                    read(me, bf, r, (n, win[bf]))
-                if not last:
-                    bars[f"acc_empty{bf}"].arrive()
-                    win[bf] += 1
-                    yield None
-                    continue
-                early = "epi_releases_before_low_read" in mistakes
-                if early:
-                    bars[f"acc_empty{bf}"].arrive()
-                    yield None
-                read(me, bf, 2, (n, "low"))
-                if not early:
-                    bars[f"acc_empty{bf}"].arrive()
-                win[bf] += 1
-                yield None
-            # the final conversion uses the slot's exponents and C pointer
-            if slots[qs][2] != n:
-                raise ProtocolError(f"{me}: slot {qs} of unit {n} was rewritten for unit "
-                                    f"{slots[qs][2]} while still in use")
-            # exchange: write this warp's values, meet, read the others'
-            xb = n % cfg.nxb
-            use = st.xb_use.get(xb)
-            if use and use[0] != n and use[1]:
-                raise ProtocolError(f"exchange buffer {xb} rewritten by {me} for unit {n} "
-                                    f"while {sorted(use[1])} still read unit {use[0]}")
-            if not use or use[0] != n:
-                st.xb_use[xb] = (n, set(warps))
-            bars["ep_bar"].arrive()
-            yield wait("ep_bar", epb)
-            epb += 1
-            yield None  # reads
-            st.xb_use[xb][1].discard(me)
+            ok, epb = yield from epi_unit(me, n, qs, np_, cfg.windows[b], bf, win, epb)
+            if not ok:
+                fail()
+                break
             if cfg.nxb == 1 and "no_second_exchange_barrier" not in mistakes:
+                # one exchange buffer: every warp has read it before the next unit
                 bars["ep_bar"].arrive()
-                yield wait("ep_bar", epb)
+                if not (yield wait("ep_bar", epb)):
+                    fail()
+                    break
                 epb += 1
             st.slot_readers[qs].discard(me)
             bars[f"qempty{qs}"].arrive()
@@ -273,29 +328,45 @@ def kernel_roles(st: State, units, mistakes=frozenset()):
     return roles
 
 
-def run(cfg: Config, units, seed: int, mistakes=frozenset(), max_steps: int = 2_000_000):
-    """Replay the protocol under one random schedule; raises ProtocolError on
-    a deadlock, a phase aliasing or a reuse race."""
+def run(cfg: Config, units, seed: int, mistakes=frozenset(), timeout=None,
+        max_steps: int = 2_000_000) -> State:
+    """Replay the protocol under one random schedule and return the final
+    state; raises ProtocolError on a deadlock, a phase aliasing, a reuse race
+    or an unclean exit.  ``timeout`` = (role, i): from the role's i-th
+    abortable wait on, its first wait that would block runs out of time."""
     rng = random.Random(seed)
     st = State(cfg)
     roles = kernel_roles(st, units, mistakes)
     waiting, done = {}, set()
+    nwaits = {name: 0 for name in roles}
 
-    def advance(name):
+    def advance(name, value=None):
         try:
-            waiting[name] = next(roles[name])
+            req = next(roles[name]) if value is None else roles[name].send(value)
         except StopIteration:
             done.add(name)
             waiting.pop(name, None)
+            return
+        if req is not None and req[3]:
+            nwaits[name] += 1
+        waiting[name] = req
+
+    def gives_up(name, req):
+        if not req[3]:
+            return False
+        return st.abort or (timeout is not None and name == timeout[0]
+                            and nwaits[name] > timeout[1])
 
     for name in list(roles):
         advance(name)
     for _ in range(max_steps):
-        if len(done) == len(roles) and not st.inflight and not st.copies:
-            return
-        runnable = [name for name, req in waiting.items()
-                    if req is None or req[1].passes(req[2])]
-        choices = [("role", name) for name in runnable]
+        if len(done) == len(roles):
+            if st.inflight or st.copies:
+                raise ProtocolError(f"the roles ended with {len(st.inflight)} MMA operations "
+                                    f"and {len(st.copies)} copies in flight")
+            return st
+        choices = [("role", name) for name, req in waiting.items()
+                   if req is None or req[1].passes(req[2]) or gives_up(name, req)]
         if st.copies:
             choices.append(("copy", None))
         if st.inflight:
@@ -316,8 +387,13 @@ def run(cfg: Config, units, seed: int, mistakes=frozenset(), max_steps: int = 2_
                 bar.arrive()
         else:
             req = waiting[name]
-            if req is not None and req[1].completed != req[2] + 1:
-                raise ProtocolError(f"{name}: waited for phase {req[2]} of {req[1].name}, "
-                                    f"which has completed {req[1].completed} phases")
-            advance(name)
+            if req is None:
+                advance(name)
+            elif req[1].passes(req[2]):
+                if req[1].completed != req[2] + 1:
+                    raise ProtocolError(f"{name}: waited for phase {req[2]} of {req[1].name}, "
+                                        f"which has completed {req[1].completed} phases")
+                advance(name, True)
+            else:
+                advance(name, False)  # budget expired, or the abort flag is set
     raise ProtocolError("step limit reached")

@@ -72,3 +72,35 @@ def test_planted_protocol_mistakes_are_caught(mistake):
         except sp.ProtocolError:
             caught += 1
     assert caught > 0, mistake
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_timeouts_end_cleanly(case):
+    # one role's wait runs out of time at a random point: the abort reaches
+    # every role, the status word records it, and no copy or MMA is left in
+    # flight when the roles end
+    cfg, sizes = CASES[case]
+    rng = random.Random(11)
+    aborted = 0
+    for seed in range(80):
+        units = _units(seed, sizes, cfg.windows)
+        role = rng.choice(["producer", "mma", "epi0", "epi5"])
+        st = sp.run(cfg, units, seed, timeout=(role, rng.randint(0, 12)))
+        if st.abort:
+            aborted += 1
+            assert st.status_timeout
+    assert aborted >= 20
+
+
+@pytest.mark.parametrize("mistake", ["producer_no_drain", "mma_no_drain"])
+def test_missing_drain_is_caught(mistake):
+    cfg, sizes = CASES["kernel64_b64"]
+    units = [(64, n) for n in (20, 3, 17, 1, 9)]
+    caught = 0
+    for seed in range(200):
+        role = ("mma", "producer", "epi2")[seed % 3]
+        try:
+            sp.run(cfg, units, seed, mistakes=frozenset([mistake]), timeout=(role, seed % 7))
+        except sp.ProtocolError:
+            caught += 1
+    assert caught > 0
