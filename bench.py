@@ -784,11 +784,12 @@ def oracle_sample(a, b, target_s: float):
         _ = np
 
 
-def blas_cpu_sample(a, b, rows: int):
+def blas_cpu_sample(a, b, rows: int, *, return_product: bool = False):
     """The paper's own CPU design on the same slice as the oracle sample: the
     same (A-leaf, B-leaf) pair lists, every leaf product a BLAS call (torch
     CPU FP64 batched matmul, all cores), summed into C by index.  Returns
-    (tflops, seconds, pairs, threads)."""
+    (tflops, seconds, pairs, threads), plus (C leaf rows, C leaf columns, C
+    leaves) in row-major leaf order with ``return_product``."""
     import numpy as np
     import torch
     g = a.grid
@@ -816,7 +817,11 @@ def blas_cpu_sample(a, b, rows: int):
         prod = torch.bmm(at[pa_t[s0:s0 + chunk]], bt[pb_t[s0:s0 + chunk]])
         c.index_add_(0, ci[s0:s0 + chunk], prod)
     dt = time.perf_counter() - t0
-    return 2 * a.b ** 3 * pa.size / dt / 1e12, dt, int(pa.size), threads
+    out = (2 * a.b ** 3 * pa.size / dt / 1e12, dt, int(pa.size), threads)
+    if return_product:
+        keys = np.unique(ckey)
+        out += ((keys // g).astype(np.int32), (keys % g).astype(np.int32), c.numpy())
+    return out
 
 
 def reference_arm(args, rank, world):

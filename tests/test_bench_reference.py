@@ -61,3 +61,34 @@ def test_reference_arm_two_ranks_rank0_prints_once():
     lines = _json_lines(r.stdout)
     assert len(lines) == 1
     _check_line(lines[0], 2)
+
+
+def test_paper_style_cpu_sample_computes_the_slice():
+    # the BLAS-per-leaf baseline times the real product: its C leaves equal
+    # the oracle's single-leaf products on the same slice, and its pair count
+    # equals the oracle's for that slice
+    import importlib.util
+
+    import numpy as np
+
+    import oracle
+    import workloads as w
+    spec = importlib.util.spec_from_file_location("bench_under_test",
+                                                  os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    a, b = w.config1(1024, 32, 3)
+    rows = 5
+    tf, dt, pairs, threads, crow, ccol, cv = bench.blas_cpu_sample(a, b, rows,
+                                                                    return_product=True)
+    assert tf > 0 and dt > 0 and threads >= 1
+    keep = a.brow < rows
+    sa = w.BlockMatrix(a.n, a.b, a.brow[keep], a.bcol[keep], a.vals[keep])
+    OA, OB = oracle.OMatrix.from_block_matrix(sa), oracle.OMatrix.from_block_matrix(b)
+    C, npairs = OA.multiply(OB)
+    assert pairs == npairs
+    assert set(zip(crow.tolist(), ccol.tolist())) == C.pattern()
+    for i, (r, c) in enumerate(zip(crow, ccol)):
+        ref, present = oracle.leaf_product(OA, OB, int(r), int(c))
+        assert present
+        assert np.allclose(cv[i], ref, rtol=1e-13, atol=1e-13)
