@@ -67,13 +67,11 @@ struct Cfg;
 template <>
 struct Cfg<64> {
   // N is the MMA width: two B slices side by side (2 b columns)
-  static constexpr int N = 128, PARTS = 2, SA = 6, KSTEPS = 4, STAGES = 2, WINDOW = 8;
-  static constexpr int TMEM_COLS = 512;
+  static constexpr int N = 128, PARTS = 2, SA = 6, KSTEPS = 4, WINDOW = 8;
 };
 template <>
 struct Cfg<32> {
-  static constexpr int N = 64, PARTS = 4, SA = 8, KSTEPS = 2, STAGES = 3, WINDOW = 32;
-  static constexpr int TMEM_COLS = 256;
+  static constexpr int N = 64, PARTS = 4, SA = 8, KSTEPS = 2, WINDOW = 32;
 };
 
 // MMA blocks (first stacked A slice u, first B slice j; both odd), 1-based.
@@ -102,8 +100,6 @@ struct Smem {
   static constexpr int STAGE = A_BYTES + B_BYTES;
   // exchange buffer: b = 64 hands part 1 to part 0; b = 32 gathers all 4 parts
   static constexpr int XBUF = (B == 64 ? 1 : Cfg<B>::PARTS) * B * B * 8;
-  static constexpr int TOTAL = Cfg<B>::STAGES * STAGE + XBUF + 256;
-  static constexpr size_t DYN = TOTAL + 1024;  // + alignment slack
 };
 
 // ------------------------------------------------------------ tcgen05 PTX --
