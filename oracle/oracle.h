@@ -26,21 +26,27 @@ extern "C" {
 
 typedef struct orc_mat orc_mat;
 
-/* Build a quadtree from a list of leaves (any order).  Leaf i sits at leaf
+/* Build a quadtree from a list of leaves (any order): the paper's assignment
+ * from matrix elements (Section 2.2: construction from row and column
+ * indices and values), at leaf granularity.  Leaf i sits at leaf
  * coordinates (brow[i], bcol[i]) and holds vals[i*b*b .. (i+1)*b*b) in
  * row-major order.  Leaves whose values are all zero are identically zero
- * and are not stored (nil).  n must be a positive multiple of b. */
+ * and are not stored (nil, Section 2).  n must be a positive multiple of b. */
 int orc_build(int64_t n, int32_t b, int64_t nblk, const int32_t *brow,
               const int32_t *bcol, const double *vals, orc_mat **out);
 
-/* C = A*B by the recursive quadtree algorithm; *npairs (may be NULL) gets the
- * number of leaf-times-leaf products performed. */
+/* C = A*B by the recursive quadtree algorithm (paper, Section 2: operations
+ * recurse over the non-nil branches, a nil operand gives a nil product;
+ * Section 2.2 lists the matrix-matrix multiplication); *npairs (may be
+ * NULL) gets the number of leaf-times-leaf products performed. */
 int orc_multiply(const orc_mat *A, const orc_mat *B, orc_mat **C,
                  int64_t *npairs);
 
-/* Sparse approximate product (SpAMM): the multiply recursion in which a
- * quadrant product is skipped (nil) whenever ||A_sub||_F * ||B_sub||_F < tau,
- * tested at every level including the leaves.  tau = 0 is orc_multiply. */
+/* Sparse approximate product (SpAMM; paper, Sections 1 and 2.2: the sparse
+ * approximate multiplication for matrices with decay): the multiply
+ * recursion in which a quadrant product is skipped (nil) whenever
+ * ||A_sub||_F * ||B_sub||_F < tau, tested at every level including the
+ * leaves.  tau = 0 is orc_multiply. */
 int orc_multiply_spamm(const orc_mat *A, const orc_mat *B, double tau,
                        orc_mat **C, int64_t *npairs);
 
@@ -78,19 +84,22 @@ int orc_truncate(const orc_mat *M, double eps, int kind, orc_mat **out, double *
  * below the diagonal. */
 int orc_mirror_upper(const orc_mat *U, orc_mat **out);
 
-/* Transpose (a new matrix). */
+/* Transpose (a new matrix); a helper of the backward products below. */
 int orc_transpose(const orc_mat *A, orc_mat **out);
 
 /* The matrix with exactly M's pattern whose leaves are X's leaves where X has
- * one and zero leaves elsewhere. */
+ * one and zero leaves elsewhere; the pattern restriction of the backward
+ * products below. */
 int orc_restrict(const orc_mat *X, const orc_mat *M, orc_mat **out);
 
-/* Gradients of L = f(C), C = A*B, given dC = dL/dC:
+/* Gradients of L = f(C), C = A*B, given dC = dL/dC (the chain rule for the
+ * product with the operands' patterns fixed; differentiation is not among
+ * the paper's operations):
  * dA = (dC * B^T) on A's pattern, dB = (A^T * dC) on B's pattern. */
 int orc_backward(const orc_mat *A, const orc_mat *B, const orc_mat *dC,
                  orc_mat **dA, orc_mat **dB);
 
-/* One leaf of C = A*B straight from the definition
+/* One leaf of C = A*B straight from the definition of the block product,
  * C(I,J) = sum_K A(I,K) B(K,J), K ascending.  out: b*b doubles.
  * *present (may be NULL) is 1 when at least one K contributes. */
 int orc_leaf_product(const orc_mat *A, const orc_mat *B, int64_t I, int64_t J,
