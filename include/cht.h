@@ -313,7 +313,9 @@ int cht_multiply_f64_noalloc(cht_plan_t plan, cht_mat_t A, cht_mat_t B,
                              cht_mat_t C, void *stream);
 
 /* ------------------------------------------------------------------------
- * Backward of C = A*B for a loss L(C), given dC = dL/dC:
+ * Backward of C = A*B for a loss L(C), given dC = dL/dC (differentiation
+ * is not among the paper's operations: this is the chain rule of the
+ * product with the operands' patterns held fixed):
  *   dA = (dC * B^T) restricted to A's pattern,
  *   dB = (A^T * dC) restricted to B's pattern
  * (sampled block products: only the stored leaves of A and B are outputs;
@@ -333,8 +335,11 @@ int cht_multiply_backward(cht_plan_t plan, cht_mat_t A, cht_mat_t B,
                           cht_mat_t *dA, cht_mat_t *dB);
 
 /* ------------------------------------------------------------------------
- * Batched products: `count` independent products C_i = A_i * B_i, each with
- * its own plan (own n and leaf size), computed by ONE persistent kernel
+ * Batched products (not an operation of the paper, whose task templates
+ * leave the scheduling of independent tasks to the runtime, Section 2.1;
+ * here many products share one launch): `count` independent products
+ * C_i = A_i * B_i, each with its own plan (own n and leaf size), computed
+ * by ONE persistent kernel
  * launch whose work list concatenates all products' C leaves in
  * longest-first order.  cht_batch_create allocates every output and all
  * launch tables (and may synchronise); cht_batch_run only launches (no
