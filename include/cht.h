@@ -262,6 +262,13 @@ int cht_plan_free(cht_plan_t P);
  * reproducible; scratch of one leaf per piece).  The bound returned is
  * relative to 2^(e_r + f_c), the powers of two just above the largest |A|
  * in row r and |B| in column c.
+ * Operand check: A and B must store the leaves of the plan's operands, since
+ * the plan's pair lists index their leaves.  The matrices the plan was made
+ * from pass at once; other matrices (e.g. rebuilt from the same blocks) are
+ * compared leaf key by leaf key on the device, which synchronises `stream`
+ * once.  Operands with another pattern -- even one with the same leaf count,
+ * such as plan(A, B) given (B, A) -- are refused with CHT_ERR_SHAPE before
+ * any work is queued.
  * ---------------------------------------------------------------------- */
 int cht_multiply(cht_plan_t plan, cht_mat_t A, cht_mat_t B, int mode,
                  int32_t nslices, void *stream, cht_mat_t *C,
@@ -279,7 +286,8 @@ int cht_multiply(cht_plan_t plan, cht_mat_t A, cht_mat_t B, int mode,
  * those of cht_multiply(..., CHT_FP64, ...) bit for bit.  Returns after
  * enqueuing; `stream` is ordered after the last copy (synchronise it before
  * reading h_C).  Device scratch: C itself, freed in stream order.
- * CHT_ERR_INVALID for a NULL h_C or nchunks < 1.
+ * CHT_ERR_INVALID for a NULL h_C or nchunks < 1; operands checked against
+ * the plan as in cht_multiply (CHT_ERR_SHAPE).
  * ---------------------------------------------------------------------- */
 int cht_multiply_to_host(cht_plan_t plan, cht_mat_t A, cht_mat_t B, void *stream,
                          double *h_C, int32_t nchunks);
@@ -299,7 +307,11 @@ int cht_multiply_to_host(cht_plan_t plan, cht_mat_t A, cht_mat_t B, void *stream
  * cht_mat_like of one).  Returns without waiting for the GPU.
  * Scratch: a file-scope device array of 256 bytes (held by every GPU that
  * loads the library until the process exits); this call uses its first
- * 8 bytes as the work counter and clears them at every call.  The array is
+ * 8 bytes as the work counter and clears them at every call, and the next
+ * 4 bytes as the flag of the operand check (cleared before each use).
+ * Operands are checked against the plan as in cht_multiply: when they are
+ * not the matrices the plan was made from, that check synchronises `stream`
+ * once and refuses another pattern with CHT_ERR_SHAPE.  The array is
  * shared by all calls on a device: calls whose kernels overlap on the GPU
  * (e.g. on two streams) race on it and give wrong results -- order them.
  * The first call on each device looks up the array's device address
@@ -349,6 +361,8 @@ int cht_multiply_backward(cht_plan_t plan, cht_mat_t A, cht_mat_t B,
  * pairs than one unit sums (1016 at b = 64, 4000 at b = 32) is cut into
  * pieces as in cht_multiply; cht_batch_create prepares them (scratch of one
  * leaf per piece) and cht_batch_run adds them after the launch.
+ * cht_batch_create checks every product's operands against its plan as
+ * cht_multiply does (CHT_ERR_SHAPE).
  * ---------------------------------------------------------------------- */
 int cht_batch_create(int32_t count, const cht_plan_t *plans,
                      const cht_mat_t *As, const cht_mat_t *Bs, int mode,
@@ -383,10 +397,21 @@ int64_t cht_launch_count(void);
 const char *cht_status_str(int status);
 const char *cht_last_error(void);
 
-/* Measure the FP64 arithmetic peak of this GPU: a register-resident kernel
- * of independent FP64 FMAs (engine 1) or mma.sync f64 (engine 0) on every
- * SM, timed with CUDA events.  *tflops gets useful TFLOP/s. Synchronises. */
+/* Measure the FP64 arithmetic peak of this GPU (the denominator of the FP64
+ * kernels' roofline; no passage of the paper): register-resident kernels on
+ * every SM, timed with CUDA events on `stream`, which is synchronised.
+ * engine 1: `chains` independent FP64 FMA chains per thread; engine 2: a
+ * 4 x 8 register tile of FMAs from 12 operand registers (the leaf GEMM's
+ * inner loop without its loads; `chains` ignored); engine 0: `chains`
+ * independent mma.sync m8n8k4 f64 chains per warp.  `threads` per CTA (a
+ * multiple of 32, at most 1024), `ctas_per_sm` CTAs on each SM (1..32);
+ * chains 4, 8, 16 or 32.  *tflops gets FLOP/s / 1e12 of one ~40 ms launch
+ * after a warm-up launch.  CHT_ERR_INVALID for other arguments.
+ * cht_measure_fp64_peak returns the best of chains {8, 16, 32} x
+ * {1, 2, 4} CTAs of 256 threads per SM for the engine. */
 int cht_measure_fp64_peak(int engine, void *stream, double *tflops);
+int cht_measure_fp64_peak_cfg(int engine, int chains, int threads, int ctas_per_sm,
+                              void *stream, double *tflops);
 
 #ifdef __cplusplus
 }

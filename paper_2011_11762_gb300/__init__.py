@@ -390,6 +390,15 @@ def measure_fp64_peak(engine: int = 0, stream=None) -> float:
     return t.value
 
 
+def measure_fp64_peak_cfg(engine: int, chains: int, threads: int, ctas_per_sm: int,
+                          stream=None) -> float:
+    t = ctypes.c_double()
+    _check(_lib.load().cht_measure_fp64_peak_cfg(engine, chains, threads, ctas_per_sm,
+                                                 _stream(stream), ctypes.byref(t)),
+           "cht_measure_fp64_peak_cfg")
+    return t.value
+
+
 def library_path() -> str:
     return _lib.lib_path()
 

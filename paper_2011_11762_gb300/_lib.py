@@ -54,6 +54,8 @@ SIGNATURES = {
     "cht_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "cht_last_error": (ctypes.c_char_p, []),
     "cht_measure_fp64_peak": (ctypes.c_int, [ctypes.c_int, _VP, _PD]),
+    "cht_measure_fp64_peak_cfg": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, _VP, _PD]),
 }
 
 _lib = None

@@ -144,6 +144,44 @@ int num_sms(int *sms) {
   return CHT_OK;
 }
 
+int check_plan_operands(const cht_plan *plan, const cht_mat *A, const cht_mat *B, int *d_flag,
+                        cudaStream_t s) {
+  if (!plan || !A || !B) {
+    set_error("null plan or matrix handle");
+    return CHT_ERR_INVALID;
+  }
+  if (A->pat->n != plan->n || B->pat->n != plan->n || A->pat->b != plan->b ||
+      B->pat->b != plan->b || A->pat->nnz != plan->nA || B->pat->nnz != plan->nB) {
+    set_error("matrices do not match the plan's operands (n, b or leaf count)");
+    return CHT_ERR_SHAPE;
+  }
+  const bool fastA = A->pat->id == plan->patA, fastB = B->pat->id == plan->patB;
+  if (fastA && fastB) return CHT_OK;
+  DevArray<int> flag;
+  if (!d_flag) {
+    CHT_TRY(flag.alloc(1, s));
+    d_flag = flag.p;
+  }
+  bool same = true;
+  if (!fastA) {
+    if (!plan->opA) same = false;
+    else CHT_TRY(same_leaves(*A->pat, *plan->opA, d_flag, s, &same));
+    if (!same) {
+      set_error("A does not store the leaves of the plan's left operand");
+      return CHT_ERR_SHAPE;
+    }
+  }
+  if (!fastB) {
+    if (!plan->opB) same = false;
+    else CHT_TRY(same_leaves(*B->pat, *plan->opB, d_flag, s, &same));
+    if (!same) {
+      set_error("B does not store the leaves of the plan's right operand");
+      return CHT_ERR_SHAPE;
+    }
+  }
+  return CHT_OK;
+}
+
 }  // namespace cht
 
 using namespace cht;
@@ -162,6 +200,17 @@ int check_pair(cht_mat *A, cht_mat *B) {
               (long long)B->pat->n, A->pat->b, B->pat->b);
     return CHT_ERR_SHAPE;
   }
+  return CHT_OK;
+}
+
+// Records the operand patterns in a new plan (see check_plan_operands).
+int finish_plan(cht_plan *p, cht_mat *A, cht_mat *B, int64_t *nnzb_C, int64_t *npairs,
+                cht_plan_t *out) {
+  p->opA = A->pat;
+  p->opB = B->pat;
+  if (nnzb_C) *nnzb_C = p->C->nnz;
+  if (npairs) *npairs = p->npairs;
+  *out = p;
   return CHT_OK;
 }
 
@@ -294,10 +343,7 @@ int cht_symbolic_multiply(cht_mat_t A, cht_mat_t B, void *stream, cht_plan_t *ou
   CHT_TRY(check_pair(A, B));
   cht_plan *p = nullptr;
   CHT_TRY(symbolic(*A->pat, *B->pat, as_stream(stream), &p));
-  if (nnzb_C) *nnzb_C = p->C->nnz;
-  if (npairs) *npairs = p->npairs;
-  *out = p;
-  return CHT_OK;
+  return finish_plan(p, A, B, nnzb_C, npairs, out);
 }
 
 int cht_symbolic_multiply_spamm(cht_mat_t A, cht_mat_t B, double tau, void *stream,
@@ -315,10 +361,7 @@ int cht_symbolic_multiply_spamm(cht_mat_t A, cht_mat_t B, double tau, void *stre
   CHT_TRY(leaf_norms(B->values(), B->pat->nnz, B->pat->b, nb.p, s));
   cht_plan *p = nullptr;
   CHT_TRY(symbolic(*A->pat, *B->pat, s, &p, na.p, nb.p, tau));
-  if (nnzb_C) *nnzb_C = p->C->nnz;
-  if (npairs) *npairs = p->npairs;
-  *out = p;
-  return CHT_OK;
+  return finish_plan(p, A, B, nnzb_C, npairs, out);
 }
 
 int cht_symbolic_multiply_symsquare(cht_mat_t A, void *stream, cht_plan_t *out,
@@ -329,10 +372,7 @@ int cht_symbolic_multiply_symsquare(cht_mat_t A, void *stream, cht_plan_t *out,
   }
   cht_plan *p = nullptr;
   CHT_TRY(symbolic(*A->pat, *A->pat, as_stream(stream), &p, nullptr, nullptr, 0.0, true));
-  if (nnzb_C) *nnzb_C = p->C->nnz;
-  if (npairs) *npairs = p->npairs;
-  *out = p;
-  return CHT_OK;
+  return finish_plan(p, A, A, nnzb_C, npairs, out);
 }
 
 int cht_symbolic_multiply_upper(cht_mat_t A, cht_mat_t B, void *stream, cht_plan_t *out,
@@ -344,10 +384,7 @@ int cht_symbolic_multiply_upper(cht_mat_t A, cht_mat_t B, void *stream, cht_plan
   CHT_TRY(check_pair(A, B));
   cht_plan *p = nullptr;
   CHT_TRY(symbolic(*A->pat, *B->pat, as_stream(stream), &p, nullptr, nullptr, 0.0, true));
-  if (nnzb_C) *nnzb_C = p->C->nnz;
-  if (npairs) *npairs = p->npairs;
-  *out = p;
-  return CHT_OK;
+  return finish_plan(p, A, B, nnzb_C, npairs, out);
 }
 
 int cht_mat_mirror_upper(cht_mat_t U, void *stream, cht_mat_t *out) {
@@ -438,16 +475,12 @@ int cht_multiply(cht_plan_t plan, cht_mat_t A, cht_mat_t B, int mode, int32_t ns
     return CHT_ERR_INVALID;
   }
   CHT_TRY(check_pair(A, B));
-  if (plan->n != A->pat->n || plan->b != A->pat->b || plan->nA != A->pat->nnz ||
-      plan->nB != B->pat->nnz) {
-    set_error("matrices do not match the plan's operands");
-    return CHT_ERR_SHAPE;
-  }
   if (mode != CHT_FP64 && mode != CHT_SPLIT_BF16) {
     set_error("unknown mode %d", mode);
     return CHT_ERR_INVALID;
   }
   cudaStream_t s = as_stream(stream);
+  CHT_TRY(check_plan_operands(plan, A, B, nullptr, s));
   cht_mat *m = nullptr;
   bool created = false;
   CHT_TRY(out_matrix(C, plan->C, plan->id, s, &m, &created));
@@ -491,12 +524,8 @@ int cht_multiply_to_host(cht_plan_t plan, cht_mat_t A, cht_mat_t B, void *stream
     return CHT_ERR_INVALID;
   }
   CHT_TRY(check_pair(A, B));
-  if (plan->n != A->pat->n || plan->b != A->pat->b || plan->nA != A->pat->nnz ||
-      plan->nB != B->pat->nnz) {
-    set_error("matrices do not match the plan's operands");
-    return CHT_ERR_SHAPE;
-  }
   cudaStream_t s = as_stream(stream);
+  CHT_TRY(check_plan_operands(plan, A, B, nullptr, s));
   const int64_t nC = plan->C->nnz;
   DevArray<double> cv;
   CHT_TRY(cv.alloc(static_cast<size_t>(nC) * plan->b * plan->b, s));
@@ -693,11 +722,20 @@ const char *cht_status_str(int status) {
 const char *cht_last_error(void) { return g_last_error; }
 
 int cht_measure_fp64_peak(int engine, void *stream, double *tflops) {
-  if (!tflops || (engine != 0 && engine != 1)) {
+  if (!tflops || engine < 0 || engine > 2) {
     set_error("invalid engine or null output");
     return CHT_ERR_INVALID;
   }
   return launch_fp64_peak(engine, as_stream(stream), tflops);
+}
+
+int cht_measure_fp64_peak_cfg(int engine, int chains, int threads, int ctas_per_sm,
+                              void *stream, double *tflops) {
+  if (!tflops) {
+    set_error("null output");
+    return CHT_ERR_INVALID;
+  }
+  return launch_fp64_peak_cfg(engine, chains, threads, ctas_per_sm, as_stream(stream), tflops);
 }
 
 }  // extern "C"

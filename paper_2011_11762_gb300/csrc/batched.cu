@@ -52,6 +52,8 @@ int batch_create(int32_t count, const cht_plan_t *plans, const cht_mat_t *As, co
   bt->mode = mode;
   bt->nslices = nslices;
   int64_t total_vals = 0, total_units = 0;
+  DevArray<int> flag;
+  CHT_TRY(flag.alloc(1, s));
   for (int32_t i = 0; i < count; ++i) {
     cht_plan *p = plans[i];
     cht_mat *A = As[i], *B = Bs[i];
@@ -59,8 +61,7 @@ int batch_create(int32_t count, const cht_plan_t *plans, const cht_mat_t *As, co
       set_error("product %d: null plan or matrix", i);
       return CHT_ERR_INVALID;
     }
-    if (p->n != A->pat->n || p->b != A->pat->b || p->nA != A->pat->nnz ||
-        p->nB != B->pat->nnz || B->pat->n != p->n || B->pat->b != p->b) {
+    if (check_plan_operands(p, A, B, flag.p, s) != CHT_OK) {
       set_error("product %d: matrices do not match the plan's operands", i);
       return CHT_ERR_SHAPE;
     }

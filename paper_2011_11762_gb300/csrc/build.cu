@@ -87,6 +87,14 @@ __global__ void k_split_key(const uint64_t *__restrict__ k, int64_t n, int L,
     low[i] = static_cast<int32_t>(k[i] & mask);
 }
 
+// flag = 1 if any key differs (several threads may store the same 1).
+__global__ void k_keys_differ(const uint64_t *__restrict__ x, const uint64_t *__restrict__ y,
+                              int64_t n, int *__restrict__ flag) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    if (x[i] != y[i]) *flag = 1;
+}
+
 __global__ void k_densify(const double *__restrict__ vals, const int32_t *__restrict__ brow,
                           const int32_t *__restrict__ bcol, int64_t nnz, int b,
                           double *__restrict__ out, int64_t ld) {
@@ -298,6 +306,27 @@ int build_matrix(int64_t n, int32_t b, int64_t nblocks, const int32_t *d_brow,
   CHT_TRY(build_pattern_index(*pat, s));
   m->pat = std::move(pat);
   *out = m.release();
+  return CHT_OK;
+}
+
+int same_leaves(const Pattern &x, const Pattern &y, int *d_flag, cudaStream_t s, bool *same) {
+  if (&x == &y || x.id == y.id) {
+    *same = true;
+    return CHT_OK;
+  }
+  if (x.n != y.n || x.b != y.b || x.nnz != y.nnz) {
+    *same = false;
+    return CHT_OK;
+  }
+  int h = 0;
+  if (x.nnz > 0) {
+    CHT_CUDA_TRY(cudaMemsetAsync(d_flag, 0, sizeof(int), s));
+    k_keys_differ<<<grid_for(x.nnz, 256), 256, 0, s>>>(x.mkey.p, y.mkey.p, x.nnz, d_flag);
+    CHT_TRY(launched("keys_differ"));
+    CHT_CUDA_TRY(cudaMemcpyAsync(&h, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CHT_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  *same = h == 0;
   return CHT_OK;
 }
 

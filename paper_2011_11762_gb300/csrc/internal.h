@@ -111,6 +111,10 @@ uint64_t next_id();
 int bits_for(int64_t G);
 // Fills brow/bcol and the row and column indexes from the sorted mkey.
 int build_pattern_index(Pattern &p, cudaStream_t s);
+// *same = true when x and y store the same leaves (equal n, b and Morton
+// keys).  Different pattern objects are compared on the device: d_flag is 4
+// bytes of device scratch, and the call synchronises s to read it.
+int same_leaves(const Pattern &x, const Pattern &y, int *d_flag, cudaStream_t s, bool *same);
 
 // Blocks for a grid-stride loop over n items: ceil(n / threads), at least 1
 // and at most 8 * 65535 (the loops stride by the grid).
@@ -168,6 +172,8 @@ int launch_leafgemm_f64_batch(const ProdDesc *d_prods, const int64_t *d_units, i
                               unsigned long long *d_counter, cudaStream_t s);
 
 int launch_fp64_peak(int engine, cudaStream_t s, double *tflops);
+int launch_fp64_peak_cfg(int engine, int chains, int threads, int per_sm, cudaStream_t s,
+                         double *tflops);
 
 }  // namespace cht
 
@@ -187,6 +193,9 @@ struct cht_plan {
   int32_t b = 0;
   int64_t nA = 0, nB = 0;
   uint64_t patA = 0, patB = 0;       // pattern ids of A and B
+  // the operand patterns themselves, kept so that a multiply can check that
+  // its operands store the leaves the pair lists index
+  std::shared_ptr<cht::Pattern> opA, opB;
   std::shared_ptr<cht::Pattern> C;   // product pattern
   int64_t npairs = 0;
   int64_t max_seg = 0;               // most pairs of any C leaf
@@ -200,6 +209,14 @@ struct cht_plan {
   cht::DevArray<int32_t> dB_a, dB_c;      // pairs grouped by B leaf
   cht::DevArray<int32_t> idA, idB;        // identity schedules
 };
+
+namespace cht {
+// CHT_OK when A and B store the leaves of the plan's operands (the same
+// pattern objects, or equal patterns compared with same_leaves); otherwise
+// CHT_ERR_SHAPE.  d_flag: 4 bytes of device scratch, or null to allocate.
+int check_plan_operands(const cht_plan *plan, const cht_mat *A, const cht_mat *B, int *d_flag,
+                        cudaStream_t s);
+}  // namespace cht
 
 // A batch of independent products run by one persistent launch.
 struct cht_batch {

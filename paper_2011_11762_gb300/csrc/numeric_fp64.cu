@@ -282,30 +282,63 @@ int launch_b(const GemmWork &w, cudaStream_t s, int *status, unsigned long long 
 }
 
 // ----------------------------------------------------------- FP64 peak --
-__global__ void k_peak_dfma(double *out, int iters) {
-  double a[8], x = 1.0 + 1e-9 * threadIdx.x, y = 0.999999999;
+// Register-resident FP64 throughput kernels for the roofline denominator.
+// DFMA: every thread runs CH independent FMA chains a_i <- a_i * y + x (y and
+// x kernel arguments, so nothing folds); TILE: a 4 x 8 register tile of
+// accumulators updated from 4 + 8 operand registers, the shape of the leaf
+// GEMM's inner loop without its shared-memory loads.  DMMA: every warp runs
+// CH independent mma.sync m8n8k4 f64 chains.  The results feed a store that
+// never happens, so the work cannot be removed.
+template <int CH>
+__global__ void k_peak_dfma(double *out, int iters, double y, double x0) {
+  double a[CH];
+  const double x = x0 + 1e-9 * threadIdx.x;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) a[i] = i;
+  for (int i = 0; i < CH; ++i) a[i] = 1e-3 * i;
   for (int n = 0; n < iters; ++n)
 #pragma unroll
-    for (int i = 0; i < 8; ++i) a[i] = fma(a[i], y, x);
+    for (int i = 0; i < CH; ++i) a[i] = fma(a[i], y, x);
   double s = 0;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) s += a[i];
+  for (int i = 0; i < CH; ++i) s += a[i];
   if (s == 12345.0) out[0] = s;
 }
 
-__global__ void k_peak_dmma(double *out, int iters) {
-  double d[8][2];
-  const double a = 1.0 + 1e-9 * threadIdx.x, b = 0.999999999;
+__global__ void k_peak_tile(double *out, int iters, double y, double x0) {
+  double a[4], b[8], acc[4][8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) d[i][0] = d[i][1] = i;
+  for (int i = 0; i < 4; ++i) a[i] = y * (1.0 + 1e-3 * (i + threadIdx.x));
+#pragma unroll
+  for (int j = 0; j < 8; ++j) b[j] = x0 * (1.0 - 1e-3 * j);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
   for (int n = 0; n < iters; ++n)
 #pragma unroll
-    for (int i = 0; i < 8; ++i) dmma_8x8x4(d[i][0], d[i][1], a, b);
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
   double s = 0;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) s += d[i][0] + d[i][1];
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += acc[i][j];
+  if (s == 12345.0) out[0] = s;
+}
+
+template <int CH>
+__global__ void k_peak_dmma(double *out, int iters, double y, double x0) {
+  double d[CH][2];
+  const double a = x0 + 1e-9 * threadIdx.x, b = y;
+#pragma unroll
+  for (int i = 0; i < CH; ++i) d[i][0] = d[i][1] = i;
+  for (int n = 0; n < iters; ++n)
+#pragma unroll
+    for (int i = 0; i < CH; ++i) dmma_8x8x4(d[i][0], d[i][1], a, b);
+  double s = 0;
+#pragma unroll
+  for (int i = 0; i < CH; ++i) s += d[i][0] + d[i][1];
   if (s == 12345.0) out[0] = s;
 }
 
@@ -422,37 +455,86 @@ int launch_leafgemm_f64_batch(const ProdDesc *d_prods, const int64_t *d_units, i
   return launched("leafgemm_f64_batch");
 }
 
-int launch_fp64_peak(int engine, cudaStream_t s, double *tflops) {
+// One configuration of the FP64 peak kernels: engine 1 = DFMA chains, 2 =
+// the DFMA register tile (chains ignored: 32 accumulators), 0 = DMMA chains;
+// `threads` per CTA, `per_sm` CTAs per SM on every SM.  The iteration count
+// is sized for about 40 ms per launch at 1.2 TFLOP/s; one warm-up launch,
+// then one timed launch (CUDA events on s).
+int launch_fp64_peak_cfg(int engine, int chains, int threads, int per_sm, cudaStream_t s,
+                         double *tflops) {
+  if (engine < 0 || engine > 2 || threads < 32 || threads > 1024 || threads % 32 != 0 ||
+      per_sm < 1 || per_sm > 32 ||
+      (engine != 2 && chains != 4 && chains != 8 && chains != 16 && chains != 32)) {
+    set_error("FP64 peak: engine 0..2, chains 4/8/16/32, threads a multiple of 32 in "
+              "[32, 1024], 1..32 CTAs per SM");
+    return CHT_ERR_INVALID;
+  }
   int sms = 0;
   CHT_TRY(num_sms(&sms));
+  const int grid = sms * per_sm;
+  const int ch = engine == 2 ? 32 : chains;
+  // FLOPs per iteration per thread (a DMMA's 2 * 8 * 8 * 4 shared by 32 lanes)
+  const double per_iter = engine == 0 ? ch * 2.0 * 8 * 8 * 4 / 32.0 : ch * 2.0;
+  const double target = 4.8e10;  // ~40 ms at 1.2 TFLOP/s
+  int64_t iters = static_cast<int64_t>(target / (static_cast<double>(grid) * threads * per_iter));
+  iters = std::max<int64_t>(64, std::min<int64_t>(iters, 1 << 24));
   DevArray<double> out;
   CHT_TRY(out.alloc(1, s));
-  const int threads = 256, per_sm = 4, iters = 1 << 15;
-  const int grid = sms * per_sm;
   cudaEvent_t e0, e1;
   CHT_CUDA_TRY(cudaEventCreate(&e0));
   CHT_CUDA_TRY(cudaEventCreate(&e1));
-  // warm up, then time
-  for (int rep = 0; rep < 2; ++rep) {
-    if (rep == 1) CHT_CUDA_TRY(cudaEventRecord(e0, s));
-    if (engine == 0)
-      k_peak_dmma<<<grid, threads, 0, s>>>(out.p, iters);
-    else
-      k_peak_dfma<<<grid, threads, 0, s>>>(out.p, iters);
-    CHT_TRY(launched("fp64_peak"));
+  const double y = 0.999999999, x0 = 1.0;
+  const int it = static_cast<int>(iters);
+  int rc = CHT_OK;
+  for (int rep = 0; rep < 2 && rc == CHT_OK; ++rep) {
+    if (rep == 1) cudaEventRecord(e0, s);
+    if (engine == 2) {
+      k_peak_tile<<<grid, threads, 0, s>>>(out.p, it, y, x0);
+    } else if (engine == 1) {
+      switch (ch) {
+        case 4: k_peak_dfma<4><<<grid, threads, 0, s>>>(out.p, it, y, x0); break;
+        case 8: k_peak_dfma<8><<<grid, threads, 0, s>>>(out.p, it, y, x0); break;
+        case 16: k_peak_dfma<16><<<grid, threads, 0, s>>>(out.p, it, y, x0); break;
+        default: k_peak_dfma<32><<<grid, threads, 0, s>>>(out.p, it, y, x0); break;
+      }
+    } else {
+      switch (ch) {
+        case 4: k_peak_dmma<4><<<grid, threads, 0, s>>>(out.p, it, y, x0); break;
+        case 8: k_peak_dmma<8><<<grid, threads, 0, s>>>(out.p, it, y, x0); break;
+        case 16: k_peak_dmma<16><<<grid, threads, 0, s>>>(out.p, it, y, x0); break;
+        default: k_peak_dmma<32><<<grid, threads, 0, s>>>(out.p, it, y, x0); break;
+      }
+    }
+    rc = launched("fp64_peak");
   }
-  CHT_CUDA_TRY(cudaEventRecord(e1, s));
-  CHT_CUDA_TRY(cudaEventSynchronize(e1));
   float ms = 0.f;
-  CHT_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+  if (rc == CHT_OK) {
+    cudaError_t e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) rc = cuda_fail(e, "fp64 peak timing");
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  // per thread per iteration: 8 FMAs (DFMA); per warp per iteration:
-  // 8 MMAs of 8x8x4 (DMMA)
-  const double warps = static_cast<double>(grid) * threads / 32.0;
-  const double flops = engine == 0 ? warps * iters * 8.0 * 2.0 * 8 * 8 * 4
-                                   : static_cast<double>(grid) * threads * iters * 8.0 * 2.0;
-  *tflops = flops / (ms * 1e-3) / 1e12;
+  if (rc != CHT_OK) return rc;
+  *tflops = static_cast<double>(grid) * threads * static_cast<double>(iters) * per_iter /
+            (ms * 1e-3) / 1e12;
+  return CHT_OK;
+}
+
+// The best of a small sweep (chains x CTAs per SM, 256 threads).
+int launch_fp64_peak(int engine, cudaStream_t s, double *tflops) {
+  double best = 0.0;
+  const int chain_set[] = {8, 16, 32};
+  const int occ_set[] = {1, 2, 4};
+  for (int ch : chain_set)
+    for (int occ : occ_set) {
+      double t = 0.0;
+      CHT_TRY(launch_fp64_peak_cfg(engine, ch, 256, occ, s, &t));
+      best = std::max(best, t);
+      if (engine == 2) break;
+    }
+  *tflops = best;
   return CHT_OK;
 }
 
@@ -469,7 +551,9 @@ int launch_fp64_peak(int engine, cudaStream_t s, double *tflops) {
 // with cudaGetSymbolAddress and passed to the kernel.
 namespace cht {
 namespace {
-constexpr int kNoAllocScratchBytes = 256;  // stated maximum; this call uses 8
+// stated maximum; this call uses 12 bytes: the 8-byte work counter and a
+// 4-byte flag for the operand-pattern comparison
+constexpr int kNoAllocScratchBytes = 256;
 constexpr int kNoAllocMaxDevices = 64;
 __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocScratchBytes / 8];
 std::mutex g_noalloc_mutex;
@@ -503,11 +587,12 @@ extern "C" int cht_multiply_f64_noalloc(cht_plan_t plan, cht_mat_t A, cht_mat_t 
     set_error("null plan or matrix handle");
     return CHT_ERR_INVALID;
   }
-  if (A->pat->n != plan->n || B->pat->n != plan->n || A->pat->b != plan->b ||
-      B->pat->b != plan->b || A->pat->nnz != plan->nA || B->pat->nnz != plan->nB) {
-    set_error("matrices do not match the plan's operands");
-    return CHT_ERR_SHAPE;
-  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long *counter = nullptr;
+  CHT_TRY(noalloc_scratch(&counter));
+  // operands on other pattern objects are compared with the plan's on the
+  // device, the flag in the static array's second word (no allocation)
+  CHT_TRY(check_plan_operands(plan, A, B, reinterpret_cast<int *>(counter + 1), s));
   if (C->pat->id != plan->C->id) {
     set_error("C must be a matrix on the plan's product pattern (from cht_multiply or "
               "cht_mat_like of one)");
@@ -523,9 +608,6 @@ extern "C" int cht_multiply_f64_noalloc(cht_plan_t plan, cht_mat_t A, cht_mat_t 
     return CHT_ERR_UNSUPPORTED;
   }
   if (plan->C->nnz == 0) return CHT_OK;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  unsigned long long *counter = nullptr;
-  CHT_TRY(noalloc_scratch(&counter));
   int *status = nullptr;
   CHT_TRY(device_status_ptr(&status));
   // the work counter must start at zero; the array keeps the last call's value

@@ -41,13 +41,44 @@ def assert_same_pattern(M, omat):
     assert np.array_equal(gr, orow) and np.array_equal(gc, ocol)
 
 
-def assert_values_close(M, omat, tol=1e-13):
+_SAME = object()
+
+
+def assert_values_close(M, omat, tol=1e-13, leaf_tol=_SAME):
+    """Whole-matrix relative Frobenius error <= tol and, unless leaf_tol is
+    None, the largest per-leaf relative Frobenius error <= leaf_tol (default:
+    tol).  A leaf whose reference is exactly zero is measured against the
+    root-mean-square leaf norm instead, so that a small wrong leaf cannot hide
+    under the norm of the whole matrix.
+
+    Callers pass leaf_tol=None for the split form, whose error is relative to
+    the row and column maxima of the operands (the splitting scales whole
+    lines), not to each leaf, and for truncated purification iterates, whose
+    smallest kept leaves carry the cancellation of 3X^2 - 2X^3."""
     _, _, gv = host_leaves(M)
     _, _, ov = omat.leaves()
     assert gv.shape == ov.shape
     err = setref.rel_fro(gv, ov)
     assert err <= tol, f"relative Frobenius error {err:.3e} > {tol:.1e}"
+    if leaf_tol is _SAME:
+        leaf_tol = tol
+    if leaf_tol is not None and ov.shape[0] > 0:
+        worst, leaf = max_leaf_rel_err(gv, ov)
+        assert worst <= leaf_tol, (f"leaf {leaf}: relative Frobenius error {worst:.3e} > "
+                                   f"{leaf_tol:.1e}")
     return err
+
+
+def max_leaf_rel_err(gv, ov):
+    """(largest per-leaf relative Frobenius error, its leaf index)."""
+    n = ov.shape[0]
+    num = np.linalg.norm((gv - ov).reshape(n, -1), axis=1)
+    den = np.linalg.norm(ov.reshape(n, -1), axis=1)
+    rms = float(np.sqrt(np.mean(den * den)))
+    den = np.where(den > 0, den, rms if rms > 0 else 1.0)
+    rel = num / den
+    i = int(np.argmax(rel))
+    return float(rel[i]), i
 
 
 def check_plan_pairs(plan, a, b):

@@ -63,6 +63,22 @@ def pairs_per_c_leaf(pa: set, pb: set) -> dict:
     return {c: sorted(ks) for c, ks in out.items()}
 
 
+def product_pattern_counts(a_row, a_col, b_row, b_col, grid: int):
+    """The boolean block product with multiplicities, as a sparse matrix
+    product of the 0/1 leaf patterns (scipy CSR x CSR): arrays (I, J, count)
+    of every C leaf, count = the number of K with A(I, K) and B(K, J)
+    stored, in row-major (I, J) order.  For patterns too large for the set
+    versions above."""
+    from scipy import sparse
+    ones = lambda r, c: sparse.csr_matrix(
+        (np.ones(len(r), dtype=np.int64), (np.asarray(r, np.int64), np.asarray(c, np.int64))),
+        shape=(grid, grid))
+    p = (ones(a_row, a_col) @ ones(b_row, b_col)).tocoo()
+    order = np.lexsort((p.col, p.row))
+    return (p.row[order].astype(np.int64), p.col[order].astype(np.int64),
+            p.data[order].astype(np.int64))
+
+
 def banded_column_counts(n: int, half_width: int) -> np.ndarray:
     """Nonzeros of each column of an n x n banded matrix, |i - j| <= w."""
     k = np.arange(n, dtype=np.int64)

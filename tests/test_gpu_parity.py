@@ -223,12 +223,82 @@ def test_bounded_wait_reports_timeout(lib):
     gu.assert_values_close(C, Co, FP64_TOL)
 
 
-def test_full_size_3d_locality_sampled(lib):
-    # N = 65536, 64x64 leaves (the benchmark workload): pattern counts exact,
-    # sampled C leaves against the oracle's single-leaf product.
+@pytest.fixture(scope="module")
+def full3d(lib):
+    """The benchmark workload: 3D locality, N = 65536, 64x64 leaves."""
     a, b = w.config2(65536)
     A, B = gu.upload(lib, a), gu.upload(lib, b)
+    return a, b, A, B, lib.cht_symbolic_multiply(A, B)
+
+
+def _shift_rows(m):
+    """The same leaves with their leaf rows moved down by one (cyclically):
+    as many leaves as m, on another pattern."""
+    return w.BlockMatrix(m.n, m.b, ((m.brow + 1) % m.grid).astype(np.int32), m.bcol.copy(),
+                         m.vals.copy())
+
+
+def test_operands_checked_against_plan(lib):
+    # The plan's pair lists index the leaves of its operands, so operands on
+    # another pattern with the same leaf count are refused before any work;
+    # a matrix rebuilt from the same blocks (another pattern object, the same
+    # leaves) is accepted and gives the same product bit for bit.
+    torch = pytest.importorskip("torch")
+    a, b = w.config1(2048, 32, 4)
+    A, B = gu.upload(lib, a), gu.upload(lib, b)
     plan = lib.cht_symbolic_multiply(A, B)
+    C, _ = lib.cht_multiply(plan, A, B, sync=True)
+    As = gu.upload(lib, _shift_rows(a))
+    Bs = gu.upload(lib, _shift_rows(b))
+    assert As.nblocks == A.nblocks and Bs.nblocks == B.nblocks
+    for x, y in ((As, B), (A, Bs), (As, Bs)):
+        for mode in (lib.CHT_FP64, lib.CHT_SPLIT_BF16):
+            with pytest.raises(lib.ChtError) as e:
+                lib.cht_multiply(plan, x, y, mode=mode)
+            assert e.value.code == lib.CHT_ERR_SHAPE
+        with pytest.raises(lib.ChtError) as e:
+            lib.cht_multiply(plan, x, y, out=C)  # an existing output is not touched either
+        assert e.value.code == lib.CHT_ERR_SHAPE
+        out = torch.empty((plan.nnzb_C, a.b, a.b), dtype=torch.float64, pin_memory=True)
+        with pytest.raises(lib.ChtError) as e:
+            lib.cht_multiply_to_host(plan, x, y, out)
+        assert e.value.code == lib.CHT_ERR_SHAPE
+        with pytest.raises(lib.ChtError) as e:
+            lib.Batch([plan], [x], [y])
+        assert e.value.code == lib.CHT_ERR_SHAPE
+    ref = C.values().clone()
+    A2, B2 = gu.upload(lib, a), gu.upload(lib, b)  # rebuilt: equal patterns
+    for x, y in ((A2, B), (A, B2), (A2, B2)):
+        C2, _ = lib.cht_multiply(plan, x, y, sync=True)
+        assert torch.equal(C2.values(), ref)
+    lib.sync_status()
+
+
+def test_full_size_operands_checked_against_plan(lib, full3d):
+    # On the benchmark workload A and B share one pattern (same lattice and
+    # cutoff; only their values differ), so plan(A, B) applied to (B, A)
+    # indexes stored leaves and is the product B*A: accepted, and equal bit
+    # for bit to the product on plan(B, A).  A with its leaf rows shifted
+    # has as many leaves (60104) on another pattern: refused.
+    torch = pytest.importorskip("torch")
+    a, b, A, B, plan = full3d
+    assert A.nblocks == B.nblocks
+    BA, _ = lib.cht_multiply(plan, B, A, sync=True)
+    ref, _ = lib.cht_multiply(lib.cht_symbolic_multiply(B, A), B, A, sync=True)
+    assert torch.equal(BA.values(), ref.values())
+    del BA, ref
+    As = gu.upload(lib, _shift_rows(a))
+    assert As.nblocks == A.nblocks
+    for x, y in ((As, B), (B, As)):
+        with pytest.raises(lib.ChtError) as e:
+            lib.cht_multiply(plan, x, y)
+        assert e.value.code == lib.CHT_ERR_SHAPE
+
+
+def test_full_size_3d_locality_sampled(lib, full3d):
+    # N = 65536, 64x64 leaves (the benchmark workload): pattern counts exact,
+    # sampled C leaves against the oracle's single-leaf product.
+    a, b, A, B, plan = full3d
     pa = setref.pattern_set(a.brow, a.bcol)
     pb = setref.pattern_set(b.brow, b.bcol)
     assert plan.npairs == setref.pair_count(pa, pb)

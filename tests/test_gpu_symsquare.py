@@ -46,7 +46,7 @@ def test_symsquare_matches_oracle(lib, name):
     gu.assert_same_pattern(U, OU)
     gu.assert_values_close(U, OU, FP64_TOL)
     Us, _ = lib.cht_multiply(plan, A, A, mode=lib.CHT_SPLIT_BF16, sync=True)
-    gu.assert_values_close(Us, OU, SPLIT_TOL)
+    gu.assert_values_close(Us, OU, SPLIT_TOL, leaf_tol=None)
     # the mirrored upper triangle is the full product
     full = lib.cht_mat_mirror_upper(U)
     OC, _ = OA.multiply(OA)

@@ -87,3 +87,51 @@ def test_noalloc_rejects_foreign_output():
     plan = cht.cht_symbolic_multiply(A, B)
     rc = lib.cht_multiply_f64_noalloc(plan.handle, A.handle, B.handle, A.handle, None)
     assert rc == cht.CHT_ERR_INVALID
+
+
+def test_noalloc_checks_operands_without_allocating():
+    # The operand check compares patterns on the device with its flag in the
+    # static array: a rebuilt operand (same leaves, another pattern object)
+    # is accepted and gives cht_multiply's result, an operand with as many
+    # leaves on another pattern is refused -- with the allocator refusing.
+    import torch
+    cht = gu.cht()
+    lib = cht.load()
+    a, b = w.config1(2048, 32, 4)
+    A, B = cht.from_block_matrix(a), cht.from_block_matrix(b)
+    plan = cht.cht_symbolic_multiply(A, B)
+    ref, _ = cht.cht_multiply(plan, A, B, sync=True)
+    ref_vals = ref.values().cpu().numpy()
+    out = ref.like()
+    A2 = cht.from_block_matrix(a)
+    shifted = w.BlockMatrix(a.n, a.b, ((a.brow + 1) % a.grid).astype(np.int32), a.bcol.copy(),
+                            a.vals.copy())
+    As = cht.from_block_matrix(shifted)
+    assert As.nblocks == A.nblocks
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    calls = {"alloc": 0, "free": 0}
+
+    def refuse(nbytes, s, ctx):
+        calls["alloc"] += 1
+        return None
+
+    def count_free(p, nbytes, s, ctx):
+        calls["free"] += 1
+
+    alloc_cb, free_cb = _ALLOC(refuse), _FREE(count_free)
+    torch.cuda.synchronize()
+    gc.disable()
+    assert lib.cht_set_allocator(alloc_cb, free_cb, None) == 0
+    try:
+        rc_same = lib.cht_multiply_f64_noalloc(plan.handle, A2.handle, B.handle, out.handle,
+                                               stream)
+        rc_other = lib.cht_multiply_f64_noalloc(plan.handle, As.handle, B.handle, out.handle,
+                                                stream)
+    finally:
+        assert lib.cht_set_allocator(None, None, None) == 0
+        gc.enable()
+    assert calls == {"alloc": 0, "free": 0}
+    assert rc_same == 0, lib.cht_last_error().decode()
+    assert rc_other == cht.CHT_ERR_SHAPE
+    cht.sync_status()
+    assert setref.rel_fro(out.values().cpu().numpy(), ref_vals) <= FP64_TOL
