@@ -45,6 +45,7 @@ METRIC = "block-sparse C=A·B useful TFLOP/s, FP64 vs split form at stated rel. 
 UNIT = "TFLOP/s"
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, profiling recipe's nominal figure
 L2_BYTES = 129e6
+MEASURED = {}  # peaks measured in this run (the FP64 sweep), for the sections
 
 
 def parse_args():
@@ -172,6 +173,32 @@ def unique_bytes(nA, nB, nC, b):
     return (nA + nB + nC) * b * b * 8
 
 
+def workload_config(n, b, npairs, nA, nB, nC, world):
+    """The `config` object of the JSON line (both arms print the same one)."""
+    inputs = (nA + nB) * b * b * 8
+    return {"workload": f"3d_locality_N{n}_b{b}_cutoff6", "n": n, "leaf": b, "pairs": npairs,
+            "nnzb_A": nA, "nnzb_B": nB, "nnzb_C": nC, "step": "symbolic + FP64 numeric",
+            "l2": f"inputs {inputs / 1e9:.1f} GB > L2 {L2_BYTES / 1e6:.0f} MB",
+            "parallelism": f"replicas x{world}"}
+
+
+def host_pattern_counts(a, b):
+    """(stored A leaves, stored B leaves, pairs, C leaves) of A*B on the host:
+    all-zero leaves dropped as the library drops them, then a sparse product
+    of the 0/1 leaf patterns (no values)."""
+    import numpy as np
+    from scipy import sparse
+    g = a.grid
+
+    def ones(m):
+        keep = np.any(m.vals.reshape(m.nblocks, -1) != 0, axis=1)
+        r, c = m.brow[keep].astype(np.int64), m.bcol[keep].astype(np.int64)
+        return sparse.csr_matrix((np.ones(r.size, dtype=np.int64), (r, c)), shape=(g, g))
+    pa, pb = ones(a), ones(b)
+    p = pa @ pb
+    return int(pa.nnz), int(pb.nnz), int(p.sum()), int(p.nnz)
+
+
 # -------------------------------------------------------------- GPU timing --
 
 class Timer:
@@ -256,53 +283,102 @@ def fp64_main(args, world, rank, cht, torch):
 
 
 def fp64_e2e(args, world, cht, torch, a, b):
-    """Same metric through the public API with host buffers: H2D of the
-    leaf lists from pinned memory, build, symbolic, and the multiply that
-    writes C to pinned host memory (its copies overlap its later chunks)."""
+    """Same metric through the public API with host buffers, run as a serving
+    loop runs it: every step copies its inputs (the leaf lists of A and B)
+    host -> device from pinned memory, builds A and B, runs the symbolic
+    phase and the multiply that writes C to pinned host memory (its copies
+    overlap its later chunks).  The next step's inputs are copied on a copy
+    stream into a second set of landing buffers while this step computes,
+    so every step's copies are inside the timed region but hidden behind the
+    previous step's arithmetic.  The copies are timed on the copy stream
+    (h2d_gbs); a few steps without the prefetch are timed as well."""
     import numpy as np
     pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
-    ha = [pin(a.brow), pin(a.bcol), pin(a.vals)]
-    hb = [pin(b.brow), pin(b.bcol), pin(b.vals)]
-    h2d = sum(t.numel() * t.element_size() for t in ha + hb)
+    hosts = [pin(a.brow), pin(a.bcol), pin(a.vals), pin(b.brow), pin(b.bcol), pin(b.vals)]
+    h2d = sum(t.numel() * t.element_size() for t in hosts)
     stream = torch.cuda.current_stream()
-    out_host = None
-    flops = None
+    cstream = torch.cuda.Stream()
+    land = [[torch.empty(t.shape, dtype=t.dtype, device="cuda") for t in hosts]
+            for _ in range(2)]
+    state = {"out": None, "flops": None, "d2h": 0}
+    copy_ms = []
 
-    # device landing buffers for the inputs, reused every step (as a serving
-    # loop would); every step still copies all input bytes host -> device
-    da = [torch.empty(t.shape, dtype=t.dtype, device="cuda") for t in ha]
-    db = [torch.empty(t.shape, dtype=t.dtype, device="cuda") for t in hb]
+    def prefetch(slot, built, copied):
+        # the slot's buffers are free once the build that read them is done
+        cstream.wait_event(built[slot])
+        t0 = torch.cuda.Event(enable_timing=True)
+        t0.record(cstream)
+        with torch.cuda.stream(cstream):
+            for d, h in zip(land[slot], hosts):
+                d.copy_(h, non_blocking=True)
+        copied[slot].record(cstream)
+        return t0
 
-    def step():
-        nonlocal out_host, flops
-        for d, h in zip(da + db, ha + hb):
-            d.copy_(h, non_blocking=True)
-        A = cht.cht_mat_from_blocks(a.n, a.b, *da)
-        B = cht.cht_mat_from_blocks(b.n, b.b, *db)
+    def one_step(slot, copied, built, next_fn):
+        stream.wait_event(copied[slot])
+        d = land[slot]
+        A = cht.cht_mat_from_blocks(a.n, a.b, d[0], d[1], d[2])
+        B = cht.cht_mat_from_blocks(b.n, b.b, d[3], d[4], d[5])
+        built[slot].record(stream)
+        pending = next_fn() if next_fn else None
         p = cht.cht_symbolic_multiply(A, B)
         shape = (p.nnzb_C, a.b, a.b)
-        if out_host is None or tuple(out_host.shape) != shape:
-            out_host = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+        if state["out"] is None or tuple(state["out"].shape) != shape:
+            state["out"] = torch.empty(shape, dtype=torch.float64, pin_memory=True)
         # C straight to pinned host memory, chunk by chunk while it computes
-        cht.cht_multiply_to_host(p, A, B, out_host, nchunks=8)
-        flops = p.useful_flops
-        stream.synchronize()
-        return out_host.numel() * 8
+        cht.cht_multiply_to_host(p, A, B, state["out"], nchunks=8)
+        state["flops"] = p.useful_flops
+        state["d2h"] = state["out"].numel() * 8
+        stream.synchronize()  # this step's C is in host memory
+        return pending
 
-    d2h = 0
-    for _ in range(max(1, args.warmup)):
-        d2h = step()
+    def run(k_steps, overlap):
+        copied = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        built = [torch.cuda.Event() for _ in range(2)]
+        starts = [None, None]
+        starts[0] = prefetch(0, built, copied)
+        for k in range(k_steps):
+            slot = k % 2
+            if overlap and k + 1 < k_steps:
+                nxt = lambda: prefetch(1 - slot, built, copied)
+            else:
+                nxt = None
+            if not overlap and k > 0:
+                starts[slot] = prefetch(slot, built, copied)
+            t_start = starts[slot]
+            started = one_step(slot, copied, built, nxt)
+            copied[slot].synchronize()
+            copy_ms.append(t_start.elapsed_time(copied[slot]))
+            if started is not None:
+                starts[1 - slot] = started
+
+    run(max(1, args.warmup), True)
     barrier(world)
     torch.cuda.synchronize()
+    copy_ms.clear()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
+    run(args.steps, True)
     torch.cuda.synchronize()
     barrier(world)
     el = max_over_ranks(time.perf_counter() - t0, world)
+    cms = statistics.median(copy_ms)
+    serial_steps = max(2, args.steps // 4)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    run(serial_steps, False)
+    torch.cuda.synchronize()
+    el_serial = max_over_ranks(time.perf_counter() - t1, world)
+    flops = state["flops"]
     return {"value": flops * world * args.steps / el / 1e12, "unit": UNIT,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": el * 1e3 / args.steps}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": state["d2h"],
+            "ms_per_step": el * 1e3 / args.steps,
+            "h2d_ms_per_step": cms, "h2d_gbs": h2d / (cms * 1e-3) / 1e9,
+            "how": ("each step's inputs copied host->device on a copy stream while the "
+                    "previous step computes (two landing buffers); C streamed to pinned "
+                    "host memory in 8 chunks while later chunks compute"),
+            "without_prefetch": {"value": flops * world * serial_steps / el_serial / 1e12,
+                                 "ms_per_step": el_serial * 1e3 / serial_steps,
+                                 "steps": serial_steps}}
 
 
 # ------------------------------------------------------- extra sections --
@@ -423,14 +499,18 @@ def section_banded(args, world, cht, torch):
     cht.sync_status()
     flops = plan.useful_flops
     ubytes = unique_bytes(A.nblocks, B.nblocks, plan.nnzb_C, A.b)
-    roof_ms = max(flops / (FP64_NOMINAL_TFLOPS * 1e12), ubytes / 6760.6e9) * 1e3
+    fp64_peak = MEASURED.get("fp64", FP64_NOMINAL_TFLOPS)
+    hbm = _measured_peak("hbm_gbs")
+    roof_ms = max(flops / (fp64_peak * 1e12), ubytes / (hbm * 1e9)) * 1e3
     return {"workload": "banded_N4096_b32_hw4", "pairs": plan.npairs,
             "nnzb_A": A.nblocks, "nnzb_B": B.nblocks, "nnzb_C": plan.nnzb_C,
             "useful_flops": flops, "unique_bytes": ubytes,
             "kernel_ms": kms, "kernel_tflops": flops / kms / 1e9,
             "roofline_ms": roof_ms, "frac_of_roofline": roof_ms / kms,
-            "roofline_basis": "FP64 nominal 1.25 TFLOP/s (compute-bound: the byte floor "
-                              "at the measured 6760 GB/s is far lower)",
+            "roofline_basis": (f"FP64 peak {fp64_peak:.3f} TFLOP/s "
+                               f"({'measured in this run' if 'fp64' in MEASURED else 'nominal'}"
+                               f"; compute-bound: the byte floor at the measured {hbm:.0f} GB/s "
+                               "is far lower)"),
             "step_ms": sms, "step_tflops": flops / sms / 1e9,
             "l2": "flushed (258 MB write) before each timed launch", "reps": reps}
 
@@ -729,12 +809,29 @@ def section_batched(args, world, cht, torch):
             bt.run()
         ms = _time_steps(torch, torch.cuda.current_stream(), g.replay, args.steps, args.warmup)
         cht.sync_status()
+
+        # the plain path on the same work: the same plans, operands and leaf
+        # sizes, one cht_multiply per product (each its own launch(es)),
+        # writing into the batch's outputs
+        def separate():
+            for i in range(bt.count):
+                A_i, B_i = tuned.mats[i]
+                cht.cht_multiply(tuned.plans[i], A_i, B_i, mode=mode, out=bt.output(i))
+        ms_sep = _time_steps(torch, torch.cuda.current_stream(), separate,
+                             max(1, args.steps // 2), min(args.warmup, 2))
+        cht.sync_status()
         results[name] = [(tuned.leaf_sizes[i], bt.output(i).values()) for i in range(bt.count)]
         out[name] = {"value": native_flops * world / (ms * 1e-3) / 1e12, "unit": UNIT,
                      "ms_per_step": ms, "leaf_sizes": {"32": tuned.leaf_sizes.count(32),
                                                        "64": tuned.leaf_sizes.count(64)},
                      "schedule": tuned.schedule, "launches_per_step": "1 graph replay",
-                     "graph": True}
+                     "graph": True,
+                     "vs_separate": {
+                         "separate_ms": ms_sep,
+                         "separate_value": native_flops * world / (ms_sep * 1e-3) / 1e12,
+                         "batch_speedup": ms_sep / ms,
+                         "what": "the same 64 products, plans and leaf sizes as 64 "
+                                 "consecutive cht_multiply calls (eager launches)"}}
         out[name]["_keep"] = (tuned, g)
     same = [(x, y) for (bx, x), (by, y) in zip(results["split"], results["fp64"]) if bx == by]
     num = sum(float(torch.linalg.norm((x - y).reshape(-1))) ** 2 for x, y in same) ** 0.5
@@ -744,6 +841,29 @@ def section_batched(args, world, cht, torch):
     for k in ("fp64", "split"):
         out[k].pop("_keep")
     return out
+
+
+def fp64_peak_sweep(cht, torch):
+    """FP64 throughput kernels over a small sweep (DFMA chains, the DFMA
+    register tile, the leaf GEMM's inner loop on shared-memory leaves, DMMA
+    chains; 128/256 threads; 1..8 CTAs per SM): the best is the FP64
+    roofline denominator."""
+    table = []
+    for engine, name in ((1, "dfma"), (2, "dfma_tile"), (3, "leaf_loop"), (0, "dmma")):
+        chain_set = {2: (32,), 3: (64, 32)}.get(engine, (8, 16, 32))
+        for ch in chain_set:
+            for threads in ((128,) if engine == 3 else (128, 256)):
+                for occ in (1, 2, 4, 8):
+                    t = cht.measure_fp64_peak_cfg(engine, ch, threads, occ)
+                    table.append({"kernel": name, "chains": ch, "threads": threads,
+                                  "ctas_per_sm": occ, "tflops": t})
+    best = max(table, key=lambda r: r["tflops"])
+    cfg = (f"{best['kernel']}, {best['chains']} chains, {best['threads']} threads x "
+           f"{best['ctas_per_sm']} CTAs per SM")
+    return {"best": best["tflops"], "best_cfg": cfg, "unit": UNIT,
+            "by_kernel": {k: max(r["tflops"] for r in table if r["kernel"] == k)
+                          for k in ("dfma", "dfma_tile", "leaf_loop", "dmma")},
+            "configs": len(table)}
 
 
 def _measured_peak(key):
@@ -849,13 +969,19 @@ def reference_arm(args, rank, world):
     value = flops * len(times) / total / 1e12
     sample = (f"first {rows} of {a.grid} leaf rows of A times B ({npairs} leaf pairs, "
               f"{flops / 1e9:.1f} GFLOP per step) of the 3D-locality N={args.n} b={a.b} product")
+    nA, nB, full_pairs, full_nC = host_pattern_counts(a, b)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total * 1e3 / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": f"3d_locality_N{args.n}_b{a.b}_cutoff6", "n": args.n,
-                   "leaf": a.b, "l2": "CPU run"},
+        # the workload's own config (as the GPU arm prints it); the CPU rate
+        # is measured on the slice described under "sample"
+        "config": workload_config(args.n, a.b, full_pairs, nA, nB, full_nC, world),
+        "sample": {"leaf_rows": rows, "of_leaf_rows": a.grid, "pairs": npairs,
+                   "flops_per_step": flops,
+                   "note": "the CPU oracle's rate is taken on this exact slice of the product "
+                           "(C's first leaf rows); a full product would take hours"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -896,7 +1022,8 @@ def main():
 
     res = fp64_main(args, world, rank, cht, torch)
     a, b = res.pop("host")
-    fp64_peak_meas = max(cht.measure_fp64_peak(1), cht.measure_fp64_peak(0))
+    fp64_peak = fp64_peak_sweep(cht, torch)
+    MEASURED["fp64"] = fp64_peak["best"]
 
     e2e = None
     if not args.no_e2e:
@@ -931,40 +1058,44 @@ def main():
         except Exception as e:  # context only; never hides the headline
             cpu_blas = {"status": "error", "error": f"{type(e).__name__}: {e}"}
 
-    # The leaf GEMM changed after its DRAM counters were taken (its per-unit
-    # loop became a device function shared with the batched kernel), so no
-    # traffic figure is claimed for the current build.
+    # DRAM traffic of the leaf GEMM from its ncu capture (profiles/), scaled
+    # from the captured case to this launch by the pair count
     prof = read_profile_traffic("leafgemm_f64_3d_locality")
-    traffic = None
-    traffic_note = ("null: the kernel changed after the ncu capture in "
-                    "profiles/leafgemm_f64_3d_locality.txt")
+    traffic, traffic_note = None, "no ncu capture of the current kernel in profiles/"
     if prof and "dram_bytes_per_pair" in prof:
-        traffic_note += (f" ({float(prof['dram_bytes_per_pair']) / 1e3:.0f} KB of DRAM "
-                         "traffic per pair there, on the earlier build)")
+        traffic = float(prof["dram_bytes_per_pair"]) * res["npairs"]
+        traffic_note = (f"ncu: {float(prof['dram_bytes_per_pair']):.0f} DRAM bytes per pair at "
+                        f"{prof.get('captured_case', 'a smaller case')}, x {res['npairs']} pairs")
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    clk = res["clocks"].get("sm_mhz") or 0.0
+    peak = fp64_peak["best"]
     roofline = {
         "kernel": "k_leafgemm_f64 (DFMA)", "bound": "alu",
-        "achieved": res["kernel_achieved"], "peak": FP64_NOMINAL_TFLOPS, "unit": UNIT,
-        "frac": res["kernel_achieved"] / FP64_NOMINAL_TFLOPS, "traffic": traffic,
+        "achieved": res["kernel_achieved"], "peak": peak, "unit": UNIT,
+        "frac": res["kernel_achieved"] / peak, "traffic": traffic,
         "traffic_note": traffic_note,
-        "peak_source": ("GB300 nominal dense FP64 (profiling recipe; no FP64 entry in the "
-                        "measured peaks); FP64 microbenchmark on this GPU: "
-                        f"{fp64_peak_meas:.3f} TFLOP/s"),
+        "peak_source": ("measured on this GPU: best of the FP64 throughput kernels "
+                        f"({fp64_peak['best_cfg']}); the sweep is under fp64_peak"),
+        "per_clock": {"sms": sms, "sm_mhz_median_in_step": clk,
+                      "fp64_fma_per_clk_per_sm": (peak * 1e12 / (2 * sms * clk * 1e6)
+                                                  if clk else None),
+                      "kernel_fma_per_clk_per_sm": (res["kernel_achieved"] * 1e12 /
+                                                    (2 * sms * clk * 1e6) if clk else None),
+                      "nominal_tflops": FP64_NOMINAL_TFLOPS},
         "algorithmic_flops_per_launch": res["flops"],
-        "hbm_floor_ms": res["unique_bytes"] / 6760.6e9 * 1e3,
+        "hbm_floor_ms": res["unique_bytes"] / _measured_peak("hbm_gbs") / 1e9 * 1e3,
     }
     line = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"3d_locality_N{args.n}_b{res['b']}_cutoff6",
-                   "n": args.n, "leaf": res["b"], "pairs": res["npairs"], "nnzb_A": res["nA"],
-                   "nnzb_B": res["nB"], "nnzb_C": res["nC"], "step": "symbolic + FP64 numeric",
-                   "l2": f"inputs {res['inputs_bytes'] / 1e9:.1f} GB > L2 {L2_BYTES / 1e6:.0f} MB",
-                   "parallelism": f"replicas x{world}"},
+        "config": workload_config(args.n, res["b"], res["npairs"], res["nA"], res["nB"],
+                                  res["nC"], world),
         "roofline": roofline, "cpu_baseline": cpu, "cpu_blas_baseline": cpu_blas, "e2e": e2e,
         "gpu_launches": res["launches"], "clocks": res["clocks"],
         "symbolic_ms": res["symbolic_ms"], "numeric_ms": res["kernel_ms"],
+        "fp64_peak": fp64_peak,
     }
     line.update(extra)
     if rank == 0:

@@ -402,13 +402,17 @@ const char *cht_last_error(void);
  * every SM, timed with CUDA events on `stream`, which is synchronised.
  * engine 1: `chains` independent FP64 FMA chains per thread; engine 2: a
  * 4 x 8 register tile of FMAs from 12 operand registers (the leaf GEMM's
- * inner loop without its loads; `chains` ignored); engine 0: `chains`
- * independent mma.sync m8n8k4 f64 chains per warp.  `threads` per CTA (a
- * multiple of 32, at most 1024), `ctas_per_sm` CTAs on each SM (1..32);
+ * inner loop without its loads; `chains` ignored); engine 3: the leaf
+ * GEMM's own inner loop (DFMA register tile fed from shared memory) over one
+ * pair of b x b leaves held in shared memory, b = `chains` (32 or 64), 128
+ * threads; engine 0: `chains` independent mma.sync m8n8k4 f64 chains per
+ * warp.  `threads` per CTA (a multiple of 32, at most 1024 and at most what
+ * the kernel's registers allow), `ctas_per_sm` CTAs on each SM (1..32);
  * chains 4, 8, 16 or 32.  *tflops gets FLOP/s / 1e12 of one ~40 ms launch
  * after a warm-up launch.  CHT_ERR_INVALID for other arguments.
- * cht_measure_fp64_peak returns the best of chains {8, 16, 32} x
- * {1, 2, 4} CTAs of 256 threads per SM for the engine. */
+ * cht_measure_fp64_peak returns the best of chains {8, 16, 32} (engine 3:
+ * b = 32, 64) x {1, 2, 4} CTAs per SM for the engine (256 threads; engine 3:
+ * 128). */
 int cht_measure_fp64_peak(int engine, void *stream, double *tflops);
 int cht_measure_fp64_peak_cfg(int engine, int chains, int threads, int ctas_per_sm,
                               void *stream, double *tflops);

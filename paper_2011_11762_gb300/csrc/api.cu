@@ -722,7 +722,7 @@ const char *cht_status_str(int status) {
 const char *cht_last_error(void) { return g_last_error; }
 
 int cht_measure_fp64_peak(int engine, void *stream, double *tflops) {
-  if (!tflops || engine < 0 || engine > 2) {
+  if (!tflops || engine < 0 || engine > 3) {
     set_error("invalid engine or null output");
     return CHT_ERR_INVALID;
   }

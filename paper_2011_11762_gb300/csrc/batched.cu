@@ -69,6 +69,7 @@ int batch_create(int32_t count, const cht_plan_t *plans, const cht_mat_t *As, co
       set_error("product %d: leaf size %d (the batched kernels take 32 or 64)", i, p->b);
       return CHT_ERR_UNSUPPORTED;
     }
+    if (p->b > bt->maxb) bt->maxb = p->b;
     bt->plans.push_back(p);
     bt->As.push_back(A);
     bt->Bs.push_back(B);
@@ -140,7 +141,7 @@ int batch_create(int32_t count, const cht_plan_t *plans, const cht_mat_t *As, co
 
 int batch_run(cht_batch *b, cudaStream_t s) {
   if (b->mode == CHT_SPLIT_BF16) return split_batch_run(b, s);
-  return launch_leafgemm_f64_batch(b->prods.p, b->units.p, b->nunits, b->counter.p, s);
+  return launch_leafgemm_f64_batch(b->prods.p, b->units.p, b->nunits, b->maxb, b->counter.p, s);
 }
 
 int batch_output(cht_batch *b, int32_t i, cht_mat **C) {

@@ -58,17 +58,22 @@ __global__ void k_compact(const uint64_t *__restrict__ skeys, const int32_t *__r
   }
 }
 
-__global__ void k_decode(const uint64_t *__restrict__ mkey, int64_t n, int L,
-                         int32_t *__restrict__ brow, int32_t *__restrict__ bcol,
-                         uint64_t *__restrict__ rkey, uint64_t *__restrict__ ckey,
-                         int32_t *__restrict__ idx) {
+__global__ void k_decode(const uint64_t *__restrict__ mkey, int64_t n,
+                         int32_t *__restrict__ brow, int32_t *__restrict__ bcol) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const uint32_t r = morton_row(mkey[i]), c = morton_col(mkey[i]);
-    brow[i] = static_cast<int32_t>(r);
-    bcol[i] = static_cast<int32_t>(c);
-    rkey[i] = (static_cast<uint64_t>(r) << L) | c;
-    ckey[i] = (static_cast<uint64_t>(c) << L) | r;
+    brow[i] = static_cast<int32_t>(morton_row(mkey[i]));
+    bcol[i] = static_cast<int32_t>(morton_col(mkey[i]));
+  }
+}
+
+// (row << L) | col and the leaf index, for the row-index sort.
+__global__ void k_row_keys(const int32_t *__restrict__ brow, const int32_t *__restrict__ bcol,
+                           int64_t n, int L, uint64_t *__restrict__ rkey,
+                           int32_t *__restrict__ idx) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    rkey[i] = (static_cast<uint64_t>(brow[i]) << L) | static_cast<uint32_t>(bcol[i]);
     idx[i] = static_cast<int32_t>(i);
   }
 }
@@ -120,30 +125,40 @@ int build_pattern_index(Pattern &p, cudaStream_t s) {
   const int64_t nnz = p.nnz;
   CHT_TRY(p.brow.alloc(nnz, s));
   CHT_TRY(p.bcol.alloc(nnz, s));
+  if (nnz > 0) {
+    k_decode<<<grid_for(nnz, 256), 256, 0, s>>>(p.mkey.p, nnz, p.brow.p, p.bcol.p);
+    CHT_TRY(launched("decode"));
+  }
+  return CHT_OK;
+}
+
+Pattern::~Pattern() {
+  if (rows_ready) cudaEventDestroy(rows_ready);
+}
+
+int ensure_row_index(const Pattern &p, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(p.rows_mutex);
+  if (p.have_rows) {
+    // ordered after the build, whichever stream it ran on
+    CHT_CUDA_TRY(cudaStreamWaitEvent(s, p.rows_ready, 0));
+    return CHT_OK;
+  }
+  const int64_t nnz = p.nnz;
   CHT_TRY(p.rowptr.alloc(p.G + 1, s));
-  CHT_TRY(p.colptr.alloc(p.G + 1, s));
   CHT_TRY(p.rowcol.alloc(nnz, s));
   CHT_TRY(p.rowleaf.alloc(nnz, s));
-  CHT_TRY(p.colrow.alloc(nnz, s));
-  CHT_TRY(p.colleaf.alloc(nnz, s));
-  DevArray<uint64_t> rkey, ckey, sk;
+  DevArray<uint64_t> rkey, sk;
   DevArray<int32_t> idx, cnt;
   CHT_TRY(rkey.alloc(nnz, s));
-  CHT_TRY(ckey.alloc(nnz, s));
   CHT_TRY(sk.alloc(nnz, s));
   CHT_TRY(idx.alloc(nnz, s));
   CHT_TRY(cnt.alloc(p.G, s));
   if (nnz > 0) {
-    k_decode<<<grid_for(nnz, 256), 256, 0, s>>>(p.mkey.p, nnz, p.L, p.brow.p, p.bcol.p, rkey.p,
-                                                ckey.p, idx.p);
-    CHT_TRY(launched("decode"));
+    k_row_keys<<<grid_for(nnz, 256), 256, 0, s>>>(p.brow.p, p.bcol.p, nnz, p.L, rkey.p, idx.p);
+    CHT_TRY(launched("row_keys"));
     // CSR by leaf row: sort by (row, col)
     CHT_TRY(radix_sort_pairs(rkey.p, idx.p, sk.p, p.rowleaf.p, nnz, 2 * p.L, s));
     k_split_key<<<grid_for(nnz, 256), 256, 0, s>>>(sk.p, nnz, p.L, p.rowcol.p);
-    CHT_TRY(launched("split_key"));
-    // CSC by leaf column: sort by (col, row)
-    CHT_TRY(radix_sort_pairs(ckey.p, idx.p, sk.p, p.colleaf.p, nnz, 2 * p.L, s));
-    k_split_key<<<grid_for(nnz, 256), 256, 0, s>>>(sk.p, nnz, p.L, p.colrow.p);
     CHT_TRY(launched("split_key"));
   }
   CHT_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * p.G, s));
@@ -152,12 +167,10 @@ int build_pattern_index(Pattern &p, cudaStream_t s) {
     CHT_TRY(launched("count"));
   }
   CHT_TRY(scan_exclusive(cnt.p, p.rowptr.p, p.G, s));
-  CHT_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * p.G, s));
-  if (nnz > 0) {
-    k_count<<<grid_for(nnz, 256), 256, 0, s>>>(p.bcol.p, nnz, cnt.p);
-    CHT_TRY(launched("count"));
-  }
-  CHT_TRY(scan_exclusive(cnt.p, p.colptr.p, p.G, s));
+  if (!p.rows_ready)
+    CHT_CUDA_TRY(cudaEventCreateWithFlags(&p.rows_ready, cudaEventDisableTiming));
+  CHT_CUDA_TRY(cudaEventRecord(p.rows_ready, s));
+  p.have_rows = true;
   return CHT_OK;
 }
 

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstdint>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "cht.h"
@@ -93,7 +94,10 @@ struct DevArray {
 };
 
 // ---------------------------------------------------------------- pattern --
-// The stored leaves of a matrix in Morton order, with row and column indexes.
+// The stored leaves of a matrix in Morton order, with a row index (CSR) that
+// is built the first time a symbolic phase reads it: most product patterns
+// are never the right operand of another product, and the index costs two
+// radix-sort passes per build.
 struct Pattern {
   int64_t n = 0;
   int32_t b = 0;
@@ -103,14 +107,24 @@ struct Pattern {
   uint64_t id = 0; // unique per pattern object
   DevArray<uint64_t> mkey;                   // Morton keys, ascending
   DevArray<int32_t> brow, bcol;              // per leaf
-  DevArray<int64_t> rowptr, colptr;          // [G + 1]
-  DevArray<int32_t> rowcol, rowleaf;         // CSR by leaf row (cols ascending)
-  DevArray<int32_t> colrow, colleaf;         // CSC by leaf col (rows ascending)
+  // CSR by leaf row (columns ascending); see ensure_row_index
+  mutable DevArray<int64_t> rowptr;          // [G + 1]
+  mutable DevArray<int32_t> rowcol, rowleaf; // [nnz]
+  mutable bool have_rows = false;
+  mutable cudaEvent_t rows_ready = nullptr;  // recorded after the index build
+  mutable std::mutex rows_mutex;
+  Pattern() = default;
+  Pattern(const Pattern &) = delete;
+  Pattern &operator=(const Pattern &) = delete;
+  ~Pattern();
 };
 uint64_t next_id();
 int bits_for(int64_t G);
-// Fills brow/bcol and the row and column indexes from the sorted mkey.
+// Fills brow/bcol from the sorted mkey.
 int build_pattern_index(Pattern &p, cudaStream_t s);
+// Makes p's row index available to work queued on s after this call: built
+// on s at the first call, later calls on other streams wait for that build.
+int ensure_row_index(const Pattern &p, cudaStream_t s);
 // *same = true when x and y store the same leaves (equal n, b and Morton
 // keys).  Different pattern objects are compared on the device: d_flag is 4
 // bytes of device scratch, and the call synchronises s to read it.
@@ -166,10 +180,11 @@ struct ProdDesc {
   int32_t b;
   int32_t pad;
 };
-// Batched FP64 multiply: units (product << 32 | output leaf) in one launch.
+// Batched FP64 multiply: units (product << 32 | output leaf) in one launch;
+// maxb = the largest leaf size among the products (32 or 64).
 // d_counter: 8 bytes of device scratch, zeroed by the call.
 int launch_leafgemm_f64_batch(const ProdDesc *d_prods, const int64_t *d_units, int64_t nunits,
-                              unsigned long long *d_counter, cudaStream_t s);
+                              int maxb, unsigned long long *d_counter, cudaStream_t s);
 
 int launch_fp64_peak(int engine, cudaStream_t s, double *tflops);
 int launch_fp64_peak_cfg(int engine, int chains, int threads, int per_sm, cudaStream_t s,
@@ -230,6 +245,7 @@ struct cht_batch {
   cht::DevArray<double> cvals;    // every product's C values
   cht::DevArray<unsigned long long> counter;
   int64_t nunits = 0;
+  int maxb = 32;                  // largest leaf size among the products
   std::vector<std::unique_ptr<cht_mat>> views;
   void *split_state = nullptr;    // owned by the split path
   ~cht_batch();

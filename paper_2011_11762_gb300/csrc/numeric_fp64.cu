@@ -213,12 +213,14 @@ __global__ void __launch_bounds__(kThreads)
 
 // Batched form: units from many products (each with its own leaf size) in
 // one launch.  Unit u is product units[u] >> 32, output leaf units[u] & 0xffffffff.
-template <int ENGINE>
+// MAXB is the largest leaf size of the batch: the stage ring is sized for it
+// (a batch of 32-leaf products gets the 32-leaf kernel's ring and occupancy).
+template <int ENGINE, int MAXB>
 __global__ void __launch_bounds__(kThreads)
     k_leafgemm_f64_batch(const ProdDesc *__restrict__ prods, const int64_t *__restrict__ units,
                          int64_t nunits, int *__restrict__ status, int64_t wait_ns,
                          unsigned long long *__restrict__ next_unit) {
-  constexpr int S = 2, PITCH = 64 * 64;
+  constexpr int S = LeafCfg<MAXB>::kStages, PITCH = MAXB * MAXB;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double *sx = reinterpret_cast<double *>(smem_raw);
   double *sy = sx + S * PITCH;
@@ -241,13 +243,19 @@ __global__ void __launch_bounds__(kThreads)
     const ProdDesc d = prods[packed >> 32];
     const int64_t o = packed & 0xffffffffLL;
     const int64_t p0 = d.seg[o], np = d.seg[o + 1] - p0;
-    bool ok;
-    if (d.b == 64)
-      ok = run_unit<64, false, false, ENGINE, S>(d.X, d.Y, d.Z + o * 4096, d.px, d.py, p0, np, sx,
-                                                 sy, PITCH, full, it, wait_ns, status);
-    else
+    bool ok = false;
+    if constexpr (MAXB == 64) {
+      if (d.b == 64)
+        ok = run_unit<64, false, false, ENGINE, S>(d.X, d.Y, d.Z + o * 4096, d.px, d.py, p0, np,
+                                                   sx, sy, PITCH, full, it, wait_ns, status);
+      else
+        ok = run_unit<32, false, false, ENGINE, S>(d.X, d.Y, d.Z + o * 1024, d.px, d.py, p0, np,
+                                                   sx, sy, PITCH, full, it, wait_ns, status);
+    } else {
+      // every product of this batch has 32-leaves
       ok = run_unit<32, false, false, ENGINE, S>(d.X, d.Y, d.Z + o * 1024, d.px, d.py, p0, np, sx,
                                                  sy, PITCH, full, it, wait_ns, status);
+    }
     if (!ok) return;
   }
 }
@@ -324,6 +332,30 @@ __global__ void k_peak_tile(double *out, int iters, double y, double x0) {
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) s += acc[i][j];
+  if (s == 12345.0) out[0] = s;
+}
+
+// The leaf GEMM's own inner loop (Tile<B, ..., DFMA>::mac) over one pair of
+// B x B leaves held in shared memory, `iters` times: the FP64 kernel's
+// arithmetic and shared-memory loads without its copies and unit hand-offs.
+template <int B>
+__global__ void __launch_bounds__(kThreads) k_peak_leaf(double *out, int iters, double y,
+                                                        double x0) {
+  extern __shared__ __align__(16) double peak_smem[];
+  double *sx = peak_smem, *sy = peak_smem + B * B;
+  for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+    sx[e] = y * (1.0 + 1e-6 * e);
+    sy[e] = x0 * (1.0 - 1e-6 * e);
+  }
+  __syncthreads();
+  Tile<B, false, false, 1> tile;
+  tile.zero();
+  for (int n = 0; n < iters; ++n) tile.mac(sx, sy);
+  double s = 0;
+#pragma unroll
+  for (int i = 0; i < Tile<B, false, false, 1>::RM; ++i)
+#pragma unroll
+    for (int j = 0; j < Tile<B, false, false, 1>::RN; ++j) s += tile.acc[i][j];
   if (s == 12345.0) out[0] = s;
 }
 
@@ -436,14 +468,16 @@ int multiply_f64_to_host(const GemmWork &w0, int64_t nchunks, double *h_out, cud
 }
 
 int launch_leafgemm_f64_batch(const ProdDesc *d_prods, const int64_t *d_units, int64_t nunits,
-                              unsigned long long *d_counter, cudaStream_t s) {
+                              int maxb, unsigned long long *d_counter, cudaStream_t s) {
   if (nunits <= 0) return CHT_OK;
   int *status = nullptr;
   CHT_TRY(device_status_ptr(&status));
   int sms = 0;
   CHT_TRY(num_sms(&sms));
-  const size_t smem = sizeof(double) * 2 * 2 * 64 * 64 + 16 * 2;
-  auto kern = g_opt.fp64_engine ? k_leafgemm_f64_batch<1> : k_leafgemm_f64_batch<0>;
+  const size_t smem = maxb == 64 ? LeafCfg<64>::kSmem : LeafCfg<32>::kSmem;
+  auto kern = maxb == 64
+                  ? (g_opt.fp64_engine ? k_leafgemm_f64_batch<1, 64> : k_leafgemm_f64_batch<0, 64>)
+                  : (g_opt.fp64_engine ? k_leafgemm_f64_batch<1, 32> : k_leafgemm_f64_batch<0, 32>);
   CHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem)));
   int occ = 0;
@@ -462,19 +496,45 @@ int launch_leafgemm_f64_batch(const ProdDesc *d_prods, const int64_t *d_units, i
 // then one timed launch (CUDA events on s).
 int launch_fp64_peak_cfg(int engine, int chains, int threads, int per_sm, cudaStream_t s,
                          double *tflops) {
-  if (engine < 0 || engine > 2 || threads < 32 || threads > 1024 || threads % 32 != 0 ||
-      per_sm < 1 || per_sm > 32 ||
-      (engine != 2 && chains != 4 && chains != 8 && chains != 16 && chains != 32)) {
-    set_error("FP64 peak: engine 0..2, chains 4/8/16/32, threads a multiple of 32 in "
-              "[32, 1024], 1..32 CTAs per SM");
+  const bool chains_ok = engine == 3 ? (chains == 32 || chains == 64)
+                                     : (chains == 4 || chains == 8 || chains == 16 ||
+                                        chains == 32 || engine == 2);
+  if (engine < 0 || engine > 3 || threads < 32 || threads > 1024 || threads % 32 != 0 ||
+      per_sm < 1 || per_sm > 32 || !chains_ok || (engine == 3 && threads != kThreads)) {
+    set_error("FP64 peak: engine 0..3, chains 4/8/16/32 (engine 3: the leaf size, 32 or 64, "
+              "with %d threads), threads a multiple of 32 in [32, 1024], 1..32 CTAs per SM",
+              kThreads);
+    return CHT_ERR_INVALID;
+  }
+  const void *fn = nullptr;
+  switch (engine) {
+    case 0:
+      fn = chains == 4 ? (const void *)k_peak_dmma<4> : chains == 8 ? (const void *)k_peak_dmma<8>
+           : chains == 16 ? (const void *)k_peak_dmma<16> : (const void *)k_peak_dmma<32>;
+      break;
+    case 1:
+      fn = chains == 4 ? (const void *)k_peak_dfma<4> : chains == 8 ? (const void *)k_peak_dfma<8>
+           : chains == 16 ? (const void *)k_peak_dfma<16> : (const void *)k_peak_dfma<32>;
+      break;
+    case 2: fn = (const void *)k_peak_tile; break;
+    default: fn = chains == 64 ? (const void *)k_peak_leaf<64> : (const void *)k_peak_leaf<32>;
+  }
+  cudaFuncAttributes fa;
+  CHT_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+  if (threads > fa.maxThreadsPerBlock) {
+    set_error("FP64 peak: %d threads exceed this kernel's %d (registers)", threads,
+              fa.maxThreadsPerBlock);
     return CHT_ERR_INVALID;
   }
   int sms = 0;
   CHT_TRY(num_sms(&sms));
   const int grid = sms * per_sm;
   const int ch = engine == 2 ? 32 : chains;
-  // FLOPs per iteration per thread (a DMMA's 2 * 8 * 8 * 4 shared by 32 lanes)
-  const double per_iter = engine == 0 ? ch * 2.0 * 8 * 8 * 4 / 32.0 : ch * 2.0;
+  // FLOPs per iteration per thread (a DMMA's 2 * 8 * 8 * 4 shared by 32 lanes;
+  // one leaf product, 2 b^3, shared by the kThreads threads)
+  const double per_iter = engine == 0   ? ch * 2.0 * 8 * 8 * 4 / 32.0
+                          : engine == 3 ? 2.0 * ch * ch * ch / kThreads
+                                        : ch * 2.0;
   const double target = 4.8e10;  // ~40 ms at 1.2 TFLOP/s
   int64_t iters = static_cast<int64_t>(target / (static_cast<double>(grid) * threads * per_iter));
   iters = std::max<int64_t>(64, std::min<int64_t>(iters, 1 << 24));
@@ -488,7 +548,19 @@ int launch_fp64_peak_cfg(int engine, int chains, int threads, int per_sm, cudaSt
   int rc = CHT_OK;
   for (int rep = 0; rep < 2 && rc == CHT_OK; ++rep) {
     if (rep == 1) cudaEventRecord(e0, s);
-    if (engine == 2) {
+    if (engine == 3) {
+      // two b x b leaves of dynamic shared memory (64 KB at b = 64)
+      const int smem = static_cast<int>(2 * sizeof(double) * ch * ch);
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "fp64 peak smem attribute");
+        break;
+      }
+      if (ch == 64)
+        k_peak_leaf<64><<<grid, threads, smem, s>>>(out.p, it, y, x0);
+      else
+        k_peak_leaf<32><<<grid, threads, smem, s>>>(out.p, it, y, x0);
+    } else if (engine == 2) {
       k_peak_tile<<<grid, threads, 0, s>>>(out.p, it, y, x0);
     } else if (engine == 1) {
       switch (ch) {
@@ -522,17 +594,18 @@ int launch_fp64_peak_cfg(int engine, int chains, int threads, int per_sm, cudaSt
   return CHT_OK;
 }
 
-// The best of a small sweep (chains x CTAs per SM, 256 threads).
+// The best of a small sweep for the engine (chains x CTAs per SM).
 int launch_fp64_peak(int engine, cudaStream_t s, double *tflops) {
   double best = 0.0;
   const int chain_set[] = {8, 16, 32};
+  const int leaf_set[] = {32, 64};
   const int occ_set[] = {1, 2, 4};
-  for (int ch : chain_set)
+  for (int i = 0; i < (engine == 3 ? 2 : 3); ++i)
     for (int occ : occ_set) {
       double t = 0.0;
-      CHT_TRY(launch_fp64_peak_cfg(engine, ch, 256, occ, s, &t));
+      const int ch = engine == 3 ? leaf_set[i] : chain_set[i];
+      CHT_TRY(launch_fp64_peak_cfg(engine, ch, engine == 3 ? kThreads : 256, occ, s, &t));
       best = std::max(best, t);
-      if (engine == 2) break;
     }
   *tflops = best;
   return CHT_OK;

@@ -225,6 +225,17 @@ __device__ inline bool wait_or_abort(uint64_t *bar, uint32_t parity, int64_t bud
   }
 }
 
+// The same wait for a whole warp, with one outcome for all its lanes: every
+// lane polls, and the warp goes on only if every lane saw the phase complete.
+// The epilogue's tcgen05.ld / st / wait instructions are .sync.aligned (all 32
+// lanes must execute them together), so a warp must not split between lanes
+// that saw the phase and lanes that saw the abort flag or the deadline.
+__device__ inline bool warp_wait_or_abort(uint64_t *bar, uint32_t parity, int64_t budget_ns,
+                                          volatile int *abort_flag) {
+  const bool ok = wait_or_abort(bar, parity, budget_ns, abort_flag);
+  return __all_sync(0xffffffffu, ok);
+}
+
 // -------------------------------------------------------- digits / scale --
 // The "no exponent" marker (all-zero line); also the byte-0x80 memset value.
 constexpr int kNoExp = static_cast<int>(0x80808080u);
@@ -660,7 +671,7 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
   float rl[E];  // low region (t = 6), folded: R6 2^-8 + R7 2^-16
   for (int64_t w0 = 0; w0 < np; w0 += WINDOW, ++win) {
     const bool last = w0 + WINDOW >= np, first = w0 == 0;
-    if (!wait_or_abort(acc_full, win & 1u, c.wait_ns, c.abort_flag)) return false;
+    if (!warp_wait_or_abort(acc_full, win & 1u, c.wait_ns, c.abort_flag)) return false;
     tc_fence_after();
     // exact regions r = 0, 1 (base diagonal t = 2 + 2r); column half qq of a
     // region holds diagonal t + part + qq, weight 2^(8 (5 - t - qq)) in
@@ -766,7 +777,7 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(c.ep_bar);
-      if (!wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag)) return false;
+      if (!warp_wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag)) return false;
       ++epb;
       const int er = sl.rexp[row];
       const int cb = c0 + (part == 0 ? 0 : H);
@@ -791,7 +802,7 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
         xb[(static_cast<int64_t>(part) * B + c0 + cc) * B + row] = part_value(cc);
       __syncwarp();
       if (lane == 0) mbar_arrive(c.ep_bar);
-      if (!wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag)) return false;
+      if (!warp_wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag)) return false;
       ++epb;
       const int et = threadIdx.x - 64;  // epilogue thread index
       const int r = et % B, col = (et / B) * 4;
@@ -1086,7 +1097,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t win0 = 0, win1 = 0, epb = 0;
     for (uint32_t n = 0;; ++n) {
       const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
-      if (!wait_or_abort(&c.qfull[qs], qph, c.wait_ns, c.abort_flag)) {
+      if (!warp_wait_or_abort(&c.qfull[qs], qph, c.wait_ns, c.abort_flag)) {
         fail();
         break;
       }
@@ -1115,7 +1126,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // one exchange buffer: part 0 must have read it before the next unit
         __syncwarp();
         if (lane == 0) mbar_arrive(c.ep_bar);
-        if (!wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag)) {
+        if (!warp_wait_or_abort(c.ep_bar, epb & 1u, c.wait_ns, c.abort_flag)) {
           fail();
           break;
         }

@@ -72,11 +72,13 @@ __global__ void k_heads(const uint64_t *__restrict__ skey, int64_t P, int L,
   GRID_STRIDE(i, P) head[i] = (i == 0 || (skey[i] >> L) != (skey[i - 1] >> L)) ? 1 : 0;
 }
 
-// S4: C leaf of every pair, and each C leaf's Morton key and segment start.
+// S4: C leaf of every pair, and each C leaf's Morton key and segment start;
+// *d_nC = cpos[P], the number of C leaves (read from the device, so the
+// host need not know it yet).
 __global__ void k_segments(const uint64_t *__restrict__ skey, const int64_t *__restrict__ cpos,
-                           const int32_t *__restrict__ head, int64_t P, int L, int64_t nC,
-                           uint64_t *__restrict__ ckey, int64_t *__restrict__ cseg,
-                           int32_t *__restrict__ pc) {
+                           const int32_t *__restrict__ head, int64_t P, int L,
+                           const int64_t *__restrict__ d_nC, uint64_t *__restrict__ ckey,
+                           int64_t *__restrict__ cseg, int32_t *__restrict__ pc) {
   GRID_STRIDE(i, P) {
     const int64_t c = cpos[i] - (head[i] ? 0 : 1);
     pc[i] = static_cast<int32_t>(c);
@@ -84,23 +86,27 @@ __global__ void k_segments(const uint64_t *__restrict__ skey, const int64_t *__r
       cseg[c] = i;
       ckey[c] = skey[i] >> L;
     }
-    if (i == 0) cseg[nC] = P;
+    if (i == 0) cseg[*d_nC] = P;
   }
 }
 
-// S5: longest-first order key (stable sort keeps Morton order among ties).
+// S5: longest-first order key (stable sort keeps Morton order among ties);
+// 16 bits: segments of 65535 pairs or more all count as longest.
+constexpr int kLptBits = 16;
 __global__ void k_lpt_keys(const int64_t *__restrict__ seg, int64_t n, uint64_t *__restrict__ key,
                            int32_t *__restrict__ idx) {
   GRID_STRIDE(u, n) {
     int64_t len = seg[u + 1] - seg[u];
-    if (len > 0xffffffffLL) len = 0xffffffffLL;
-    key[u] = 0xffffffffULL - static_cast<uint64_t>(len);
+    if (len > 0xffffLL) len = 0xffffLL;
+    key[u] = 0xffffULL - static_cast<uint64_t>(len);
     idx[u] = static_cast<int32_t>(u);
   }
 }
 
-__global__ void k_max_seg(const int64_t *__restrict__ seg, int64_t n,
+// Longest segment of the *d_n segments of seg (the count read on the device).
+__global__ void k_max_seg(const int64_t *__restrict__ seg, const int64_t *__restrict__ d_n,
                           unsigned long long *__restrict__ out) {
+  const int64_t n = *d_n;
   unsigned long long m = 0;
   GRID_STRIDE(u, n) m = max(m, static_cast<unsigned long long>(seg[u + 1] - seg[u]));
 #pragma unroll
@@ -226,6 +232,7 @@ static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
                         const double *normB = nullptr, double tau = 0.0,
                         bool upper_only = false) {
   const int L = A.L;
+  CHT_TRY(ensure_row_index(B, s));
   DevArray<int32_t> cnt;
   DevArray<int64_t> off;
   CHT_TRY(cnt.alloc(A.nnz, s));
@@ -311,7 +318,7 @@ int schedule_units(const int64_t *seg, int64_t n, int32_t *order, cudaStream_t s
   CHT_TRY(idx.alloc(n, s));
   k_lpt_keys<<<grid_for(n, 256), 256, 0, s>>>(seg, n, key.p, idx.p);
   CHT_TRY(launched("lpt_keys"));
-  return radix_sort_pairs(key.p, idx.p, skey.p, order, n, 32, s);
+  return radix_sort_pairs(key.p, idx.p, skey.p, order, n, kLptBits, s);
 }
 
 int leaf_norms(const double *vals, int64_t n, int b, double *out, cudaStream_t s) {
@@ -351,8 +358,32 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
     CHT_TRY(launched("heads"));
   }
   CHT_TRY(scan_exclusive(head.p, cpos.p, P, s));
-  int64_t nC = 0;
-  CHT_TRY(read_i64(cpos.p + P, &nC, s));
+  // C leaves <= P: segments and keys are written at that capacity, and one
+  // synchronisation reads the C leaf count and the longest segment together
+  const int64_t *d_nC = cpos.p + P;
+  DevArray<uint64_t> ckey_cap;
+  DevArray<int64_t> cseg_cap, stats;
+  CHT_TRY(ckey_cap.alloc(P, s));
+  CHT_TRY(cseg_cap.alloc(P + 1, s));
+  CHT_TRY(plan->pc.alloc(P, s));
+  CHT_TRY(stats.alloc(1, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(stats.p, 0, sizeof(int64_t), s));
+  if (P > 0) {
+    k_segments<<<grid_for(P, 256), 256, 0, s>>>(skey.p, cpos.p, head.p, P, L, d_nC, ckey_cap.p,
+                                                cseg_cap.p, plan->pc.p);
+    CHT_TRY(launched("segments"));
+    k_max_seg<<<grid_for(P, 256), 256, 0, s>>>(cseg_cap.p, d_nC,
+                                                reinterpret_cast<unsigned long long *>(stats.p));
+    CHT_TRY(launched("max_seg"));
+  } else {
+    CHT_CUDA_TRY(cudaMemsetAsync(cseg_cap.p, 0, sizeof(int64_t), s));
+  }
+  int64_t host_stats[2] = {0, 0};
+  CHT_CUDA_TRY(cudaMemcpyAsync(&host_stats[0], d_nC, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CHT_CUDA_TRY(cudaMemcpyAsync(&host_stats[1], stats.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CHT_CUDA_TRY(cudaStreamSynchronize(s));
+  const int64_t nC = host_stats[0];
+  plan->max_seg = host_stats[1];
 
   auto C = std::make_shared<Pattern>();
   C->n = A.n;
@@ -363,26 +394,14 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   C->id = next_id();
   CHT_TRY(C->mkey.alloc(nC, s));
   CHT_TRY(plan->cseg.alloc(nC + 1, s));
-  CHT_TRY(plan->pc.alloc(P, s));
   CHT_TRY(plan->order.alloc(nC, s));
-  if (P > 0) {
-    k_segments<<<grid_for(P, 256), 256, 0, s>>>(skey.p, cpos.p, head.p, P, L, nC, C->mkey.p,
-                                                plan->cseg.p, plan->pc.p);
-    CHT_TRY(launched("segments"));
-  } else {
-    CHT_CUDA_TRY(cudaMemsetAsync(plan->cseg.p, 0, sizeof(int64_t), s));
-  }
+  if (nC > 0)
+    CHT_CUDA_TRY(cudaMemcpyAsync(C->mkey.p, ckey_cap.p, sizeof(uint64_t) * nC,
+                                 cudaMemcpyDeviceToDevice, s));
+  CHT_CUDA_TRY(cudaMemcpyAsync(plan->cseg.p, cseg_cap.p, sizeof(int64_t) * (nC + 1),
+                               cudaMemcpyDeviceToDevice, s));
   CHT_TRY(build_pattern_index(*C, s));
   CHT_TRY(schedule_units(plan->cseg.p, nC, plan->order.p, s));
-  if (nC > 0) {
-    DevArray<int64_t> mx;
-    CHT_TRY(mx.alloc(1, s));
-    CHT_CUDA_TRY(cudaMemsetAsync(mx.p, 0, sizeof(int64_t), s));
-    k_max_seg<<<grid_for(nC, 256), 256, 0, s>>>(plan->cseg.p, nC,
-                                                 reinterpret_cast<unsigned long long *>(mx.p));
-    CHT_TRY(launched("max_seg"));
-    CHT_TRY(read_i64(mx.p, &plan->max_seg, s));
-  }
   plan->pa = std::move(pa);
   plan->pb = std::move(pb);
   plan->C = std::move(C);
@@ -456,6 +475,7 @@ int backward_lists_recompute(const Pattern &A, const Pattern &B, const Pattern &
   DevArray<int32_t> pa, pb;
   int64_t P = 0;
   CHT_TRY(make_triples(A, B, s, skey, pa, pb, &P));
+  CHT_TRY(ensure_row_index(dC, s));
   DevArray<int32_t> pc, keep, ka, kb, kc;
   DevArray<int64_t> pos;
   CHT_TRY(pc.alloc(P, s));

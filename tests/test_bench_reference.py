@@ -27,7 +27,14 @@ def _check_line(line, n_gpus):
     assert line["impl"] == "reference"
     assert line["n_gpus"] == n_gpus and line["steps"] == 1 and line["warmup"] == 0
     assert line["value"] > 0 and line["unit"] == "TFLOP/s" and line["higher_is_better"]
-    assert line["config"]["workload"] == "3d_locality_N8192_b64_cutoff6"
+    cfg = line["config"]
+    # the GPU arm's config keys and values for the same workload (N = 8192:
+    # 5160 leaves per operand, 12792 C leaves, 226536 pairs)
+    assert cfg == {"workload": "3d_locality_N8192_b64_cutoff6", "n": 8192, "leaf": 64,
+                   "pairs": 226536, "nnzb_A": 5160, "nnzb_B": 5160, "nnzb_C": 12792,
+                   "step": "symbolic + FP64 numeric", "l2": "inputs 0.3 GB > L2 129 MB",
+                   "parallelism": f"replicas x{n_gpus}"}
+    assert line["sample"]["pairs"] > 0 and line["sample"]["leaf_rows"] >= 1
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     assert "leaf rows" in cb["sample"]
