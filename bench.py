@@ -435,26 +435,65 @@ def section_split(args, world, cht, torch):
 
         _time_steps(torch, stream, numeric_only, args.steps, 1)
         kms = statistics.mean(kern.ms()[1:])
-        # MMA work: per pair, (6 | 4) blocks of M = 128, N = 2b, K = b
-        nblk = 6 if A.b == 64 else 4
-        slice_flops = plan.npairs * nblk * 2 * 128 * (2 * A.b) * A.b
-        prof = read_profile_traffic("split_gemm_3d_locality" if A.b == 64
+        b_ = A.b
+        s_ = 6
+        # algorithmic work of the split form: s (s + 1) / 2 = 21 slice
+        # products per leaf pair; bytes: the FP64 operands read and C
+        # written once, the (unpadded) BF16 slices written and read once
+        alg_flops = plan.npairs * (s_ * (s_ + 1) // 2) * 2 * b_ ** 3
+        alg_bytes = ((A.nblocks + B.nblocks + plan.nnzb_C) * b_ * b_ * 8
+                     + 2 * (A.nblocks + B.nblocks) * s_ * b_ * b_ * 2)
+        # what the MMA blocks issue: per pair (6 | 4) blocks of M = 128, N = 2b, K = b
+        nblk = 6 if b_ == 64 else 4
+        mma_flops = plan.npairs * nblk * 2 * 128 * (2 * b_) * b_
+        hbm = _measured_peak("hbm_gbs")
+        t_tensor = alg_flops / (peak_bf16 * 1e12)
+        t_hbm = alg_bytes / (hbm * 1e9)
+        prof = read_profile_traffic("split_gemm_3d_locality" if b_ == 64
                                     else "split_gemm_random_b32")
         traffic = (float(prof["dram_bytes_per_pair"]) * plan.npairs
                    if prof and "dram_bytes_per_pair" in prof else None)
+        if t_tensor >= t_hbm:
+            roof = {"bound": "tensor", "achieved": alg_flops / (kms * 1e-3) / 1e12,
+                    "peak": peak_bf16, "unit": "TFLOP/s",
+                    "frac": alg_flops / (kms * 1e-3) / 1e12 / peak_bf16,
+                    "peak_source": "measured bf16 dense (burst)"}
+        else:
+            roof = {"bound": "hbm", "achieved": alg_bytes / (kms * 1e-3) / 1e9,
+                    "peak": hbm, "unit": "GB/s",
+                    "frac": alg_bytes / (kms * 1e-3) / 1e9 / hbm,
+                    "peak_source": "measured copy bandwidth"}
+        roof.update({"kernel": "the split numeric phase (tcgen05 kind::f16 kernels), timed "
+                               "with its exponent and slicing pre-kernels",
+                     "traffic": traffic, "algorithmic_flops_per_launch": alg_flops,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "slice_products_per_pair": s_ * (s_ + 1) // 2,
+                     "mma_flops_per_launch": mma_flops,
+                     "mma_frac_of_bf16_peak": mma_flops / (kms * 1e-3) / 1e12 / peak_bf16,
+                     "roofline_ms": max(t_tensor, t_hbm) * 1e3})
         entry = {
             "value": flops * world / (ms_split * 1e-3) / 1e12, "unit": UNIT,
             "ms_per_step": ms_split, "numeric_ms": kms, "pairs": plan.npairs,
+            "nnzb_C": plan.nnzb_C, "one_pair_c_leaves": None,
             "rel_fro_err_vs_fp64": err, "a_priori_bound": bound,
-            "roofline": {"kernel": "k_split_gemm (tcgen05 kind::f16), timed with its "
-                                   "exponent and slicing pre-kernels",
-                         "bound": "tensor", "achieved": slice_flops / (kms * 1e-3) / 1e12,
-                         "peak": peak_bf16, "unit": "TFLOP/s",
-                         "frac": slice_flops / (kms * 1e-3) / 1e12 / peak_bf16,
-                         "traffic": traffic,
-                         "algorithmic_flops_per_launch": slice_flops,
-                         "peak_source": "measured bf16 dense (burst)"},
+            "roofline": roof,
         }
+        if b_ == 32:
+            seg = torch.diff(plan.arrays()["cseg"])
+            entry["one_pair_c_leaves"] = int((seg == 1).sum())
+            # the same numeric phase with every C leaf on the general kernel
+            cht.set_option(cht.OPT_SPLIT_SINGLE, 0)
+            try:
+                kern0 = Timer(stream)
+
+                def general_only():
+                    e = kern0.start()
+                    cht.cht_multiply(plan, A, B, mode=cht.CHT_SPLIT_BF16, out=Cs)
+                    kern0.stop(e)
+                _time_steps(torch, stream, general_only, args.steps, 1)
+            finally:
+                cht.set_option(cht.OPT_SPLIT_SINGLE, 1)
+            entry["general_kernel_only_numeric_ms"] = statistics.mean(kern0.ms()[1:])
         if name.startswith("random"):
             def step_fp64():
                 p = cht.cht_symbolic_multiply(A, B)

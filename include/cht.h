@@ -256,7 +256,12 @@ int cht_plan_free(cht_plan_t P);
  * Each C leaf is summed in ascending K by one CTA: results are bitwise
  * reproducible run to run.  No atomics touch C.
  * CHT_SPLIT_BF16: nslices = 0 or 6 (6 digits of 8 bits per operand, 48
- * bits); inputs must be finite; b = 32 or 64.  One work unit sums at most
+ * bits); inputs must be finite; b = 32 or 64.  At b = 32 the C leaves with
+ * exactly one leaf pair are computed by a kernel that stacks four of them
+ * sharing a B leaf in one MMA (slice pairs i + j <= 7); the other C leaves
+ * by the general kernel (8 A digits, 4 stacked A slices).  The first such
+ * multiply on a plan groups its one-pair leaves and keeps the groups in the
+ * plan (synchronises `stream` twice).  One work unit sums at most
  * 1016 (b = 64) or 4000 (b = 32) leaf pairs exactly; a C leaf with more is
  * cut into equal pieces whose sums are added in FP64 in piece order (still
  * reproducible; scratch of one leaf per piece).  The bound returned is
@@ -380,8 +385,16 @@ typedef enum {
                                  (default 2e9; 0 makes every wait expire:
                                  a test hook for the timeout path)         */
   CHT_OPT_CTAS_PER_SM = 2,    /* persistent grid = SMs * this (0 = auto)   */
-  CHT_OPT_FP64_ENGINE = 3     /* 0 = DMMA (mma.sync f64), 1 = DFMA (default:
-                                 the faster of the two on GB300)           */
+  CHT_OPT_FP64_ENGINE = 3,    /* 0 = DMMA (mma.sync f64); 1 = DFMA (default:
+                                 faster than DMMA on GB300; 256-thread CTAs
+                                 with 4 x 4 register tiles at b = 64, 128
+                                 threads at b = 32); 2 = DFMA with 128-thread
+                                 CTAs (4 x 8 tiles) at b = 64 as well      */
+  CHT_OPT_SPLIT_SINGLE = 4    /* split form, 32-leaves: 1 (default) = C
+                                 leaves with one leaf pair go to the kernel
+                                 that groups them by B leaf (see
+                                 cht_multiply); 0 = every C leaf to the
+                                 general kernel                            */
 } cht_option;
 int cht_set_option(int option, int64_t value);
 int cht_get_option(int option, int64_t *value);

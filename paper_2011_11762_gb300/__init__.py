@@ -21,6 +21,7 @@ OPT_SCHEDULE = 0
 OPT_WAIT_BUDGET_NS = 1
 OPT_CTAS_PER_SM = 2
 OPT_FP64_ENGINE = 3
+OPT_SPLIT_SINGLE = 4
 
 CHT_OK = 0
 CHT_ERR_INVALID = -1

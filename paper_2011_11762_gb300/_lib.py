@@ -61,8 +61,13 @@ SIGNATURES = {
 _lib = None
 
 
+def checked() -> bool:
+    """CHT_BOUNDS_CHECK=1 selects the bounds-checked debug build."""
+    return os.environ.get("CHT_BOUNDS_CHECK", "0") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked() else _build.LIB
 
 
 def load(build_if_needed: bool = True):
@@ -72,11 +77,12 @@ def load(build_if_needed: bool = True):
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_needed and _build.stale():
-        _build.build()
-    if not os.path.exists(_build.LIB):
-        raise ImportError(f"libcht is not built ({_build.LIB}); run build()")
-    lib = ctypes.CDLL(_build.LIB)
+    path = lib_path()
+    if build_if_needed and _build.stale(checked()):
+        _build.build(checked=checked())
+    if not os.path.exists(path):
+        raise ImportError(f"libcht is not built ({path}); run build()")
+    lib = ctypes.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.restype = res

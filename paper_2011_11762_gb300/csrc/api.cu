@@ -497,6 +497,10 @@ int cht_multiply(cht_plan_t plan, cht_mat_t A, cht_mat_t B, int mode, int32_t ns
     w.order = plan->order.p;
     w.nunits = plan->C->nnz;
     w.b = plan->b;
+    w.nx = A->pat->nnz;
+    w.ny = B->pat->nnz;
+    w.nz = plan->C->nnz;
+    w.npairs = plan->npairs;
     rc = launch_leafgemm_f64(w, s);
     // every output is a dot product of length at most n, computed in FP64:
     // |fl(C) - C| <= gamma_n |A| |B| with gamma_n = n u / (1 - n u)
@@ -538,6 +542,10 @@ int cht_multiply_to_host(cht_plan_t plan, cht_mat_t A, cht_mat_t B, void *stream
   w.seg = plan->cseg.p;
   w.nunits = nC;
   w.b = plan->b;
+  w.nx = A->pat->nnz;
+  w.ny = B->pat->nnz;
+  w.nz = nC;
+  w.npairs = plan->npairs;
   return multiply_f64_to_host(w, nchunks, h_C, s);
 }
 
@@ -586,6 +594,10 @@ int cht_multiply_backward(cht_plan_t plan, cht_mat_t A, cht_mat_t B, cht_mat_t d
     w.nunits = pa.nnz;
     w.b = pa.b;
     w.trans_y = 1;
+    w.nx = dC->pat->nnz;
+    w.ny = pb.nnz;
+    w.nz = pa.nnz;
+    w.npairs = lists->npairs;
     rc = launch_leafgemm_f64(w, s);
   }
   if (rc == CHT_OK && mb) {
@@ -600,6 +612,10 @@ int cht_multiply_backward(cht_plan_t plan, cht_mat_t A, cht_mat_t B, cht_mat_t d
     w.nunits = pb.nnz;
     w.b = pb.b;
     w.trans_x = 1;
+    w.nx = pa.nnz;
+    w.ny = dC->pat->nnz;
+    w.nz = pb.nnz;
+    w.npairs = lists->npairs;
     rc = launch_leafgemm_f64(w, s);
   }
   if (rc != CHT_OK) {
@@ -661,8 +677,12 @@ int cht_set_option(int option, int64_t value) {
       g_opt.ctas_per_sm = static_cast<int>(value);
       return CHT_OK;
     case CHT_OPT_FP64_ENGINE:
-      if (value != 0 && value != 1) break;
+      if (value < 0 || value > 2) break;
       g_opt.fp64_engine = static_cast<int>(value);
+      return CHT_OK;
+    case CHT_OPT_SPLIT_SINGLE:
+      if (value != 0 && value != 1) break;
+      g_opt.split_single = static_cast<int>(value);
       return CHT_OK;
     default:
       break;
@@ -678,6 +698,7 @@ int cht_get_option(int option, int64_t *value) {
     case CHT_OPT_WAIT_BUDGET_NS: *value = g_opt.wait_budget_ns; return CHT_OK;
     case CHT_OPT_CTAS_PER_SM: *value = g_opt.ctas_per_sm; return CHT_OK;
     case CHT_OPT_FP64_ENGINE: *value = g_opt.fp64_engine; return CHT_OK;
+    case CHT_OPT_SPLIT_SINGLE: *value = g_opt.split_single; return CHT_OK;
     default: break;
   }
   set_error("invalid option %d", option);
@@ -693,6 +714,12 @@ int cht_sync_status(void *stream) {
   CHT_CUDA_TRY(cudaMemcpy(&h, dptr, sizeof(int), cudaMemcpyDeviceToHost));
   if (h != 0) {
     CHT_CUDA_TRY(cudaMemset(dptr, 0, sizeof(int)));
+    if (h & DEV_STATUS_BAD_INDEX) {
+      // (the bounds-checked build; other roles of the kernel then give up
+      // through its abort path, which also records a timeout)
+      set_error("a kernel met a leaf, pair or unit index outside its array");
+      return CHT_ERR_INVALID;
+    }
     if (h & DEV_STATUS_TIMEOUT) {
       set_error("a device-side wait ran out of its time budget");
       return CHT_ERR_TIMEOUT;

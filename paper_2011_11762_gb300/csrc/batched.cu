@@ -90,6 +90,10 @@ int batch_create(int32_t count, const cht_plan_t *plans, const cht_mat_t *As, co
     d.py = p->pb.p;
     d.seg = p->cseg.p;
     d.b = p->b;
+    d.nx = bt->As[i]->pat->nnz;
+    d.ny = bt->Bs[i]->pat->nnz;
+    d.nz = p->C->nnz;
+    d.npairs = p->npairs;
     auto v = std::make_unique<cht_mat>();
     v->pat = p->C;
     v->plan_id = p->id;
@@ -141,7 +145,8 @@ int batch_create(int32_t count, const cht_plan_t *plans, const cht_mat_t *As, co
 
 int batch_run(cht_batch *b, cudaStream_t s) {
   if (b->mode == CHT_SPLIT_BF16) return split_batch_run(b, s);
-  return launch_leafgemm_f64_batch(b->prods.p, b->units.p, b->nunits, b->maxb, b->counter.p, s);
+  return launch_leafgemm_f64_batch(b->prods.p, b->count, b->units.p, b->nunits, b->maxb,
+                                   b->counter.p, s);
 }
 
 int batch_output(cht_batch *b, int32_t i, cht_mat **C) {

@@ -40,11 +40,25 @@ struct Options {
   int64_t wait_budget_ns = 2000000000LL;
   int ctas_per_sm = 0;            // 0 = auto
   int fp64_engine = 1;            // 0 DMMA, 1 DFMA (measured faster on GB300)
+  int split_single = 1;           // 32-leaf split form: one-pair C leaves grouped by B leaf
 };
 extern Options g_opt;
 
 // Device status word (one per device, zero = OK); kernels OR flags into it.
 enum : int { DEV_STATUS_TIMEOUT = 1, DEV_STATUS_BAD_INDEX = 2 };
+
+// Bounds-checked debug build (compiled with -DCHT_BOUNDS_CHECK): the kernels
+// test every leaf, pair and unit index they follow against the length of the
+// array it indexes before they use it; a failed test records
+// DEV_STATUS_BAD_INDEX and the access is skipped (the FP64 kernels skip the
+// pair or unit, the split kernels stop through their abort path).  In the
+// normal build CHT_INDEX_OK is the constant true and the tests vanish.
+#ifdef CHT_BOUNDS_CHECK
+#define CHT_INDEX_OK(cond, status) \
+  ((cond) || (atomicOr((status), static_cast<int>(::cht::DEV_STATUS_BAD_INDEX)), false))
+#else
+#define CHT_INDEX_OK(cond, status) true
+#endif
 int device_status_ptr(int **ptr);
 int num_sms(int *sms);
 
@@ -162,6 +176,8 @@ struct GemmWork {
   int64_t nunits;
   int32_t b;
   int trans_x, trans_y;   // use X^T / Y^T in the product
+  // lengths (read by the bounds-checked build): leaves of X, Y and Z, pairs
+  int64_t nx, ny, nz, npairs;
 };
 // Z[o] = sum_p op(X[px[p]]) op(Y[py[p]]) for every unit; FP64.
 int launch_leafgemm_f64(const GemmWork &w, cudaStream_t s);
@@ -179,12 +195,14 @@ struct ProdDesc {
   const int64_t *seg;
   int32_t b;
   int32_t pad;
+  int64_t nx, ny, nz, npairs;  // lengths, as in GemmWork
 };
 // Batched FP64 multiply: units (product << 32 | output leaf) in one launch;
 // maxb = the largest leaf size among the products (32 or 64).
 // d_counter: 8 bytes of device scratch, zeroed by the call.
-int launch_leafgemm_f64_batch(const ProdDesc *d_prods, const int64_t *d_units, int64_t nunits,
-                              int maxb, unsigned long long *d_counter, cudaStream_t s);
+int launch_leafgemm_f64_batch(const ProdDesc *d_prods, int32_t nprods, const int64_t *d_units,
+                              int64_t nunits, int maxb, unsigned long long *d_counter,
+                              cudaStream_t s);
 
 int launch_fp64_peak(int engine, cudaStream_t s, double *tflops);
 int launch_fp64_peak_cfg(int engine, int chains, int threads, int per_sm, cudaStream_t s,
@@ -223,6 +241,9 @@ struct cht_plan {
   cht::DevArray<int32_t> dA_c, dA_b;      // pairs grouped by A leaf
   cht::DevArray<int32_t> dB_a, dB_c;      // pairs grouped by B leaf
   cht::DevArray<int32_t> idA, idB;        // identity schedules
+  // the split form's grouping of one-pair C leaves (32-leaves), built on
+  // first use; owned here, defined in split.cu
+  std::shared_ptr<void> split_groups;
 };
 
 namespace cht {

@@ -28,6 +28,15 @@ namespace cht {
 namespace {
 
 constexpr int kThreads = 128;  // 4 warps, a 2 x 2 grid of warp tiles
+
+// Arithmetic engines: 0 = DMMA (128 threads), 1 = DFMA with a 4 x 8 (b = 64)
+// or 2 x 4 (b = 32) register tile per thread (128 threads), 2 = DFMA with a
+// 4 x 4 tile per thread (256 threads, b = 64).  GB300 issues about two FP64
+// FMAs per clock per SM; with one 128-thread CTA per SM (the 64-leaf ring
+// fills shared memory) each scheduler has one warp and its shared-memory
+// loads and barriers leave the FP64 pipe idle about 5% of the time; two
+// warps per scheduler hide them.
+__host__ __device__ constexpr int threads_of(int engine) { return engine == 2 ? 256 : 128; }
 constexpr int64_t kDrainBudgetNs = 2000000000LL;
 
 template <int B>
@@ -129,6 +138,43 @@ struct Tile<B, TX, TY, 1> {
   }
 };
 
+// DFMA, 256 threads: thread tile RM x RN; 16 row groups x 16 column groups.
+template <int B, bool TX, bool TY>
+struct Tile<B, TX, TY, 2> {
+  static constexpr int RM = B / 16, RN = B / 16;
+  double acc[RM][RN];
+  __device__ void zero() {
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; ++j) acc[i][j] = 0.0;
+  }
+  __device__ void mac(const double *xs, const double *ys) {
+    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll 4
+    for (int k = 0; k < B; ++k) {
+      double a[RM], b[RN];
+#pragma unroll
+      for (int i = 0; i < RM; ++i) a[i] = ldx<B, TX>(xs, tr * RM + i, k);
+#pragma unroll
+      for (int j = 0; j < RN; ++j) b[j] = ldy<B, TY>(ys, k, tc * RN + j);
+#pragma unroll
+      for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+  }
+  __device__ void store(double *z) const {
+    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; j += 2)
+        *reinterpret_cast<double2 *>(z + (tr * RM + i) * B + tc * RN + j) =
+            make_double2(acc[i][j], acc[i][j + 1]);
+  }
+};
+
 // One output leaf: Z = sum over the pair segment [p0, p0 + np) of
 // op(X[px[p]]) op(Y[py[p]]), with a ring of S shared-memory stages (stage
 // pitch `pitch` doubles).  `it` counts the pairs this CTA consumed so far
@@ -139,17 +185,22 @@ __device__ bool run_unit(const double *__restrict__ X, const double *__restrict_
                          double *__restrict__ Z, const int32_t *__restrict__ px,
                          const int32_t *__restrict__ py, int64_t p0, int64_t np, double *sx,
                          double *sy, int pitch, uint64_t *full, uint32_t &it, int64_t wait_ns,
-                         int *status) {
+                         int *status, int64_t nx, int64_t ny) {
   constexpr int LEAF = B * B;
   constexpr uint32_t kBytes = LEAF * sizeof(double);
   const int tid = threadIdx.x;
   auto issue = [&](int64_t p, uint32_t st) {
-    const double *xsrc = X + static_cast<int64_t>(px[p]) * LEAF;
-    const double *ysrc = Y + static_cast<int64_t>(py[p]) * LEAF;
-    mbar_arrive_expect_tx(&full[st], 2 * kBytes);
-    bulk_g2s(sx + st * pitch, xsrc, kBytes, &full[st]);
-    bulk_g2s(sy + st * pitch, ysrc, kBytes, &full[st]);
+    const int64_t ix = px[p], iy = py[p];
+    if (CHT_INDEX_OK(ix >= 0 && ix < nx && iy >= 0 && iy < ny, status)) {
+      mbar_arrive_expect_tx(&full[st], 2 * kBytes);
+      bulk_g2s(sx + st * pitch, X + ix * LEAF, kBytes, &full[st]);
+      bulk_g2s(sy + st * pitch, Y + iy * LEAF, kBytes, &full[st]);
+    } else {
+      mbar_arrive(&full[st]);  // the stage's phase completes without data
+    }
   };
+  (void)nx;
+  (void)ny;
   Tile<B, TX, TY, ENGINE> tile;
   tile.zero();
   if (tid == 0)
@@ -178,7 +229,7 @@ __device__ bool run_unit(const double *__restrict__ X, const double *__restrict_
 }
 
 template <int B, bool TX, bool TY, int ENGINE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(threads_of(ENGINE))
     k_leafgemm_f64(const GemmWork w, int *__restrict__ status, int64_t wait_ns,
                    unsigned long long *__restrict__ next_unit) {
   using Cfg = LeafCfg<B>;
@@ -204,9 +255,11 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     if (u >= w.nunits) break;
     const int64_t o = w.order[u];
+    if (!CHT_INDEX_OK(o >= 0 && o < w.nz, status)) continue;
     const int64_t p0 = w.seg[o], np = w.seg[o + 1] - p0;
+    if (!CHT_INDEX_OK(p0 >= 0 && np >= 0 && p0 + np <= w.npairs, status)) continue;
     if (!run_unit<B, TX, TY, ENGINE, S>(w.X, w.Y, w.Z + o * LEAF, w.px, w.py, p0, np, sx, sy,
-                                        LEAF, full, it, wait_ns, status))
+                                        LEAF, full, it, wait_ns, status, w.nx, w.ny))
       return;
   }
 }
@@ -216,10 +269,12 @@ __global__ void __launch_bounds__(kThreads)
 // MAXB is the largest leaf size of the batch: the stage ring is sized for it
 // (a batch of 32-leaf products gets the 32-leaf kernel's ring and occupancy).
 template <int ENGINE, int MAXB>
-__global__ void __launch_bounds__(kThreads)
-    k_leafgemm_f64_batch(const ProdDesc *__restrict__ prods, const int64_t *__restrict__ units,
-                         int64_t nunits, int *__restrict__ status, int64_t wait_ns,
+__global__ void __launch_bounds__(threads_of(ENGINE))
+    k_leafgemm_f64_batch(const ProdDesc *__restrict__ prods, int32_t nprods,
+                         const int64_t *__restrict__ units, int64_t nunits,
+                         int *__restrict__ status, int64_t wait_ns,
                          unsigned long long *__restrict__ next_unit) {
+  (void)nprods;
   constexpr int S = LeafCfg<MAXB>::kStages, PITCH = MAXB * MAXB;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double *sx = reinterpret_cast<double *>(smem_raw);
@@ -240,21 +295,24 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     if (u >= nunits) break;
     const int64_t packed = units[u];
+    if (!CHT_INDEX_OK((packed >> 32) >= 0 && (packed >> 32) < nprods, status)) continue;
     const ProdDesc d = prods[packed >> 32];
     const int64_t o = packed & 0xffffffffLL;
+    if (!CHT_INDEX_OK(o < d.nz, status)) continue;
     const int64_t p0 = d.seg[o], np = d.seg[o + 1] - p0;
+    if (!CHT_INDEX_OK(p0 >= 0 && np >= 0 && p0 + np <= d.npairs, status)) continue;
     bool ok = false;
     if constexpr (MAXB == 64) {
       if (d.b == 64)
         ok = run_unit<64, false, false, ENGINE, S>(d.X, d.Y, d.Z + o * 4096, d.px, d.py, p0, np,
-                                                   sx, sy, PITCH, full, it, wait_ns, status);
+                                                   sx, sy, PITCH, full, it, wait_ns, status, d.nx, d.ny);
       else
         ok = run_unit<32, false, false, ENGINE, S>(d.X, d.Y, d.Z + o * 1024, d.px, d.py, p0, np,
-                                                   sx, sy, PITCH, full, it, wait_ns, status);
+                                                   sx, sy, PITCH, full, it, wait_ns, status, d.nx, d.ny);
     } else {
       // every product of this batch has 32-leaves
       ok = run_unit<32, false, false, ENGINE, S>(d.X, d.Y, d.Z + o * 1024, d.px, d.py, p0, np, sx,
-                                                 sy, PITCH, full, it, wait_ns, status);
+                                                 sy, PITCH, full, it, wait_ns, status, d.nx, d.ny);
     }
     if (!ok) return;
   }
@@ -268,16 +326,17 @@ int launch_t(const GemmWork &w, cudaStream_t s, int *status, unsigned long long 
                                     static_cast<int>(Cfg::kSmem)));
   int sms = 0;
   CHT_TRY(num_sms(&sms));
+  constexpr int NT = threads_of(ENGINE);
   int per_sm = g_opt.ctas_per_sm;
   if (per_sm <= 0) {
     int occ = 0;
-    CHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, Cfg::kSmem));
+    CHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, Cfg::kSmem));
     per_sm = std::max(1, occ);
   }
   int64_t grid = std::min<int64_t>(w.nunits, static_cast<int64_t>(sms) * per_sm);
   if (grid < 1) grid = 1;
-  kern<<<static_cast<unsigned>(grid), kThreads, Cfg::kSmem, s>>>(w, status, g_opt.wait_budget_ns,
-                                                                 counter);
+  kern<<<static_cast<unsigned>(grid), NT, Cfg::kSmem, s>>>(w, status, g_opt.wait_budget_ns,
+                                                           counter);
   return launched("leafgemm_f64");
 }
 
@@ -338,9 +397,9 @@ __global__ void k_peak_tile(double *out, int iters, double y, double x0) {
 // The leaf GEMM's own inner loop (Tile<B, ..., DFMA>::mac) over one pair of
 // B x B leaves held in shared memory, `iters` times: the FP64 kernel's
 // arithmetic and shared-memory loads without its copies and unit hand-offs.
-template <int B>
-__global__ void __launch_bounds__(kThreads) k_peak_leaf(double *out, int iters, double y,
-                                                        double x0) {
+template <int B, int ENG>
+__global__ void __launch_bounds__(threads_of(ENG)) k_peak_leaf(double *out, int iters, double y,
+                                                               double x0) {
   extern __shared__ __align__(16) double peak_smem[];
   double *sx = peak_smem, *sy = peak_smem + B * B;
   for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
@@ -348,14 +407,14 @@ __global__ void __launch_bounds__(kThreads) k_peak_leaf(double *out, int iters, 
     sy[e] = x0 * (1.0 - 1e-6 * e);
   }
   __syncthreads();
-  Tile<B, false, false, 1> tile;
+  Tile<B, false, false, ENG> tile;
   tile.zero();
   for (int n = 0; n < iters; ++n) tile.mac(sx, sy);
   double s = 0;
 #pragma unroll
-  for (int i = 0; i < Tile<B, false, false, 1>::RM; ++i)
+  for (int i = 0; i < Tile<B, false, false, ENG>::RM; ++i)
 #pragma unroll
-    for (int j = 0; j < Tile<B, false, false, 1>::RN; ++j) s += tile.acc[i][j];
+    for (int j = 0; j < Tile<B, false, false, ENG>::RN; ++j) s += tile.acc[i][j];
   if (s == 12345.0) out[0] = s;
 }
 
@@ -385,7 +444,9 @@ int launch_leafgemm_f64(const GemmWork &w, cudaStream_t s) {
   CHT_CUDA_TRY(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), s));
   const int engine = g_opt.fp64_engine;
   if (w.b == 64)
-    return engine ? launch_b<64, 1>(w, s, status, counter.p) : launch_b<64, 0>(w, s, status, counter.p);
+    return engine == 1   ? launch_b<64, 2>(w, s, status, counter.p)
+           : engine == 2 ? launch_b<64, 1>(w, s, status, counter.p)
+                         : launch_b<64, 0>(w, s, status, counter.p);
   if (w.b == 32)
     return engine ? launch_b<32, 1>(w, s, status, counter.p) : launch_b<32, 0>(w, s, status, counter.p);
   set_error("leaf size %d: the numeric kernels take b = 32 or b = 64", w.b);
@@ -467,25 +528,32 @@ int multiply_f64_to_host(const GemmWork &w0, int64_t nchunks, double *h_out, cud
   return rc;
 }
 
-int launch_leafgemm_f64_batch(const ProdDesc *d_prods, const int64_t *d_units, int64_t nunits,
-                              int maxb, unsigned long long *d_counter, cudaStream_t s) {
+int launch_leafgemm_f64_batch(const ProdDesc *d_prods, int32_t nprods, const int64_t *d_units,
+                              int64_t nunits, int maxb, unsigned long long *d_counter,
+                              cudaStream_t s) {
   if (nunits <= 0) return CHT_OK;
   int *status = nullptr;
   CHT_TRY(device_status_ptr(&status));
   int sms = 0;
   CHT_TRY(num_sms(&sms));
   const size_t smem = maxb == 64 ? LeafCfg<64>::kSmem : LeafCfg<32>::kSmem;
+  // engines as for single products: 64-leaf batches take the 256-thread DFMA
+  // tile unless the 128-thread one is asked for
+  const int engine = g_opt.fp64_engine == 0 ? 0 : (maxb == 64 && g_opt.fp64_engine == 1) ? 2 : 1;
   auto kern = maxb == 64
-                  ? (g_opt.fp64_engine ? k_leafgemm_f64_batch<1, 64> : k_leafgemm_f64_batch<0, 64>)
-                  : (g_opt.fp64_engine ? k_leafgemm_f64_batch<1, 32> : k_leafgemm_f64_batch<0, 32>);
+                  ? (engine == 2 ? k_leafgemm_f64_batch<2, 64>
+                     : engine == 1 ? k_leafgemm_f64_batch<1, 64> : k_leafgemm_f64_batch<0, 64>)
+                  : (engine ? k_leafgemm_f64_batch<1, 32> : k_leafgemm_f64_batch<0, 32>);
+  const int NT = threads_of(engine);
   CHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem)));
   int occ = 0;
-  CHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
+  CHT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
   const int64_t grid = std::min<int64_t>(nunits, static_cast<int64_t>(sms) * std::max(1, occ));
   CHT_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s));
-  kern<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(d_prods, d_units, nunits, status,
-                                                          g_opt.wait_budget_ns, d_counter);
+  kern<<<static_cast<unsigned>(grid), NT, smem, s>>>(d_prods, nprods, d_units, nunits,
+                                                          status, g_opt.wait_budget_ns,
+                                                          d_counter);
   return launched("leafgemm_f64_batch");
 }
 
@@ -500,10 +568,11 @@ int launch_fp64_peak_cfg(int engine, int chains, int threads, int per_sm, cudaSt
                                      : (chains == 4 || chains == 8 || chains == 16 ||
                                         chains == 32 || engine == 2);
   if (engine < 0 || engine > 3 || threads < 32 || threads > 1024 || threads % 32 != 0 ||
-      per_sm < 1 || per_sm > 32 || !chains_ok || (engine == 3 && threads != kThreads)) {
+      per_sm < 1 || per_sm > 32 || !chains_ok ||
+      (engine == 3 && threads != 128 && !(threads == 256 && chains == 64))) {
     set_error("FP64 peak: engine 0..3, chains 4/8/16/32 (engine 3: the leaf size, 32 or 64, "
-              "with %d threads), threads a multiple of 32 in [32, 1024], 1..32 CTAs per SM",
-              kThreads);
+              "with 128 threads, or 64 with 256), threads a multiple of 32 in [32, 1024], "
+              "1..32 CTAs per SM");
     return CHT_ERR_INVALID;
   }
   const void *fn = nullptr;
@@ -517,7 +586,9 @@ int launch_fp64_peak_cfg(int engine, int chains, int threads, int per_sm, cudaSt
            : chains == 16 ? (const void *)k_peak_dfma<16> : (const void *)k_peak_dfma<32>;
       break;
     case 2: fn = (const void *)k_peak_tile; break;
-    default: fn = chains == 64 ? (const void *)k_peak_leaf<64> : (const void *)k_peak_leaf<32>;
+    default:
+      fn = chains == 32 ? (const void *)k_peak_leaf<32, 1>
+           : threads == 256 ? (const void *)k_peak_leaf<64, 2> : (const void *)k_peak_leaf<64, 1>;
   }
   cudaFuncAttributes fa;
   CHT_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
@@ -533,7 +604,7 @@ int launch_fp64_peak_cfg(int engine, int chains, int threads, int per_sm, cudaSt
   // FLOPs per iteration per thread (a DMMA's 2 * 8 * 8 * 4 shared by 32 lanes;
   // one leaf product, 2 b^3, shared by the kThreads threads)
   const double per_iter = engine == 0   ? ch * 2.0 * 8 * 8 * 4 / 32.0
-                          : engine == 3 ? 2.0 * ch * ch * ch / kThreads
+                          : engine == 3 ? 2.0 * ch * ch * ch / threads
                                         : ch * 2.0;
   const double target = 4.8e10;  // ~40 ms at 1.2 TFLOP/s
   int64_t iters = static_cast<int64_t>(target / (static_cast<double>(grid) * threads * per_iter));
@@ -556,10 +627,12 @@ int launch_fp64_peak_cfg(int engine, int chains, int threads, int per_sm, cudaSt
         rc = cuda_fail(e, "fp64 peak smem attribute");
         break;
       }
-      if (ch == 64)
-        k_peak_leaf<64><<<grid, threads, smem, s>>>(out.p, it, y, x0);
+      if (ch == 32)
+        k_peak_leaf<32, 1><<<grid, threads, smem, s>>>(out.p, it, y, x0);
+      else if (threads == 256)
+        k_peak_leaf<64, 2><<<grid, threads, smem, s>>>(out.p, it, y, x0);
       else
-        k_peak_leaf<32><<<grid, threads, smem, s>>>(out.p, it, y, x0);
+        k_peak_leaf<64, 1><<<grid, threads, smem, s>>>(out.p, it, y, x0);
     } else if (engine == 2) {
       k_peak_tile<<<grid, threads, 0, s>>>(out.p, it, y, x0);
     } else if (engine == 1) {
@@ -604,7 +677,7 @@ int launch_fp64_peak(int engine, cudaStream_t s, double *tflops) {
     for (int occ : occ_set) {
       double t = 0.0;
       const int ch = engine == 3 ? leaf_set[i] : chain_set[i];
-      CHT_TRY(launch_fp64_peak_cfg(engine, ch, engine == 3 ? kThreads : 256, occ, s, &t));
+      CHT_TRY(launch_fp64_peak_cfg(engine, ch, engine == 3 ? 128 : 256, occ, s, &t));
       best = std::max(best, t);
     }
   *tflops = best;
@@ -695,9 +768,15 @@ extern "C" int cht_multiply_f64_noalloc(cht_plan_t plan, cht_mat_t A, cht_mat_t 
   w.order = plan->order.p;
   w.nunits = plan->C->nnz;
   w.b = plan->b;
+  w.nx = A->pat->nnz;
+  w.ny = B->pat->nnz;
+  w.nz = plan->C->nnz;
+  w.npairs = plan->npairs;
   const int engine = g_opt.fp64_engine;
   if (w.b == 64)
-    return engine ? launch_b<64, 1>(w, s, status, counter) : launch_b<64, 0>(w, s, status, counter);
+    return engine == 1   ? launch_b<64, 2>(w, s, status, counter)
+           : engine == 2 ? launch_b<64, 1>(w, s, status, counter)
+                         : launch_b<64, 0>(w, s, status, counter);
   return engine ? launch_b<32, 1>(w, s, status, counter) : launch_b<32, 0>(w, s, status, counter);
 }
 

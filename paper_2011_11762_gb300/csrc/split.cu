@@ -94,7 +94,9 @@ struct Blocks<32> {
 
 template <int B>
 struct Smem {
-  static constexpr int TILE = B * 128;  // one slice: B rows x 64 bf16 (SW128 K-major)
+  // one slice: B rows of B bf16 values (K-major): 128-byte rows with the
+  // 128-byte swizzle at b = 64, 64-byte rows with the 64-byte swizzle at b = 32
+  static constexpr int TILE = B * B * 2;
   static constexpr int A_BYTES = Cfg<B>::SA * TILE;
   static constexpr int B_BYTES = kSB * TILE;
   static constexpr int STAGE = A_BYTES + B_BYTES;
@@ -205,6 +207,21 @@ __device__ inline uint64_t sw128_desc(uint32_t saddr) {
   d |= static_cast<uint64_t>(2) << 61;                 // 128-byte swizzle
   return d;
 }
+// The same for the 64-byte swizzle layout (rows of 64 bytes, 8-row groups
+// 512 bytes apart): the tiles of 32-leaves, whose rows hold 32 bf16 values.
+__device__ inline uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3ffff) >> 4);  // start address
+  d |= static_cast<uint64_t>(1) << 16;                 // leading offset (unused here)
+  d |= static_cast<uint64_t>(512 >> 4) << 32;          // stride: 8-row group pitch
+  d |= static_cast<uint64_t>(1) << 46;                 // descriptor version
+  d |= static_cast<uint64_t>(4) << 61;                 // 64-byte swizzle
+  return d;
+}
+template <int B>
+__device__ inline uint64_t tile_desc(uint32_t saddr) {
+  return B == 64 ? sw128_desc(saddr) : sw64_desc(saddr);
+}
 
 // Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major.
 __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
@@ -305,6 +322,16 @@ __device__ inline uint32_t pack_bf16x2(int lo, int hi) {
 __host__ __device__ inline int sw128_offset(int r, int c) {
   return (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
 }
+// The same in a 64-byte-swizzled tile (c < 4): the swizzle XORs the chunk
+// index with bits 7 and 8 of the row's byte offset, i.e. with (r >> 1) & 3.
+__host__ __device__ inline int sw64_offset(int r, int c) {
+  return (r >> 3) * 512 + (r & 7) * 64 + ((c ^ ((r >> 1) & 3)) << 4);
+}
+// Byte offset of 16-byte chunk c of row r in a slice tile of a b-leaf.
+template <int B>
+__host__ __device__ inline int tile_offset(int r, int c) {
+  return B == 64 ? sw128_offset(r, c) : sw64_offset(r, c);
+}
 
 // v * 2^e2 rounded to nearest-even with 64-bit integer operations, |v| < 2^63.
 // Outside the normal range of doubles (never for finite inputs of moderate
@@ -385,13 +412,14 @@ __global__ void k_col_exp(const double *__restrict__ vals, const int32_t *__rest
 }
 
 // A slices: thread per (leaf, row r, chunk c of 8 K values).  Leaf layout in
-// global memory = the shared-memory image: [SA][B rows][128 bytes], swizzled.
+// global memory = the shared-memory image: [SA][B rows][2 B bytes], swizzled
+// (128-byte swizzle at b = 64, 64-byte swizzle at b = 32).
 template <int B, int SA>
 __global__ void k_split_a(const double *__restrict__ vals, const int32_t *__restrict__ brow,
                           int64_t nleaves, const int *__restrict__ row_exp,
                           uint8_t *__restrict__ out) {
   constexpr int CH = B / 8;  // logical chunks per row holding data
-  constexpr int TILE = B * 128;
+  constexpr int TILE = Smem<B>::TILE;
   const int64_t total = nleaves * B * CH;
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
        t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -417,7 +445,7 @@ __global__ void k_split_a(const double *__restrict__ vals, const int32_t *__rest
 #pragma unroll
       for (int i = 0; i < SA; ++i) d[i][k] = dk[i];
     }
-    uint8_t *base = out + leaf * SA * TILE + sw128_offset(r, c);
+    uint8_t *base = out + leaf * SA * TILE + tile_offset<B>(r, c);
 #pragma unroll
     for (int i = 0; i < SA; ++i) {
       uint4 v;
@@ -440,7 +468,7 @@ __global__ void k_split_a(const double *__restrict__ vals, const int32_t *__rest
 template <int B>
 struct SplitBSmem {
   static constexpr int IN = B * (B + 1) * 8;  // the staged leaf (padded rows)
-  static constexpr int OUT = kSB * B * 128;   // the slice tiles of one leaf
+  static constexpr int OUT = kSB * Smem<B>::TILE;  // the slice tiles of one leaf
   static constexpr int TOTAL = IN + OUT;
   static_assert(IN % 16 == 0 && OUT % 16 == 0, "16-byte aligned parts");
 };
@@ -451,7 +479,7 @@ __global__ void __launch_bounds__(256) k_split_b(const double *__restrict__ vals
                                                  int64_t nleaves, const int *__restrict__ col_exp,
                                                  uint8_t *__restrict__ out) {
   constexpr int CH = B / 8;
-  constexpr int TILE = B * 128;
+  constexpr int TILE = Smem<B>::TILE;
   constexpr int OUT = SplitBSmem<B>::OUT;
   extern __shared__ __align__(16) uint8_t smem_b[];
   double(*tile)[B + 1] = reinterpret_cast<double(*)[B + 1]>(smem_b);
@@ -480,7 +508,7 @@ __global__ void __launch_bounds__(256) k_split_b(const double *__restrict__ vals
 #pragma unroll
         for (int j = 0; j < kSB; ++j) g[j][k] = gk[j];
       }
-      uint8_t *base = img + sw128_offset(n, c);
+      uint8_t *base = img + tile_offset<B>(n, c);
 #pragma unroll
       for (int j = 0; j < kSB; ++j) {
         uint4 v;
@@ -516,6 +544,9 @@ struct SplitProd {
   double *const *cptr;      // per unit: output leaf (null: C + unit * b * b)
   int32_t b;
   int32_t pad;
+  // lengths (read by the bounds-checked build): A and B leaves, units (the
+  // entries of cseg less one), pairs, leaves per side
+  int64_t nA, nB, nunits, npairs, G;
 };
 
 // Kernel-wide sizes for the largest leaf size a launch serves.
@@ -529,7 +560,9 @@ struct KCfg<64> {
 };
 template <>
 struct KCfg<32> {
-  static constexpr int STAGES = 2, STAGE = Smem<32>::STAGE, XBUF = Smem<32>::XBUF, NXB = 2;
+  // 4 stages of 28 KB (8 A + 6 B tiles of 2 KB): one-pair units need the
+  // copies of several units in flight to hide their latency
+  static constexpr int STAGES = 4, STAGE = Smem<32>::STAGE, XBUF = Smem<32>::XBUF, NXB = 2;
   // two accumulator sets of 256 columns: the MMA of unit n + 1 runs while
   // the epilogue still reads unit n
   static constexpr int TMEM_COLS = 512;
@@ -589,8 +622,8 @@ __device__ __forceinline__ void issue_blocks(uint32_t sa, uint32_t sb, uint32_t 
     const int bu = Blocks<B>::u(bi), bj = Blocks<B>::j(bi);
     const int r = (bu + bj - 2) >> 1;  // region 0..2
     if ((which == 1 && r != 2) || (which == 2 && r == 2)) continue;
-    const uint64_t ad = sw128_desc(sa + (bu - 1) * SM::TILE);
-    const uint64_t bd = sw128_desc(sb + (bj - 1) * SM::TILE);  // slices j, j+1
+    const uint64_t ad = tile_desc<B>(sa + (bu - 1) * SM::TILE);
+    const uint64_t bd = tile_desc<B>(sb + (bj - 1) * SM::TILE);  // slices j, j+1
     const uint32_t dt = tmem + static_cast<uint32_t>(r * N);
 #pragma unroll
     for (int kk = 0; kk < CF::KSTEPS; ++kk) {
@@ -826,15 +859,17 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
 
 // The persistent split kernel.  Units come from a device counter in order
 // (neighbouring C leaves, in Morton order within a product, run together and
-// share A and B slices through L2): with `prods` NULL unit u is C leaf u of
-// `single`; otherwise product units[u] >> 32, C leaf units[u] & 0xffffffff.
+// share A and B slices through L2): with `prods` and `units` NULL unit u is C
+// leaf u of `single`; with `units` only, C leaf units[u] of `single`;
+// otherwise product units[u] >> 32, C leaf units[u] & 0xffffffff.
 // `next_unit` (8 bytes, zero at launch) is the unit counter.
 template <int MAXB>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_split_gemm(const SplitProd single, const SplitProd *__restrict__ prods,
+    k_split_gemm(const SplitProd single, const SplitProd *__restrict__ prods, int32_t nprods,
                  const int64_t *__restrict__ units, int64_t nunits,
                  unsigned long long *__restrict__ next_unit, int *__restrict__ status,
                  int64_t wait_ns) {
+  (void)nprods;
   using KC = KCfg<MAXB>;
   constexpr int S = KC::STAGES;
   constexpr int NB = MAXB == 32 ? 2 : 1;  // TMEM accumulator sets
@@ -908,7 +943,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) u0 = atomicAdd(next_unit, static_cast<unsigned long long>(kChunk));
       u0 = __shfl_sync(0xffffffffu, u0, 0);
       int valid_l = 0, b_l = 0, crow_l = 0, ccol_l = 0;
-      long long p0_l = 0, p1_l = 0;
+      long long p0_l = 0, p1_l = 0, na_l = 0, nb_l = 0;
       const int *re_l = nullptr, *ce_l = nullptr;
       const int32_t *pa_l = nullptr, *pb_l = nullptr;
       const uint8_t *as_l = nullptr, *bs_l = nullptr;
@@ -917,14 +952,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         const unsigned long long u = u0 + lane;
         if (u < static_cast<unsigned long long>(nunits)) {
           valid_l = 1;
-          const int64_t packed = prods ? units[u] : static_cast<int64_t>(u);
-          const int64_t o = prods ? (packed & 0xffffffffLL) : packed;
-          const SplitProd &dl = prods ? prods[packed >> 32] : single;
+          const int64_t packed = units ? units[u] : static_cast<int64_t>(u);
+          const int64_t o = units ? (packed & 0xffffffffLL) : packed;
+          if (prods && !CHT_INDEX_OK((packed >> 32) >= 0 && (packed >> 32) < nprods, status))
+            valid_l = 0;
+          const SplitProd &dl = prods && valid_l ? prods[packed >> 32] : single;
+          if (valid_l && !CHT_INDEX_OK(o >= 0 && o < dl.nunits, status)) valid_l = 0;
+          if (valid_l) {
           b_l = dl.b;
           p0_l = dl.cseg[o];
           p1_l = dl.cseg[o + 1];
           crow_l = dl.crow[o];
           ccol_l = dl.ccol[o];
+          if (!CHT_INDEX_OK(p0_l >= 0 && p0_l <= p1_l && p1_l <= dl.npairs && crow_l >= 0 &&
+                                crow_l < dl.G && ccol_l >= 0 && ccol_l < dl.G,
+                            status))
+            valid_l = 0;
           re_l = dl.row_exp;
           ce_l = dl.col_exp;
           pa_l = dl.pa;
@@ -932,6 +975,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           as_l = dl.a_slices;
           bs_l = dl.b_slices;
           C_l = dl.cptr ? dl.cptr[o] : dl.C + o * dl.b * dl.b;
+          na_l = dl.nA;
+          nb_l = dl.nB;
+          }
         }
       }
       // exponents (rows lane, lane + 32) and the first 32 pair indices of unit j
@@ -997,6 +1043,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             __shfl_sync(0xffffffffu, reinterpret_cast<long long>(bs_l), j));
         double *Cp = reinterpret_cast<double *>(
             __shfl_sync(0xffffffffu, reinterpret_cast<long long>(C_l), j));
+        const long long na_j = __shfl_sync(0xffffffffu, na_l, j);
+        const long long nb_j = __shfl_sync(0xffffffffu, nb_l, j);
+        (void)na_j;
+        (void)nb_j;
         sl.rexp[lane] = exp16(cur.re0);
         sl.cexp[lane] = exp16(cur.ce0);
         if (b == 64) {
@@ -1029,6 +1079,12 @@ __global__ void __launch_bounds__(kThreads, 1)
               done = true;
               break;
             }
+            if (!CHT_INDEX_OK(pa_i >= 0 && pa_i < na_j && pb_i >= 0 && pb_i < nb_j, status)) {
+              // a bad leaf index: stop through the abort path, no copy issued
+              if (lane == 0) *c.abort_flag = 1;
+              done = true;
+              break;
+            }
             if (lane == 0) {
               mbar_arrive_expect_tx(&c.full[st], static_cast<uint32_t>(a_bytes + b_bytes));
             }
@@ -1037,7 +1093,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // flight instead of two large ones)
             {
               uint8_t *sa = c.stage_base + st * c.stage_bytes;
-              const int tile = b * 128;
+              const int tile = b == 64 ? Smem<64>::TILE : Smem<32>::TILE;
               const int na = a_bytes / tile, nb = b_bytes / tile;
               if (lane < na)
                 bulk_g2s(sa + lane * tile, a_slices + static_cast<int64_t>(pa_i) * a_bytes +
@@ -1143,6 +1199,375 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) tmem_dealloc(c.tmem, KC::TMEM_COLS);
 }
 
+
+// ------------------------------------------------ one-pair C leaves, b = 32 --
+// A C leaf with a single leaf pair is one product A(I, K) B(K, J).  These
+// leaves are grouped by their B leaf: a group holds up to 4 of them,
+// (I_0, J) .. (I_3, J), all with the same B(K, J).  One MMA stacks slice i of
+// the group's 4 A leaves along M = 128 (32 rows each) against B slice j
+// (N = 32), so TMEM lane quarter q holds C leaf q of the group, and all slice
+// diagonals of an element land in the same lane: the epilogue needs no
+// exchange between warps.
+//
+// Slice pairs: exactly those with i + j <= 7 (21 MMAs of K = 32, each two
+// K = 16 instructions).  The pairs of diagonal t = i + j accumulate into TMEM
+// region t - 2 (32 columns).  A region sums at most 6 pairs of 32 digit
+// products of magnitude <= 2^14, below 2^22: exact in FP32.  In units of
+// 2^-56 of 2^(e_r + f_c + 2) the element is the integer
+//     T = sum_{t=2..7} S_t 2^(56 - 8t)     (|T| < 2^62),
+// assembled in int64 by T <- 2^8 T + S_t and converted once.  A uses the
+// 8-digit slices of the 32-leaf path (digits 1..6 here), B its 6 digits.
+//
+// Roles as in k_split_gemm: warp 0 producer (groups taken 8 at a time from a
+// device counter; per group one bulk copy of the B leaf's 6 slice tiles and
+// one per A tile), warp 1 MMA issuer (one thread), warps 2..9 epilogue (two
+// warps per lane quarter, 16 columns each).  Two accumulator sets of 192
+// columns: the MMAs of group n + 1 run while the epilogue reads group n; the
+// epilogue reads the six regions, releases its set, then assembles and
+// stores.  Every wait is bounded.
+namespace single32 {
+constexpr int kStages = 3;
+constexpr int kTile = Smem<32>::TILE;                 // 2 KB
+constexpr int kASlices = 6;                           // A digits used
+constexpr int kA = kASlices * 4 * kTile;              // [slice][unit][tile]: 48 KB
+constexpr int kB = kSB * kTile;                       // 12 KB
+constexpr int kStage = kA + kB;
+constexpr int kRegionsS = 6;                          // diagonals 2..7
+constexpr int kSetCols = 256;                         // accumulator set pitch (192 used)
+constexpr int kChunk = 8;                             // groups per counter step
+constexpr int kNPairs = 21;
+// the pairs (i, j), i + j <= 7, diagonal by diagonal (t = 2, 3, ..., 7)
+__device__ constexpr int pair_t(int x) {
+  return x < 1 ? 2 : x < 3 ? 3 : x < 6 ? 4 : x < 10 ? 5 : x < 15 ? 6 : 7;
+}
+__device__ constexpr int pair_i(int x) {
+  return x - (x < 1 ? 0 : x < 3 ? 1 : x < 6 ? 3 : x < 10 ? 6 : x < 15 ? 10 : 15) + 1;
+}
+}  // namespace single32
+
+struct SingleWork {
+  const uint8_t *a_slices;  // [nA][8][tile]
+  const uint8_t *b_slices;  // [nB][6][tile]
+  const int32_t *gb;        // per group: B leaf
+  const int32_t *ga;        // per group: 4 A leaves
+  const int32_t *gc;        // per group: 4 C leaves (-1: none)
+  const int32_t *crow, *ccol;
+  const int *row_exp, *col_exp;
+  double *C;
+  int64_t ngroups;
+  int64_t nA, nB, nC, G;  // lengths (read by the bounds-checked build)
+};
+
+struct alignas(16) GSlot {
+  double *C[4];     // output leaves (null: no unit in this quarter)
+  const int *row_exp, *col_exp;  // the product's line exponents
+  int32_t crow[4];  // the leaves' rows
+  int32_t ccol;     // the shared leaf column
+  int32_t count;    // units in the group (0: no more groups)
+  int32_t pad[2];
+};
+
+constexpr size_t single32_smem() {
+  return static_cast<size_t>(single32::kStages) * single32::kStage + kQueue * sizeof(GSlot) +
+         256 + 1024;
+}
+
+// Group u is group u of `single` (works NULL), or, in a batch, group
+// gunits[u] & 0xffffffff of product gunits[u] >> 32 (works[product]).
+__global__ void __launch_bounds__(kThreads, 1)
+    k_split_single32(const SingleWork single, const SingleWork *__restrict__ works,
+                     int32_t nworks, const int64_t *__restrict__ gunits, int64_t ntotal,
+                     unsigned long long *__restrict__ next_group, int *__restrict__ status,
+                     int64_t wait_ns) {
+  (void)nworks;
+  using namespace single32;
+  constexpr int S = kStages;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_addr = smem_addr(smem_raw);
+  uint8_t *smem = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
+  uint8_t *stage_base = smem;
+  GSlot *queue = reinterpret_cast<GSlot *>(smem + S * kStage);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(queue + kQueue);
+  uint64_t *full = bars, *empty = bars + S, *qfull = bars + 2 * S, *qempty = qfull + kQueue;
+  uint64_t *acc_full = qempty + kQueue, *acc_empty = acc_full + 2, *drain = acc_full + 4;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < S; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    for (int i = 0; i < kQueue; ++i) {
+      mbar_init(&qfull[i], 1);
+      mbar_init(&qempty[i], 1 + kEpiWarps);
+    }
+    for (int bf = 0; bf < 2; ++bf) {
+      mbar_init(&acc_full[bf], 1);
+      mbar_init(&acc_empty[bf], kEpiWarps);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  auto fail = [&]() {
+    atomicOr(status, DEV_STATUS_TIMEOUT);
+    *abort_flag = 1;
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------- producer --
+    uint32_t n = 0;  // groups staged (queue position and stage count)
+    bool done = false;
+    while (!done) {
+      unsigned long long u0 = 0;
+      if (lane == 0) u0 = atomicAdd(next_group, static_cast<unsigned long long>(kChunk));
+      u0 = __shfl_sync(0xffffffffu, u0, 0);
+      // lane l resolves group u0 + l: its product's descriptor and indices
+      const unsigned long long u = u0 + lane;
+      int gb_l = 0, ccol_l = 0;
+      int ga_l[4] = {0, 0, 0, 0}, gc_l[4] = {-1, -1, -1, -1}, cr_l[4] = {0, 0, 0, 0};
+      bool valid_l = lane < kChunk && u < static_cast<unsigned long long>(ntotal);
+      int64_t g = 0;
+      const SingleWork *wp = &single;
+      if (valid_l && works) {
+        const int64_t packed = gunits[u];
+        if (CHT_INDEX_OK((packed >> 32) >= 0 && (packed >> 32) < nworks, status))
+          wp = &works[packed >> 32];
+        else
+          valid_l = false;
+        g = packed & 0xffffffffLL;
+      } else {
+        g = static_cast<int64_t>(u);
+      }
+      const SingleWork &w = *wp;
+      if (valid_l && !CHT_INDEX_OK(g < w.ngroups, status)) valid_l = false;
+      const uint8_t *as_l = w.a_slices, *bs_l = w.b_slices;
+      double *C_l = w.C;
+      const int *re_l = w.row_exp, *ce_l = w.col_exp;
+      if (valid_l) {
+        gb_l = w.gb[g];
+        bool ok = gb_l >= 0 && gb_l < w.nB;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ga_l[q] = w.ga[4 * g + q];
+          gc_l[q] = w.gc[4 * g + q];
+          ok = ok && gc_l[q] < w.nC && (gc_l[q] < 0 || (ga_l[q] >= 0 && ga_l[q] < w.nA));
+        }
+        ok = ok && gc_l[0] >= 0;
+        if (!CHT_INDEX_OK(ok, status)) valid_l = false;
+      }
+      if (valid_l) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cr_l[q] = gc_l[q] >= 0 ? w.crow[gc_l[q]] : 0;
+        ccol_l = w.ccol[gc_l[0]];
+        bool ok = ccol_l >= 0 && ccol_l < w.G;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ok = ok && cr_l[q] >= 0 && cr_l[q] < w.G;
+        if (!CHT_INDEX_OK(ok, status)) valid_l = false;
+      }
+      for (int j = 0; j < kChunk && !done; ++j) {
+        const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
+        const bool ok = wait_or_abort(&qempty[qs], qph ^ 1u, wait_ns, abort_flag);
+        if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
+          if (lane == 0) fail();
+          done = true;
+          break;
+        }
+        GSlot &sl = queue[qs];
+        const int valid = __shfl_sync(0xffffffffu, valid_l ? 1 : 0, j);
+        if (!valid) {
+          if (lane == 0) {
+            sl.count = 0;
+            mbar_arrive(&qfull[qs]);
+          }
+          done = true;
+          break;
+        }
+        int ga[4], gc[4], cr[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ga[q] = __shfl_sync(0xffffffffu, ga_l[q], j);
+          gc[q] = __shfl_sync(0xffffffffu, gc_l[q], j);
+          cr[q] = __shfl_sync(0xffffffffu, cr_l[q], j);
+        }
+        const uint8_t *a_slices = reinterpret_cast<const uint8_t *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(as_l), j));
+        const uint8_t *b_slices = reinterpret_cast<const uint8_t *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(bs_l), j));
+        double *Cbase = reinterpret_cast<double *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(C_l), j));
+        const int *row_exp = reinterpret_cast<const int *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(re_l), j));
+        const int *col_exp = reinterpret_cast<const int *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(ce_l), j));
+        const int gbv = __shfl_sync(0xffffffffu, gb_l, j);
+        const int ccv = __shfl_sync(0xffffffffu, ccol_l, j);
+        int count = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) count += gc[q] >= 0 ? 1 : 0;
+        if (lane < 4) {
+          sl.C[lane] = gc[lane] >= 0 ? Cbase + static_cast<int64_t>(gc[lane]) * 1024 : nullptr;
+          sl.crow[lane] = cr[lane];
+        }
+        if (lane == 0) {
+          sl.ccol = ccv;
+          sl.count = count;
+          sl.row_exp = row_exp;
+          sl.col_exp = col_exp;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&qfull[qs]);
+        // the group's tiles: B slices 1..6 (one copy) and A slices 1..6 of
+        // each unit into [slice][unit]
+        const uint32_t st = n % S, ph = (n / S) & 1u;
+        const bool w_ok = wait_or_abort(&empty[st], ph ^ 1u, wait_ns, abort_flag);
+        if (!__shfl_sync(0xffffffffu, w_ok ? 1 : 0, 0)) {
+          if (lane == 0) fail();
+          done = true;
+          break;
+        }
+        if (lane == 0)
+          mbar_arrive_expect_tx(&full[st], static_cast<uint32_t>(kB + count * kASlices * kTile));
+        __syncwarp();
+        uint8_t *sa = stage_base + st * kStage;
+        if (lane < 4 * kASlices) {
+          const int q = lane / kASlices, i = lane % kASlices;
+          if (gc[q] >= 0)
+            bulk_g2s(sa + (i * 4 + q) * kTile,
+                     a_slices + (static_cast<int64_t>(ga[q]) * Cfg<32>::SA + i) * kTile,
+                     static_cast<uint32_t>(kTile), &full[st]);
+        } else if (lane == 4 * kASlices) {
+          bulk_g2s(sa + kA, b_slices + static_cast<int64_t>(gbv) * kB, static_cast<uint32_t>(kB),
+                   &full[st]);
+        }
+        ++n;
+      }
+    }
+    if (lane == 0) {
+      for (uint32_t j = (n >= S ? n - S : 0); j < n; ++j)
+        mbar_wait_bounded(&full[j % S], (j / S) & 1u, kDrainNs);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------ MMA issuer --
+    if (lane == 0) {
+      constexpr uint32_t IDESC = make_idesc(128, 32);
+      for (uint32_t n = 0;; ++n) {
+        const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
+        if (!wait_or_abort(&qfull[qs], qph, wait_ns, abort_flag)) {
+          fail();
+          break;
+        }
+        if (queue[qs].count == 0) break;
+        mbar_arrive(&qempty[qs]);
+        // accumulator set bf: the epilogue must have read the group before
+        // last (the previous user of this set)
+        const uint32_t bf = n & 1u, use = n >> 1;
+        if (!wait_or_abort(&acc_empty[bf], (use & 1u) ^ 1u, wait_ns, abort_flag)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = n % S, ph = (n / S) & 1u;
+        if (!wait_or_abort(&full[st], ph, wait_ns, abort_flag)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = smem_addr(stage_base + st * kStage), sb = sa + kA;
+        const uint32_t set = tmem + bf * kSetCols;
+#pragma unroll
+        for (int x = 0; x < kNPairs; ++x) {
+          const int t = pair_t(x), i = pair_i(x), j = t - i;
+          const bool first = x == 0 || pair_t(x - 1) != t;  // first pair of its diagonal
+          const uint64_t ad = sw64_desc(sa + (i - 1) * 4 * kTile);
+          const uint64_t bd = sw64_desc(sb + (j - 1) * kTile);
+          const uint32_t dt = set + static_cast<uint32_t>((t - 2) * 32);
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk)
+            tc_mma(dt, ad + 2 * kk, bd + 2 * kk, IDESC, (first && kk == 0) ? 0u : 1u);
+        }
+        tc_commit(&empty[st]);  // the stage is free when these MMAs finish
+        tc_commit(&acc_full[bf]);
+      }
+      tc_commit(drain);
+      mbar_wait_bounded(drain, 0, kDrainNs);
+    }
+  } else {
+    // -------------------------------------------------------- epilogue --
+    const int q = warp & 3;                 // lane quarter = unit of the group
+    const int c0 = (warp >= 6) ? 16 : 0;    // this warp's 16 columns
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * q) << 16);
+    for (uint32_t n = 0;; ++n) {
+      const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
+      if (!warp_wait_or_abort(&qfull[qs], qph, wait_ns, abort_flag)) {
+        fail();
+        break;
+      }
+      const GSlot &sl = queue[qs];
+      if (sl.count == 0) break;
+      double *Cq = sl.C[q];
+      // line exponents (loaded while the MMAs run)
+      const int er = Cq ? sl.row_exp[static_cast<int64_t>(sl.crow[q]) * 32 + lane] : kNoExp;
+      int fc[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) fc[c] = sl.col_exp[static_cast<int64_t>(sl.ccol) * 32 + c0 + c];
+      const uint32_t bf = n & 1u, use = n >> 1;
+      if (!warp_wait_or_abort(&acc_full[bf], use & 1u, wait_ns, abort_flag)) {
+        fail();
+        break;
+      }
+      tc_fence_after();
+      // the six diagonals, most significant first: T <- 2^8 T + S_t
+      const uint32_t base = lane_base + bf * kSetCols + c0;
+      long long T[16];
+      {
+        float v[16];
+        tmem_ld16(base, v);
+        tc_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) T[c] = __float2int_rn(v[c]);
+      }
+#pragma unroll
+      for (int r = 1; r < kRegionsS; ++r) {
+        float v[16];
+        tmem_ld16(base + static_cast<uint32_t>(r * 32), v);
+        tc_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) T[c] = T[c] * 256 + __float2int_rn(v[c]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[bf]);  // the MMA may reuse this set
+      if (Cq) {
+        double *dst = Cq + lane * 32 + c0;
+#pragma unroll
+        for (int c = 0; c < 16; c += 2) {
+          double2 o;
+          o.x = (er == kNoExp || fc[c] == kNoExp) ? 0.0 : scaled_i64_to_double(T[c], er + fc[c] - 56);
+          o.y = (er == kNoExp || fc[c + 1] == kNoExp)
+                    ? 0.0
+                    : scaled_i64_to_double(T[c + 1], er + fc[c + 1] - 56);
+          *reinterpret_cast<double2 *>(dst + c) = o;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&qempty[qs]);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
 // Scratch of one operand pair: line exponents and slices.
 struct Operands {
   DevArray<int> row_exp, col_exp;
@@ -1211,12 +1636,18 @@ SplitProd make_prod(const cht_plan *plan, const Operands &op, double *Cvals) {
   d.col_exp = op.col_exp.p;
   d.C = Cvals;
   d.b = plan->b;
+  d.nA = plan->nA;
+  d.nB = plan->nB;
+  d.nunits = plan->C->nnz;
+  d.npairs = plan->npairs;
+  d.G = plan->C->G;
   return d;
 }
 
 template <int MAXB>
-int launch_split(const SplitProd &single, const SplitProd *prods, const int64_t *units,
-                 int64_t nunits, unsigned long long *counter, cudaStream_t s) {
+int launch_split(const SplitProd &single, const SplitProd *prods, int32_t nprods,
+                 const int64_t *units, int64_t nunits, unsigned long long *counter,
+                 cudaStream_t s) {
   if (nunits <= 0) return CHT_OK;
   CHT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
   int *status = nullptr;
@@ -1228,8 +1659,8 @@ int launch_split(const SplitProd &single, const SplitProd *prods, const int64_t 
   CHT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem)));
   const int64_t grid = std::min<int64_t>(nunits, sms);
-  kern<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(single, prods, units, nunits, counter,
-                                                          status, g_opt.wait_budget_ns);
+  kern<<<static_cast<unsigned>(grid), kThreads, smem, s>>>(single, prods, nprods, units, nunits,
+                                                          counter, status, g_opt.wait_budget_ns);
   return launched("split_gemm");
 }
 
@@ -1335,14 +1766,233 @@ __global__ void k_pack_units(int64_t n, int64_t prod, int64_t off, int64_t *__re
     units[off + u] = (prod << 32) | u;
 }
 
+// ------------------------------------- grouping of the one-pair C leaves --
+// The C leaves with exactly one pair, sorted by that pair's B leaf in row-
+// major (K, J) order -- neighbouring groups then share the A leaves of one
+// inner index K through L2 -- and cut into groups of at most 4 per B leaf;
+// the C leaves with two or more pairs form the general kernel's unit list.
+__global__ void k_classify(const int64_t *__restrict__ cseg, int64_t nC,
+                           int32_t *__restrict__ one, int32_t *__restrict__ more) {
+  for (int64_t o = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; o < nC;
+       o += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t np = cseg[o + 1] - cseg[o];
+    one[o] = np == 1 ? 1 : 0;
+    more[o] = np >= 2 ? 1 : 0;
+  }
+}
+
+__global__ void k_single_keys(const int64_t *__restrict__ cseg, const int32_t *__restrict__ pb,
+                              const int32_t *__restrict__ b_row, const int32_t *__restrict__ b_col,
+                              int L, const int32_t *__restrict__ one,
+                              const int64_t *__restrict__ opos, const int32_t *__restrict__ more,
+                              const int64_t *__restrict__ mpos, int64_t nC,
+                              uint64_t *__restrict__ key, int32_t *__restrict__ val,
+                              int64_t *__restrict__ munits) {
+  for (int64_t o = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; o < nC;
+       o += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (one[o]) {
+      const int32_t bl = pb[cseg[o]];
+      const int64_t i = opos[o];
+      key[i] = (static_cast<uint64_t>(b_row[bl]) << L) | static_cast<uint32_t>(b_col[bl]);
+      val[i] = static_cast<int32_t>(o);
+    } else if (more[o]) {
+      munits[mpos[o]] = o;
+    }
+  }
+}
+
+__global__ void k_key_heads(const uint64_t *__restrict__ key, int64_t n,
+                            int32_t *__restrict__ head) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    head[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+}
+
+// run r starts at start[r]; hx = exclusive scan of the heads
+__global__ void k_run_starts(const int32_t *__restrict__ head, const int64_t *__restrict__ hx,
+                             int64_t n, int64_t *__restrict__ start) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    if (head[i]) start[hx[i]] = i;
+}
+
+// a group starts at every 4th element of a run
+__global__ void k_group_starts(const int32_t *__restrict__ head, const int64_t *__restrict__ hx,
+                               const int64_t *__restrict__ start, int64_t n,
+                               int32_t *__restrict__ gs) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t pos = i - start[hx[i] + head[i] - 1];
+    gs[i] = (pos & 3) == 0 ? 1 : 0;
+  }
+}
+
+__global__ void k_group_fill(const int32_t *__restrict__ val, const int32_t *__restrict__ head,
+                             const int64_t *__restrict__ hx, const int64_t *__restrict__ start,
+                             const int32_t *__restrict__ gs, const int64_t *__restrict__ gx,
+                             int64_t n, const int64_t *__restrict__ cseg,
+                             const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
+                             int32_t *__restrict__ gb, int32_t *__restrict__ ga,
+                             int32_t *__restrict__ gc) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t pos = i - start[hx[i] + head[i] - 1];
+    const int64_t g = gx[i] + gs[i] - 1;
+    const int q = static_cast<int>(pos & 3);
+    const int32_t o = val[i];
+    const int64_t p = cseg[o];
+    ga[4 * g + q] = pa[p];
+    gc[4 * g + q] = o;
+    if (q == 0) gb[g] = pb[p];
+  }
+}
+
+struct SingleGroups {
+  DevArray<int32_t> gb, ga, gc;  // per group: B leaf; 4 A leaves; 4 C leaves (-1: none)
+  DevArray<int64_t> more;        // C leaves with two or more pairs
+  int64_t ngroups = 0, nmore = 0, nsingle = 0;
+};
+
+int build_single_groups(const cht_plan *plan, const Pattern &pb_pat, cudaStream_t s,
+                        SingleGroups &g) {
+  const int64_t nC = plan->C->nnz;
+  DevArray<int32_t> one, more;
+  DevArray<int64_t> opos, mpos;
+  CHT_TRY(one.alloc(nC, s));
+  CHT_TRY(more.alloc(nC, s));
+  CHT_TRY(opos.alloc(nC + 1, s));
+  CHT_TRY(mpos.alloc(nC + 1, s));
+  if (nC > 0) {
+    k_classify<<<grid_for(nC, 256), 256, 0, s>>>(plan->cseg.p, nC, one.p, more.p);
+    CHT_TRY(launched("classify"));
+  }
+  CHT_TRY(scan_exclusive(one.p, opos.p, nC, s));
+  CHT_TRY(scan_exclusive(more.p, mpos.p, nC, s));
+  int64_t counts[2] = {0, 0};
+  CHT_CUDA_TRY(cudaMemcpyAsync(&counts[0], opos.p + nC, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CHT_CUDA_TRY(cudaMemcpyAsync(&counts[1], mpos.p + nC, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CHT_CUDA_TRY(cudaStreamSynchronize(s));
+  const int64_t nS = counts[0];
+  g.nsingle = nS;
+  g.nmore = counts[1];
+  DevArray<uint64_t> key, skey;
+  DevArray<int32_t> val, sval;
+  CHT_TRY(key.alloc(nS, s));
+  CHT_TRY(skey.alloc(nS, s));
+  CHT_TRY(val.alloc(nS, s));
+  CHT_TRY(sval.alloc(nS, s));
+  CHT_TRY(g.more.alloc(g.nmore, s));
+  if (nC > 0) {
+    k_single_keys<<<grid_for(nC, 256), 256, 0, s>>>(
+        plan->cseg.p, plan->pb.p, pb_pat.brow.p, pb_pat.bcol.p, pb_pat.L, one.p, opos.p, more.p,
+        mpos.p, nC, key.p, val.p, g.more.p);
+    CHT_TRY(launched("single_keys"));
+  }
+  if (nS == 0) return CHT_OK;
+  CHT_TRY(radix_sort_pairs(key.p, val.p, skey.p, sval.p, nS, 2 * pb_pat.L, s));
+  DevArray<int32_t> head, gs;
+  DevArray<int64_t> hx, start, gx;
+  CHT_TRY(head.alloc(nS, s));
+  CHT_TRY(gs.alloc(nS, s));
+  CHT_TRY(hx.alloc(nS + 1, s));
+  CHT_TRY(start.alloc(nS, s));
+  CHT_TRY(gx.alloc(nS + 1, s));
+  k_key_heads<<<grid_for(nS, 256), 256, 0, s>>>(skey.p, nS, head.p);
+  CHT_TRY(launched("key_heads"));
+  CHT_TRY(scan_exclusive(head.p, hx.p, nS, s));
+  k_run_starts<<<grid_for(nS, 256), 256, 0, s>>>(head.p, hx.p, nS, start.p);
+  CHT_TRY(launched("run_starts"));
+  k_group_starts<<<grid_for(nS, 256), 256, 0, s>>>(head.p, hx.p, start.p, nS, gs.p);
+  CHT_TRY(launched("group_starts"));
+  CHT_TRY(scan_exclusive(gs.p, gx.p, nS, s));
+  int64_t ng = 0;
+  CHT_TRY(read_i64(gx.p + nS, &ng, s));
+  g.ngroups = ng;
+  CHT_TRY(g.gb.alloc(ng, s));
+  CHT_TRY(g.ga.alloc(4 * ng, s));
+  CHT_TRY(g.gc.alloc(4 * ng, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(g.ga.p, 0, sizeof(int32_t) * 4 * ng, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(g.gc.p, 0xff, sizeof(int32_t) * 4 * ng, s));  // -1
+  k_group_fill<<<grid_for(nS, 256), 256, 0, s>>>(sval.p, head.p, hx.p, start.p, gs.p, gx.p, nS,
+                                                 plan->cseg.p, plan->pa.p, plan->pb.p, g.gb.p,
+                                                 g.ga.p, g.gc.p);
+  return launched("group_fill");
+}
+
+// One launch over `ntotal` groups: those of `w` (works NULL), or the groups
+// gunits[] of the batch's products works[0 .. nworks).
+int launch_single32(const SingleWork &w, const SingleWork *works, int32_t nworks,
+                    const int64_t *gunits, int64_t ntotal, unsigned long long *counter,
+                    cudaStream_t s) {
+  if (ntotal <= 0) return CHT_OK;
+  CHT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+  int *status = nullptr;
+  CHT_TRY(device_status_ptr(&status));
+  int sms = 0;
+  CHT_TRY(num_sms(&sms));
+  constexpr size_t smem = single32_smem();
+  CHT_CUDA_TRY(cudaFuncSetAttribute(k_split_single32,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem)));
+  const int64_t grid = std::min<int64_t>((ntotal + single32::kChunk - 1) / single32::kChunk, sms);
+  k_split_single32<<<static_cast<unsigned>(std::max<int64_t>(grid, 1)), kThreads, smem, s>>>(
+      w, works, nworks, gunits, ntotal, counter, status, g_opt.wait_budget_ns);
+  return launched("split_single32");
+}
+
+// Packed units (product << 32) | list[u] of one product.
+__global__ void k_pack_list(int64_t n, int64_t prod, const int64_t *__restrict__ list,
+                            int64_t off, int64_t *__restrict__ units) {
+  for (int64_t u = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; u < n;
+       u += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    units[off + u] = (prod << 32) | list[u];
+}
+
+// The one-pair kernel's view of one product.
+SingleWork make_single_work(const cht_plan *plan, const Operands &op, const SingleGroups &g,
+                            double *Cvals) {
+  SingleWork sw{};
+  sw.a_slices = op.a_sl.p;
+  sw.b_slices = op.b_sl.p;
+  sw.gb = g.gb.p;
+  sw.ga = g.ga.p;
+  sw.gc = g.gc.p;
+  sw.crow = plan->C->brow.p;
+  sw.ccol = plan->C->bcol.p;
+  sw.row_exp = op.row_exp.p;
+  sw.col_exp = op.col_exp.p;
+  sw.C = Cvals;
+  sw.ngroups = g.ngroups;
+  sw.nA = plan->nA;
+  sw.nB = plan->nB;
+  sw.nC = plan->C->nnz;
+  sw.G = plan->C->G;
+  return sw;
+}
+
+// The plan's one-pair groups, built at its first use and kept in the plan.
+int plan_groups(cht_plan *plan, const Pattern &b_pat, cudaStream_t s, const SingleGroups **out) {
+  if (!plan->split_groups) {
+    auto g = std::make_shared<SingleGroups>();
+    CHT_TRY(build_single_groups(plan, b_pat, s, *g));
+    plan->split_groups = g;
+  }
+  *out = static_cast<const SingleGroups *>(plan->split_groups.get());
+  return CHT_OK;
+}
+
 struct SplitBatch {
   std::vector<Operands> ops;
   std::vector<PieceUnits> pieces;  // per product; used where has_pieces
   std::vector<char> has_pieces;
-  DevArray<int64_t> units;         // the piece-aware unit list (when any product has pieces)
+  std::vector<char> one_pair;      // product's one-pair leaves go to the one-pair kernel
+  DevArray<int64_t> units;         // the general kernel's units (when own_units)
   int64_t nunits = 0;
   bool own_units = false;
   DevArray<SplitProd> prods;
+  DevArray<SingleWork> works;      // the one-pair kernel's product table
+  DevArray<int64_t> gunits;        // (product << 32) | group, every one-pair product
+  int64_t ngunits = 0;
   DevArray<unsigned long long> counter;
   int maxb = 32;
 };
@@ -1363,6 +2013,12 @@ int split_multiply(cht_plan *plan, cht_mat *A, cht_mat *B, int nslices, cudaStre
   // elementwise bound relative to 2^(e_r + f_c): K (s + 3) 2^(-s w) with
   // K <= n, plus the FP32 rounding of the low regions (below 2^-50)
   *err_bound = static_cast<double>(plan->n) * (kSB + 3) * 0x1p-48 + 0x1p-50;
+  const bool pieces = plan->max_seg > max_unit_pairs(b);
+  const bool one_pair = b == 32 && !pieces && g_opt.split_single;
+  // the plan's one-pair groups first (their build synchronises, so it should
+  // not wait for the slicing pre-kernels)
+  const SingleGroups *groups = nullptr;
+  if (one_pair) CHT_TRY(plan_groups(plan, *B->pat, s, &groups));
   Operands op;
   CHT_TRY(alloc_operands(*A->pat, *B->pat, s, op));
   if (b == 64)
@@ -1374,19 +2030,27 @@ int split_multiply(cht_plan *plan, cht_mat *A, cht_mat *B, int nslices, cudaStre
   CHT_TRY(counter.alloc(1, s));
   int64_t nunits = plan->C->nnz;
   PieceUnits pu;
-  const bool pieces = plan->max_seg > max_unit_pairs(b);
   if (pieces) {
     CHT_TRY(make_pieces(plan, Cvals, s, pu));
     d.cseg = pu.vseg.p;
     d.crow = pu.vrow.p;
     d.ccol = pu.vcol.p;
     d.cptr = pu.vptr.p;
+    d.nunits = pu.nv;
     nunits = pu.nv;
   }
+  if (one_pair) {
+    // one-pair C leaves grouped by B leaf; the others by the general kernel
+    const SingleGroups *g = groups;
+    const SingleWork sw = make_single_work(plan, op, *g, Cvals);
+    CHT_TRY(launch_single32(sw, nullptr, 0, nullptr, sw.ngroups, counter.p, s));
+    if (g->nmore > 0) CHT_TRY(launch_split<32>(d, nullptr, 0, g->more.p, g->nmore, counter.p, s));
+    return CHT_OK;
+  }
   if (b == 64)
-    CHT_TRY(launch_split<64>(d, nullptr, nullptr, nunits, counter.p, s));
+    CHT_TRY(launch_split<64>(d, nullptr, 0, nullptr, nunits, counter.p, s));
   else
-    CHT_TRY(launch_split<32>(d, nullptr, nullptr, nunits, counter.p, s));
+    CHT_TRY(launch_split<32>(d, nullptr, 0, nullptr, nunits, counter.p, s));
   if (pieces) {
     const int64_t nC = plan->C->nnz;
     k_piece_reduce<<<static_cast<unsigned>(std::min<int64_t>(nC, 65535LL * 8)), 256, 0, s>>>(
@@ -1403,10 +2067,12 @@ int split_batch_prepare(cht_batch *bt, cudaStream_t s) {
   }
   auto sb = std::make_unique<SplitBatch>();
   std::vector<SplitProd> host(bt->count);
+  std::vector<SingleWork> works(bt->count);
   sb->ops.resize(bt->count);
   sb->pieces.resize(bt->count);
   sb->has_pieces.assign(bt->count, 0);
-  bool any = false;
+  sb->one_pair.assign(bt->count, 0);
+  bool own = false;
   for (int32_t i = 0; i < bt->count; ++i) {
     cht_plan *plan = bt->plans[i];
     CHT_TRY(alloc_operands(*bt->As[i]->pat, *bt->Bs[i]->pat, s, sb->ops[i]));
@@ -1420,22 +2086,53 @@ int split_batch_prepare(cht_batch *bt, cudaStream_t s) {
       host[i].crow = pu.vrow.p;
       host[i].ccol = pu.vcol.p;
       host[i].cptr = pu.vptr.p;
+      host[i].nunits = pu.nv;
       sb->has_pieces[i] = 1;
-      any = true;
+      own = true;
+    } else if (plan->b == 32 && g_opt.split_single) {
+      // as cht_multiply: one-pair C leaves to the one-pair kernel
+      const SingleGroups *g = nullptr;
+      CHT_TRY(plan_groups(plan, *bt->Bs[i]->pat, s, &g));
+      works[i] = make_single_work(plan, sb->ops[i], *g, bt->views[i]->view_vals);
+      sb->one_pair[i] = 1;
+      sb->ngunits += g->ngroups;
+      own = true;
     }
   }
-  if (any) {
-    // the unit list in terms of pieces: every product's units in order
+  if (own) {
+    // the general kernel's units, every product's in order: its pieces, its
+    // C leaves of two or more pairs (one-pair products), or all its C leaves
     int64_t total = 0;
-    for (int32_t i = 0; i < bt->count; ++i)
-      total += sb->has_pieces[i] ? sb->pieces[i].nv : bt->plans[i]->C->nnz;
-    if (total > 0x7fffffffLL) {
+    for (int32_t i = 0; i < bt->count; ++i) {
+      const SingleGroups *g = static_cast<const SingleGroups *>(bt->plans[i]->split_groups.get());
+      total += sb->has_pieces[i] ? sb->pieces[i].nv
+               : sb->one_pair[i] ? g->nmore
+                                 : bt->plans[i]->C->nnz;
+    }
+    if (total > 0x7fffffffLL || sb->ngunits > 0x7fffffffLL) {
       set_error("batch has too many work units");
       return CHT_ERR_UNSUPPORTED;
     }
     CHT_TRY(sb->units.alloc(total, s));
-    int64_t off = 0;
+    CHT_TRY(sb->gunits.alloc(sb->ngunits, s));
+    int64_t off = 0, goff = 0;
     for (int32_t i = 0; i < bt->count; ++i) {
+      const SingleGroups *g = static_cast<const SingleGroups *>(bt->plans[i]->split_groups.get());
+      if (sb->one_pair[i]) {
+        if (g->nmore > 0) {
+          k_pack_list<<<grid_for(g->nmore, 256), 256, 0, s>>>(g->nmore, i, g->more.p, off,
+                                                              sb->units.p);
+          CHT_TRY(launched("pack_list"));
+        }
+        off += g->nmore;
+        if (g->ngroups > 0) {
+          k_pack_units<<<grid_for(g->ngroups, 256), 256, 0, s>>>(g->ngroups, i, goff,
+                                                                 sb->gunits.p);
+          CHT_TRY(launched("pack_units"));
+        }
+        goff += g->ngroups;
+        continue;
+      }
       const int64_t n = sb->has_pieces[i] ? sb->pieces[i].nv : bt->plans[i]->C->nnz;
       if (n > 0) {
         k_pack_units<<<grid_for(n, 256), 256, 0, s>>>(n, i, off, sb->units.p);
@@ -1447,8 +2144,11 @@ int split_batch_prepare(cht_batch *bt, cudaStream_t s) {
     sb->own_units = true;
   }
   CHT_TRY(sb->prods.alloc(bt->count, s));
+  CHT_TRY(sb->works.alloc(bt->count, s));
   CHT_TRY(sb->counter.alloc(1, s));
   CHT_CUDA_TRY(cudaMemcpyAsync(sb->prods.p, host.data(), sizeof(SplitProd) * bt->count,
+                               cudaMemcpyHostToDevice, s));
+  CHT_CUDA_TRY(cudaMemcpyAsync(sb->works.p, works.data(), sizeof(SingleWork) * bt->count,
                                cudaMemcpyHostToDevice, s));
   CHT_CUDA_TRY(cudaStreamSynchronize(s));
   bt->split_state = sb.release();
@@ -1466,10 +2166,13 @@ int split_batch_run(cht_batch *bt, cudaStream_t s) {
   const SplitProd none{};
   const int64_t *units = sb->own_units ? sb->units.p : bt->units.p;
   const int64_t nunits = sb->own_units ? sb->nunits : bt->nunits;
+  if (sb->ngunits > 0)
+    CHT_TRY(launch_single32(SingleWork{}, sb->works.p, bt->count, sb->gunits.p, sb->ngunits,
+                            sb->counter.p, s));
   if (sb->maxb == 64)
-    CHT_TRY(launch_split<64>(none, sb->prods.p, units, nunits, sb->counter.p, s));
+    CHT_TRY(launch_split<64>(none, sb->prods.p, bt->count, units, nunits, sb->counter.p, s));
   else
-    CHT_TRY(launch_split<32>(none, sb->prods.p, units, nunits, sb->counter.p, s));
+    CHT_TRY(launch_split<32>(none, sb->prods.p, bt->count, units, nunits, sb->counter.p, s));
   for (int32_t i = 0; i < bt->count; ++i) {
     if (!sb->has_pieces[i]) continue;
     const cht_plan *plan = bt->plans[i];

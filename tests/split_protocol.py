@@ -81,12 +81,18 @@ class Config:
     nxb: int       # exchange buffers (2 in the 32-leaf kernel)
     stages: int    # operand stages
     windows: dict  # pairs per exact window, by leaf size
+    kind: str = "general"  # "one_pair": the kernel of one-pair C leaves
 
 
 # the kernel taking 64-leaves (and 32-leaf units of mixed batches), and the
 # 32-leaf-only kernel
 KERNEL_64 = Config(nb=1, nxb=1, stages=2, windows={64: 8, 32: 32})
-KERNEL_32 = Config(nb=2, nxb=2, stages=2, windows={32: 32})
+KERNEL_32 = Config(nb=2, nxb=2, stages=4, windows={32: 32})
+# k_split_single32: groups of up to 4 one-pair C leaves sharing a B leaf; two
+# accumulator sets of 6 regions (group n uses set n % 2), each read whole and
+# released by every epilogue warp before it stores; no exchange buffer
+ONE_PAIR = Config(nb=2, nxb=0, stages=3, windows={}, kind="one_pair")
+ONE_PAIR_REGIONS = 6
 
 
 @dataclass
@@ -328,6 +334,161 @@ def kernel_roles(st: State, units, mistakes=frozenset()):
     return roles
 
 
+def one_pair_roles(st: State, groups, mistakes=frozenset()):
+    """Generators for the roles of k_split_single32 (same conventions as
+    kernel_roles).  ``groups`` lists the units of each group this CTA takes
+    (1..4); the protocol does not depend on them.  Per group: the producer
+    stages the slot and one operand stage; the MMA thread waits for the
+    epilogue's release of the group before last (the previous user of the
+    same accumulator set), then for the stage, and restarts that set's six
+    regions; every epilogue warp reads all six regions of the group's set,
+    releases them, then stores (reading the slot) and frees the slot."""
+    cfg = st.cfg
+    S = cfg.stages
+    bars = st.bars
+    for i in range(S):
+        bars[f"full{i}"] = Barrier(f"full{i}", 1)
+        bars[f"empty{i}"] = Barrier(f"empty{i}", 1)
+    for i in range(QUEUE):
+        bars[f"qfull{i}"] = Barrier(f"qfull{i}", 1)
+        bars[f"qempty{i}"] = Barrier(f"qempty{i}", 1 + EPI_WARPS)
+    for bf in range(cfg.nb):
+        bars[f"acc_full{bf}"] = Barrier(f"acc_full{bf}", 1)
+        bars[f"acc_empty{bf}"] = Barrier(f"acc_empty{bf}", EPI_WARPS)
+    bars["drain"] = Barrier("drain", 1)
+    everyone = frozenset(["mma"] + [f"epi{w}" for w in range(EPI_WARPS)])
+    warps = frozenset(f"epi{w}" for w in range(EPI_WARPS))
+    slots = {}
+    ngroups = len(groups)
+    nb = cfg.nb
+
+    def wait(name, phase, abortable=True):
+        return ("wait", bars[name], phase, abortable)
+
+    def fail():
+        st.status_timeout = True
+        st.abort = True
+
+    def producer():
+        n = 0
+        for n in range(ngroups + 1):
+            qs = n % QUEUE
+            if not (yield wait(f"qempty{qs}", n // QUEUE - 1)):
+                fail()
+                break
+            if st.slot_readers.get(qs):
+                raise ProtocolError(f"slot {qs} rewritten for group {n} while "
+                                    f"{sorted(st.slot_readers[qs])} still use it")
+            count = groups[n] if n < ngroups else 0
+            slots[qs] = (count, n)
+            st.slot_readers[qs] = set(everyone)
+            bars[f"qfull{qs}"].arrive()
+            if count == 0:
+                break
+            yield None
+            s = n % S
+            if "producer_skips_empty_wait" not in mistakes:
+                if not (yield wait(f"empty{s}", n // S - 1)):
+                    fail()
+                    break
+            if s in st.stage_busy:
+                raise ProtocolError(f"stage {s} refilled for group {n} while MMAs of "
+                                    f"group {st.stage_busy[s]} still read it")
+            st.stage_busy[s] = n
+            bars[f"full{s}"].arrive(expect_tx=count + 1)  # A tiles of each unit, the B leaf
+            st.copies.extend([(bars[f"full{s}"], 1)] * (count + 1))
+            yield None
+        staged = n if n < ngroups else ngroups
+        if "producer_no_drain" not in mistakes:
+            for j in range(max(0, staged - S), staged):
+                yield wait(f"full{j % S}", j // S, abortable=False)
+
+    def mma():
+        for n in range(ngroups + 1):
+            qs = n % QUEUE
+            if not (yield wait(f"qfull{qs}", n // QUEUE)):
+                fail()
+                break
+            count, _ = slots[qs]
+            st.slot_readers[qs].discard("mma")
+            if count == 0:
+                break
+            bars[f"qempty{qs}"].arrive()
+            bf = n % nb
+            if "mma_skips_unit_wait" not in mistakes:
+                if not (yield wait(f"acc_empty{bf}", n // nb - 1)):
+                    fail()
+                    break
+            s = n % S
+            if not (yield wait(f"full{s}", n // S)):
+                fail()
+                break
+            for r in range(ONE_PAIR_REGIONS):
+                key = (bf, r)
+                old = st.readers.get(key)
+                if old and old[1]:
+                    raise ProtocolError(f"region {r} restarted for group {n} while "
+                                        f"{sorted(old[1])} have not read group {old[0]}")
+                st.readers[key] = (n, set(warps))
+                st.inflight.append(("mma", key))
+            st.inflight.append(("commit", bars[f"empty{s}"], n))
+            st.inflight.append(("commit", bars[f"acc_full{bf}"], None))
+            yield None
+        if "mma_no_drain" not in mistakes:
+            st.inflight.append(("commit", bars["drain"], None))
+            yield wait("drain", 0, abortable=False)
+
+    def epilogue(wid):
+        me = f"epi{wid}"
+        for n in range(ngroups + 1):
+            qs = n % QUEUE
+            if not (yield wait(f"qfull{qs}", n // QUEUE)):
+                fail()
+                break
+            count, _ = slots[qs]
+            if count == 0:
+                st.slot_readers[qs].discard(me)
+                break
+            bf = 0 if "epi_single_accumulator_set" in mistakes else n % nb
+            if not (yield wait(f"acc_full{bf}", n // nb)):
+                fail()
+                break
+            regions = range(ONE_PAIR_REGIONS)
+            if "epi_releases_before_last_region" in mistakes:
+                for r in range(ONE_PAIR_REGIONS - 1):
+                    _read(st, me, (bf, r), n)
+                bars[f"acc_empty{bf}"].arrive()
+                yield None
+                _read(st, me, (bf, ONE_PAIR_REGIONS - 1), n)
+            else:
+                for r in regions:
+                    _read(st, me, (bf, r), n)
+                bars[f"acc_empty{bf}"].arrive()
+            yield None  # assemble and store, with the slot's pointers
+            if slots[qs][1] != n:
+                raise ProtocolError(f"{me}: slot {qs} of group {n} was rewritten for group "
+                                    f"{slots[qs][1]} while still in use")
+            st.slot_readers[qs].discard(me)
+            if "epi_skips_slot_release" not in mistakes or wid != 3:
+                bars[f"qempty{qs}"].arrive()
+            yield None
+
+    roles = {"producer": producer(), "mma": mma()}
+    for wid in range(EPI_WARPS):
+        roles[f"epi{wid}"] = epilogue(wid)
+    return roles
+
+
+def _read(st: State, me: str, key, tag):
+    if any(op[0] == "mma" and op[1] == key for op in st.inflight):
+        raise ProtocolError(f"{me} reads TMEM region {key} ({tag}) while MMAs on it are in "
+                            f"flight")
+    cur = st.readers.get(key)
+    if cur is None or cur[0] != tag or me not in cur[1]:
+        raise ProtocolError(f"{me} expected {tag} in TMEM region {key}, found {cur and cur[0]}")
+    cur[1].discard(me)
+
+
 def run(cfg: Config, units, seed: int, mistakes=frozenset(), timeout=None,
         max_steps: int = 2_000_000) -> State:
     """Replay the protocol under one random schedule and return the final
@@ -336,7 +497,8 @@ def run(cfg: Config, units, seed: int, mistakes=frozenset(), timeout=None,
     abortable wait on, its first wait that would block runs out of time."""
     rng = random.Random(seed)
     st = State(cfg)
-    roles = kernel_roles(st, units, mistakes)
+    make = one_pair_roles if cfg.kind == "one_pair" else kernel_roles
+    roles = make(st, units, mistakes)
     waiting, done = {}, set()
     nwaits = {name: 0 for name in roles}
 

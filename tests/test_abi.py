@@ -43,6 +43,17 @@ def test_library_exports_every_declared_symbol(libpath):
     assert not missing, missing
 
 
+def test_checked_build_exports_every_declared_symbol():
+    # the bounds-checked debug variant (-DCHT_BOUNDS_CHECK) builds from the
+    # same sources and exports the same boundary
+    from paper_2011_11762_gb300 import build
+    path = build.build(checked=True)
+    assert path.endswith("libcht_checked.so")
+    lib = ctypes.CDLL(path)
+    missing = [n for n in sorted(_declared_functions()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
 def test_binding_signatures_cover_the_header():
     from paper_2011_11762_gb300 import _lib
     assert _declared_functions() <= set(_lib.SIGNATURES)

@@ -40,7 +40,7 @@ def lib():
 
 
 @pytest.mark.parametrize("name", list(_cases()))
-@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("engine", [0, 1, 2])
 def test_multiply_matches_oracle(lib, name, engine):
     a, b = _cases()[name]()
     A, B = gu.upload(lib, a), gu.upload(lib, b)

@@ -14,6 +14,9 @@ pytestmark = pytest.mark.gpu
 
 CASES = {
     "banded_4096_b32": lambda: w.config1(),
+    # mostly one leaf pair per C leaf: the split form groups them by B leaf
+    "random_8192_b32": lambda: (w.random_blocks(8192, 32, 0.02, 71),
+                                w.random_blocks(8192, 32, 0.02, 72)),
     "locality_8192_b64": lambda: w.config2(8192),
     # leaf (0, 0) sums 1100 pairs: the split kernel cuts it into pieces
     "line_pair_70400_b64": lambda: w.dense_line_pair(1100 * 64, 64, 1, 91),

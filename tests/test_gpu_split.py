@@ -37,6 +37,40 @@ def _kernel_pairs(b):
                    for q in range(2)}), sa
 
 
+def _single_pairs():
+    """Slice pairs of the kernel for C leaves with one leaf pair (32-leaves):
+    one MMA per pair (i, j) with i + j <= 7.  A keeps its 8 digits (only 1..6
+    meet a B digit)."""
+    return sp.slice_pairs(S), 8
+
+
+def _one_pair_mask(plan, n, b):
+    """Dense mask of the C leaves that sum exactly one leaf pair."""
+    arr = plan.arrays()
+    seg = np.diff(arr["cseg"].numpy())
+    out = np.zeros((n, n), dtype=bool)
+    for r, c in zip(arr["crow"].numpy()[seg == 1], arr["ccol"].numpy()[seg == 1]):
+        out[r * b:(r + 1) * b, c * b:(c + 1) * b] = True
+    return out
+
+
+def _emulate(lib, plan, ad, bd, b, n):
+    """The exact emulation of the split product with, for every C leaf, the
+    slice pairs of the kernel that computes it: at b = 32 the one-pair
+    leaves (grouped by B leaf) and the others (the general kernel) differ.
+    Returns (emulation, e, f, mask of the one-pair leaves or None)."""
+    pairs, sa = _kernel_pairs(b)
+    emu, e, f = sp.split_product(ad, bd, S, W, pairs=pairs, sa=sa)
+    if b != 32 or not lib.get_option(lib.OPT_SPLIT_SINGLE):
+        return emu, e, f, None
+    one = _one_pair_mask(plan, n, b)
+    if one.any():
+        p1, sa1 = _single_pairs()
+        emu1, _, _ = sp.split_product(ad, bd, S, W, pairs=p1, sa=sa1)
+        emu = np.where(one, emu1, emu)
+    return emu, e, f, one
+
+
 @pytest.fixture(scope="module")
 def lib():
     return gu.cht()
@@ -62,14 +96,17 @@ def test_split_matches_exact_emulation(lib, b, n, p):
     C, bound = lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
     got = _dense_on(C, n)
     ad, bd = a.to_dense(), bm.to_dense()
-    pairs, sa = _kernel_pairs(b)
-    emu, e, f = sp.split_product(ad, bd, S, W, pairs=pairs, sa=sa)
+    emu, e, f, one = _emulate(lib, plan, ad, bd, b, n)
     scale = np.ldexp(1.0, (e[:, None] + f[None, :]).astype(np.int64))
     mask = _dense_on(C, n) != 0
     # FP32 rounding in the two low TMEM regions (weight 2^-48 and 2^-56 of
     # 2^(e_r + f_c)): at most (steps) * 2^-23 * (partial sum <= 3 K 2^16),
     # steps <= 3 K / 16 per C leaf, so < 2^-54 K^2 relative, K = inner length
     tol = scale * float(n) ** 2 * 2.0 ** -54 + 2 * np.spacing(np.abs(emu))
+    if one is not None:
+        # one-pair leaves: every diagonal exact in FP32 and in the int64
+        # assembly, so only the final rounding to double remains
+        tol = np.where(one, 2 * np.spacing(np.abs(emu)), tol)
     diff = np.abs(got - emu)
     assert np.all(diff[mask] <= tol[mask]), float((diff / tol).max())
     ref = ad @ bd
@@ -101,8 +138,7 @@ def test_split_wide_exponent_range(lib, b):
     plan = lib.cht_symbolic_multiply(A, B)
     C, _ = lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
     got = _dense_on(C, n)
-    pairs, sa = _kernel_pairs(b)
-    emu, e, f = sp.split_product(a.to_dense(), bm.to_dense(), S, W, pairs=pairs, sa=sa)
+    emu, e, f, _ = _emulate(lib, plan, a.to_dense(), bm.to_dense(), b, n)
     assert np.all(np.isfinite(got))
     assert np.any((got != 0) & (np.abs(got) < np.finfo(np.float64).tiny))  # subnormals
     assert np.abs(got).max() > 2.0 ** 900
@@ -224,3 +260,73 @@ def test_full_size_random_sampled(lib):
         assert present
         assert setref.rel_fro(vd[c].cpu().numpy(), ref) <= 1e-13
         assert setref.rel_fro(vs[c].cpu().numpy(), ref) <= 1e-11
+
+
+def _one_pair_case(scaled: bool):
+    """32-leaves, n = 256 (8 x 8 leaf grid): random leaves, plus a full leaf
+    column 3 of A and B leaves (3, 1), (3, 5), (3, 6) alone in their
+    columns, so that C leaves (I, 1), (I, 5), (I, 6) sum exactly one pair for
+    every I: runs of 8 one-pair leaves per B leaf (two full groups of 4),
+    next to leaves of one, two and more pairs elsewhere."""
+    n, b, g = 256, 32, 8
+    rng = np.random.default_rng(65 + int(scaled))
+    pa = {(i, j) for i in range(g) for j in range(g) if rng.random() < 0.3} | \
+        {(i, 3) for i in range(g)}
+    pb = {(i, j) for i in range(g) for j in range(g)
+          if rng.random() < 0.3 and j not in (1, 5, 6)} | {(3, 1), (3, 5), (3, 6)}
+
+    def build(keys, dist):
+        keys = sorted(keys)
+        vals = (rng.standard_normal((len(keys), b, b)) if dist == "normal"
+                else rng.uniform(-1, 1, (len(keys), b, b)))
+        return w.BlockMatrix(n, b, np.array([k[0] for k in keys], np.int32),
+                             np.array([k[1] for k in keys], np.int32), vals)
+
+    a, bm = build(pa, "normal"), build(pb, "uniform")
+    if scaled:  # rows of A and columns of B over a wide exponent range
+        sr, sc = rng.integers(-60, 61, size=n), rng.integers(-60, 61, size=n)
+        for i in range(a.nblocks):
+            r0 = int(a.brow[i]) * b
+            a.vals[i] = np.ldexp(a.vals[i], sr[r0:r0 + b][:, None])
+        for i in range(bm.nblocks):
+            c0 = int(bm.bcol[i]) * b
+            bm.vals[i] = np.ldexp(bm.vals[i], sc[c0:c0 + b][None, :])
+    return a, bm
+
+
+@pytest.mark.parametrize("scaled", [False, True])
+def test_split_one_pair_leaves(lib, scaled):
+    # C leaves that sum exactly one leaf pair go to the kernel that groups
+    # them by B leaf (up to 4 per MMA), the others to the general kernel.
+    # Each against the exact emulation of its own slice pairs, the one-pair
+    # leaves to within the final rounding; then the same product with the
+    # grouping switched off (general kernel only) against its own pairs.
+    n, b = 256, 32
+    a, bm = _one_pair_case(scaled)
+    A, B = gu.upload(lib, a), gu.upload(lib, bm)
+    plan = lib.cht_symbolic_multiply(A, B)
+    seg = np.diff(plan.arrays()["cseg"].numpy())
+    assert (seg == 1).sum() >= 24 and (seg >= 2).sum() > 0
+    ad, bd = a.to_dense(), bm.to_dense()
+    mask = _dense_on(lib.cht_multiply(plan, A, B, sync=True)[0], n) != 0
+    for single in (1, 0):
+        lib.set_option(lib.OPT_SPLIT_SINGLE, single)
+        try:
+            C, _ = lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
+            emu, e, f, one = _emulate(lib, plan, ad, bd, b, n)
+        finally:
+            lib.set_option(lib.OPT_SPLIT_SINGLE, 1)
+        assert (one is not None) == bool(single)
+        got = _dense_on(C, n)
+        scale = np.ldexp(1.0, (e[:, None] + f[None, :]).astype(np.int64))
+        tol = scale * float(n) ** 2 * 2.0 ** -54 + 2 * np.spacing(np.abs(emu))
+        if one is not None:
+            # exact up to the final rounding: the emulation's own result
+            tol = np.where(one, 2 * np.spacing(np.abs(emu)), tol)
+        diff = np.abs(got - emu)
+        assert np.all(diff[mask] <= tol[mask]), (single, float((diff / tol).max()))
+        assert np.all(got[~mask] == 0)
+        ref = ad @ bd
+        assert np.all(np.abs(got - ref) <= sp.error_bound(ad, bd, S, W)
+                      + 2 * np.spacing(np.abs(ref)))
+    lib.sync_status()

@@ -1,8 +1,8 @@
 """The split kernel's barrier protocol, replayed on the host under random
 schedules (tests/split_protocol.py): no deadlock, no phase aliasing and no
 reuse race for random unit sequences (one or many exact windows per unit,
-mixed leaf sizes), in both kernel configurations; each planted protocol
-mistake is caught."""
+mixed leaf sizes), in both kernel configurations, and for the kernel of
+one-pair C leaves; each planted protocol mistake is caught."""
 
 from __future__ import annotations
 
@@ -101,6 +101,58 @@ def test_missing_drain_is_caught(mistake):
         role = ("mma", "producer", "epi2")[seed % 3]
         try:
             sp.run(cfg, units, seed, mistakes=frozenset([mistake]), timeout=(role, seed % 7))
+        except sp.ProtocolError:
+            caught += 1
+    assert caught > 0
+
+
+# ---------------------------------------------- the one-pair C leaf kernel --
+
+def _groups(seed: int):
+    rng = random.Random(seed)
+    return [rng.randint(1, 4) for _ in range(rng.randint(0, 11))]
+
+
+def test_one_pair_protocol_holds_under_random_schedules():
+    for seed in range(120):
+        sp.run(sp.ONE_PAIR, _groups(seed), seed)
+
+
+@pytest.mark.parametrize("mistake", ["mma_skips_unit_wait", "epi_releases_before_last_region",
+                                     "producer_skips_empty_wait", "epi_skips_slot_release",
+                                     "epi_single_accumulator_set"])
+def test_one_pair_planted_mistakes_are_caught(mistake):
+    groups = [4, 1, 3, 4, 2, 4, 4, 1, 4]
+    caught = 0
+    for seed in range(300):
+        try:
+            sp.run(sp.ONE_PAIR, groups, seed, mistakes=frozenset([mistake]))
+        except sp.ProtocolError:
+            caught += 1
+    assert caught > 0, mistake
+
+
+def test_one_pair_timeouts_end_cleanly():
+    rng = random.Random(12)
+    aborted = 0
+    for seed in range(80):
+        role = rng.choice(["producer", "mma", "epi0", "epi6"])
+        st = sp.run(sp.ONE_PAIR, _groups(seed) + [4, 4, 4], seed,
+                    timeout=(role, rng.randint(0, 10)))
+        if st.abort:
+            aborted += 1
+            assert st.status_timeout
+    assert aborted >= 20
+
+
+@pytest.mark.parametrize("mistake", ["producer_no_drain", "mma_no_drain"])
+def test_one_pair_missing_drain_is_caught(mistake):
+    caught = 0
+    for seed in range(200):
+        role = ("mma", "producer", "epi2")[seed % 3]
+        try:
+            sp.run(sp.ONE_PAIR, [4, 3, 4, 4, 2, 4], seed, mistakes=frozenset([mistake]),
+                   timeout=(role, seed % 7))
         except sp.ProtocolError:
             caught += 1
     assert caught > 0
