@@ -103,6 +103,21 @@ __device__ inline void bulk_g2s(void *dst_smem, const void *src, uint32_t bytes,
       : "memory");
 }
 
+// ------------------------------------------------- 16-byte async copies --
+// One 16-byte global -> shared copy (cp.async, cached in L2 only).  Both
+// addresses 16-byte aligned.
+__device__ inline void cp_async16(void *dst_smem, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst_smem)), "l"(src)
+               : "memory");
+}
+// An arrival on `bar` once every cp.async this thread issued so far has
+// landed; the barrier's expected count must include it (.noinc).
+__device__ inline void cp_async_arrive_noinc(uint64_t *bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // ------------------------------------------------------------- FP64 DMMA --
 // D (8x8) += A (8x4, row) * B (4x8, col), FP64 tensor-core MMA.
 // Lane l holds A[l/4][l%4], B[l%4][l/4], D[l/4][2*(l%4) + {0, 1}].

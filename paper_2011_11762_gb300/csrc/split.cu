@@ -168,6 +168,17 @@ __device__ inline void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ inline void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 template <int E>
 __device__ inline void tmem_ld(uint32_t taddr, float (&v)[E]);
 template <>
@@ -361,6 +372,31 @@ __device__ inline double scaled_i64_to_double(long long v, int e2) {
   if (biased <= 0 || biased >= 2047) return ldexp(static_cast<double>(v), e2);
   return __longlong_as_double(static_cast<long long>(
       sgn | (static_cast<unsigned long long>(biased) << 52) | (mant & ((1ULL << 52) - 1))));
+}
+
+// The same rounding without branches (selects only), so that a thread's
+// independent conversions interleave; *ok is false when the result would
+// leave the normal range of doubles, and the caller then uses
+// scaled_i64_to_double.  |v| < 2^63; the result is bit for bit the same.
+__device__ __forceinline__ double scaled_i64_fast(long long v, int e2, bool *ok) {
+  const unsigned long long sgn = static_cast<unsigned long long>(v) & (1ULL << 63);
+  const unsigned long long m = v < 0 ? 0ULL - static_cast<unsigned long long>(v)
+                                     : static_cast<unsigned long long>(v);
+  int top = 63 - __clzll(static_cast<long long>(m));  // -1 for m == 0
+  const int sh = top - 52;
+  const int shr = sh > 0 ? sh : 0, shl = sh < 0 ? -sh : 0;
+  unsigned long long mant = (m >> shr) << (shl < 63 ? shl : 63);
+  const unsigned long long rem = m & ((1ULL << shr) - 1ULL), half = (1ULL << shr) >> 1;
+  const bool up = shr > 0 && (rem > half || (rem == half && (mant & 1ULL)));
+  mant += up ? 1ULL : 0ULL;
+  const bool carry = (mant >> 53) != 0;
+  mant = carry ? mant >> 1 : mant;
+  top += carry ? 1 : 0;
+  const int biased = top + e2 + 1023;
+  *ok = m == 0 || (biased > 0 && biased < 2047);
+  const long long bits = static_cast<long long>(
+      sgn | (static_cast<unsigned long long>(biased & 0x7ff) << 52) | (mant & ((1ULL << 52) - 1)));
+  return m == 0 ? 0.0 : __longlong_as_double(bits);
 }
 
 // ------------------------------------------------------------ pre-kernels --
@@ -815,17 +851,37 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
       const int er = sl.rexp[row];
       const int cb = c0 + (part == 0 ? 0 : H);
       double *dst = sl.C + static_cast<int64_t>(row) * B + cb;
+      constexpr int CK = 8;  // elements converted together
 #pragma unroll
-      for (int cc = 0; cc < H; cc += 2) {
-        const long long v0 = part == 0 ? part_value(cc) : part_value(H + cc);
-        const long long v1 = part == 0 ? part_value(cc + 1) : part_value(H + cc + 1);
-        const long long t0 = v0 + xb[(cb + cc) * B + row];
-        const long long t1 = v1 + xb[(cb + cc + 1) * B + row];
-        const int f0 = sl.cexp[cb + cc], f1 = sl.cexp[cb + cc + 1];
-        double2 out;
-        out.x = (er == kNoExp16 || f0 == kNoExp16) ? 0.0 : scaled_i64_to_double(t0, er + f0 - 48);
-        out.y = (er == kNoExp16 || f1 == kNoExp16) ? 0.0 : scaled_i64_to_double(t1, er + f1 - 48);
-        *reinterpret_cast<double2 *>(dst + cc) = out;
+      for (int c8 = 0; c8 < H; c8 += CK) {
+        long long tv[CK];
+        double ov[CK];
+        bool good = true;
+#pragma unroll
+        for (int k = 0; k < CK; ++k) {
+          const int cc = c8 + k;
+          const long long v = part == 0 ? part_value(cc) : part_value(H + cc);
+          tv[k] = v + xb[(cb + cc) * B + row];
+          const int f = sl.cexp[cb + cc];
+          bool ok;
+          const double x = scaled_i64_fast(tv[k], er + f - 48, &ok);
+          const bool none = er == kNoExp16 || f == kNoExp16;
+          good = good && (ok || none);
+          ov[k] = none ? 0.0 : x;
+        }
+        if (!__all_sync(0xffffffffu, good)) {
+          // a result outside the normal range of doubles (rare): the exact
+          // general conversion
+#pragma unroll
+          for (int k = 0; k < CK; ++k) {
+            const int f = sl.cexp[cb + c8 + k];
+            ov[k] = (er == kNoExp16 || f == kNoExp16) ? 0.0
+                                                      : scaled_i64_to_double(tv[k], er + f - 48);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < CK; k += 2)
+          *reinterpret_cast<double2 *>(dst + c8 + k) = make_double2(ov[k], ov[k + 1]);
       }
     } else {
       // every part into the buffer, then all 256 threads convert 4 elements
@@ -841,13 +897,29 @@ __device__ bool epi_unit(const Slot &sl, uint32_t &win, uint32_t &epb, int64_t *
       const int r = et % B, col = (et / B) * 4;
       const int er = sl.rexp[r];
       double o4[4];
+      long long t4[4];
+      bool good = true;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         long long t = 0;
 #pragma unroll
         for (int p = 0; p < PARTS; ++p) t += xb[(static_cast<int64_t>(p) * B + col + j) * B + r];
+        t4[j] = t;
         const int f = sl.cexp[col + j];
-        o4[j] = (er == kNoExp16 || f == kNoExp16) ? 0.0 : scaled_i64_to_double(t, er + f - 48);
+        bool ok;
+        const double x = scaled_i64_fast(t, er + f - 48, &ok);
+        const bool none = er == kNoExp16 || f == kNoExp16;
+        good = good && (ok || none);
+        o4[j] = none ? 0.0 : x;
+      }
+      if (!__all_sync(0xffffffffu, good)) {
+        // a result outside the normal range of doubles (rare)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int f = sl.cexp[col + j];
+          o4[j] = (er == kNoExp16 || f == kNoExp16) ? 0.0
+                                                    : scaled_i64_to_double(t4[j], er + f - 48);
+        }
       }
       double *dst = sl.C + static_cast<int64_t>(r) * B + col;
       *reinterpret_cast<double2 *>(dst) = make_double2(o4[0], o4[1]);
@@ -1219,12 +1291,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 // 8-digit slices of the 32-leaf path (digits 1..6 here), B its 6 digits.
 //
 // Roles as in k_split_gemm: warp 0 producer (groups taken 8 at a time from a
-// device counter; per group one bulk copy of the B leaf's 6 slice tiles and
-// one per A tile), warp 1 MMA issuer (one thread), warps 2..9 epilogue (two
-// warps per lane quarter, 16 columns each).  Two accumulator sets of 192
-// columns: the MMAs of group n + 1 run while the epilogue reads group n; the
-// epilogue reads the six regions, releases its set, then assembles and
-// stores.  Every wait is bounded.
+// device counter; per group one bulk copy of the B leaf's 6 slice tiles, and
+// the 24 A tiles -- which land in [slice][unit] order, so no single bulk copy
+// can fetch a unit's six -- as 16-byte cp.async copies spread over the 32
+// lanes), warp 1 MMA issuer (one thread), warps 2..17 epilogue (four warps per
+// lane quarter, 8 columns each: the epilogue's integer assembly and
+// conversion set the pace, and four warps per scheduler hide their
+// latencies).  Two accumulator sets of 192 columns: the MMAs of group n + 1
+// run while the epilogue reads group n; the epilogue reads the six regions in
+// one round trip, releases its set, then assembles, converts and stores
+// (through a per-warp staging block, as whole row pieces).  Every wait is
+// bounded.
 namespace single32 {
 constexpr int kStages = 3;
 constexpr int kTile = Smem<32>::TILE;                 // 2 KB
@@ -1234,6 +1311,14 @@ constexpr int kB = kSB * kTile;                       // 12 KB
 constexpr int kStage = kA + kB;
 constexpr int kRegionsS = 6;                          // diagonals 2..7
 constexpr int kSetCols = 256;                         // accumulator set pitch (192 used)
+// 16 epilogue warps (four per TMEM lane quarter, 8 columns each): 18 warps
+constexpr int kEpi = 16;
+constexpr int kThreadsS = (2 + kEpi) * 32;
+constexpr int kCols = 32 / (kEpi / 4);                // columns per epilogue warp
+// per epilogue warp: its 32 x 8 block of C values, rows padded to 9 doubles
+// (few bank conflicts), for stores of whole 64-byte row pieces
+constexpr int kStgPitch = kCols + 1;
+constexpr int kStgBytes = 32 * kStgPitch * 8;
 constexpr int kChunk = 8;                             // groups per counter step
 constexpr int kNPairs = 21;
 // the pairs (i, j), i + j <= 7, diagonal by diagonal (t = 2, 3, ..., 7)
@@ -1269,12 +1354,12 @@ struct alignas(16) GSlot {
 
 constexpr size_t single32_smem() {
   return static_cast<size_t>(single32::kStages) * single32::kStage + kQueue * sizeof(GSlot) +
-         256 + 1024;
+         single32::kEpi * single32::kStgBytes + 256 + 1024;
 }
 
 // Group u is group u of `single` (works NULL), or, in a batch, group
 // gunits[u] & 0xffffffff of product gunits[u] >> 32 (works[product]).
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(single32::kThreadsS, 1)
     k_split_single32(const SingleWork single, const SingleWork *__restrict__ works,
                      int32_t nworks, const int64_t *__restrict__ gunits, int64_t ntotal,
                      unsigned long long *__restrict__ next_group, int *__restrict__ status,
@@ -1286,7 +1371,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t raw_addr = smem_addr(smem_raw);
   uint8_t *smem = smem_raw + ((1024 - (raw_addr & 1023)) & 1023);
   uint8_t *stage_base = smem;
-  GSlot *queue = reinterpret_cast<GSlot *>(smem + S * kStage);
+  double *staging = reinterpret_cast<double *>(smem + S * kStage);  // [kEpi][32][kStgPitch]
+  GSlot *queue = reinterpret_cast<GSlot *>(smem + S * kStage + kEpi * kStgBytes);
   uint64_t *bars = reinterpret_cast<uint64_t *>(queue + kQueue);
   uint64_t *full = bars, *empty = bars + S, *qfull = bars + 2 * S, *qempty = qfull + kQueue;
   uint64_t *acc_full = qempty + kQueue, *acc_empty = acc_full + 2, *drain = acc_full + 4;
@@ -1296,16 +1382,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int st = 0; st < S; ++st) {
-      mbar_init(&full[st], 1);
+      // the B copy's expect_tx arrival and one cp.async arrival per lane
+      mbar_init(&full[st], 1 + 32);
       mbar_init(&empty[st], 1);
     }
     for (int i = 0; i < kQueue; ++i) {
       mbar_init(&qfull[i], 1);
-      mbar_init(&qempty[i], 1 + kEpiWarps);
+      mbar_init(&qempty[i], 1 + kEpi);
     }
     for (int bf = 0; bf < 2; ++bf) {
       mbar_init(&acc_full[bf], 1);
-      mbar_init(&acc_empty[bf], kEpiWarps);
+      mbar_init(&acc_empty[bf], kEpi);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -1433,23 +1520,30 @@ __global__ void __launch_bounds__(kThreads, 1)
           done = true;
           break;
         }
-        if (lane == 0)
-          mbar_arrive_expect_tx(&full[st], static_cast<uint32_t>(kB + count * kASlices * kTile));
-        __syncwarp();
         uint8_t *sa = stage_base + st * kStage;
-        if (lane < 4 * kASlices) {
-          const int q = lane / kASlices, i = lane % kASlices;
-          if (gc[q] >= 0)
-            bulk_g2s(sa + (i * 4 + q) * kTile,
-                     a_slices + (static_cast<int64_t>(ga[q]) * Cfg<32>::SA + i) * kTile,
-                     static_cast<uint32_t>(kTile), &full[st]);
-        } else if (lane == 4 * kASlices) {
+        if (lane == 0) {
+          mbar_arrive_expect_tx(&full[st], static_cast<uint32_t>(kB));
           bulk_g2s(sa + kA, b_slices + static_cast<int64_t>(gbv) * kB, static_cast<uint32_t>(kB),
                    &full[st]);
         }
+        // A tile (unit q, slice i) -> sa + (i * 4 + q) tiles; lane l copies
+        // 16-byte chunks l, l + 32, .. of every tile (coalesced)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (gc[q] < 0) continue;
+          const uint8_t *src = a_slices + static_cast<int64_t>(ga[q]) * Cfg<32>::SA * kTile;
+#pragma unroll
+          for (int i = 0; i < kASlices; ++i)
+#pragma unroll
+            for (int c = lane; c < kTile / 16; c += 32)
+              cp_async16(sa + (i * 4 + q) * kTile + c * 16, src + i * kTile + c * 16);
+        }
+        cp_async_arrive_noinc(&full[st]);  // when this lane's copies have landed
         ++n;
       }
     }
+    // copies in flight land before shared memory goes away
+    cp_async_wait_all();
     if (lane == 0) {
       for (uint32_t j = (n >= S ? n - S : 0); j < n; ++j)
         mbar_wait_bounded(&full[j % S], (j / S) & 1u, kDrainNs);
@@ -1479,6 +1573,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           fail();
           break;
         }
+        // the A tiles came through the generic proxy (cp.async): order them
+        // before the tensor core's (async proxy) reads
+        fence_proxy_async_smem();
         tc_fence_after();
         const uint32_t sa = smem_addr(stage_base + st * kStage), sb = sa + kA;
         const uint32_t set = tmem + bf * kSetCols;
@@ -1501,8 +1598,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // -------------------------------------------------------- epilogue --
-    const int q = warp & 3;                 // lane quarter = unit of the group
-    const int c0 = (warp >= 6) ? 16 : 0;    // this warp's 16 columns
+    const int q = warp & 3;                     // lane quarter = unit of the group
+    const int c0 = ((warp - 2) >> 2) * kCols;   // this warp's kCols columns
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * q) << 16);
     for (uint32_t n = 0;; ++n) {
       const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
@@ -1515,47 +1612,65 @@ __global__ void __launch_bounds__(kThreads, 1)
       double *Cq = sl.C[q];
       // line exponents (loaded while the MMAs run)
       const int er = Cq ? sl.row_exp[static_cast<int64_t>(sl.crow[q]) * 32 + lane] : kNoExp;
-      int fc[16];
+      int fc[kCols];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) fc[c] = sl.col_exp[static_cast<int64_t>(sl.ccol) * 32 + c0 + c];
+      for (int c = 0; c < kCols; ++c)
+        fc[c] = sl.col_exp[static_cast<int64_t>(sl.ccol) * 32 + c0 + c];
       const uint32_t bf = n & 1u, use = n >> 1;
       if (!warp_wait_or_abort(&acc_full[bf], use & 1u, wait_ns, abort_flag)) {
         fail();
         break;
       }
       tc_fence_after();
-      // the six diagonals, most significant first: T <- 2^8 T + S_t
+      // the six diagonals, most significant first: T <- 2^8 T + S_t (all six
+      // regions in one TMEM round trip)
       const uint32_t base = lane_base + bf * kSetCols + c0;
-      long long T[16];
-      {
-        float v[16];
-        tmem_ld16(base, v);
-        tc_wait_ld();
+      float v[kRegionsS][kCols];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) T[c] = __float2int_rn(v[c]);
-      }
-#pragma unroll
-      for (int r = 1; r < kRegionsS; ++r) {
-        float v[16];
-        tmem_ld16(base + static_cast<uint32_t>(r * 32), v);
-        tc_wait_ld();
-#pragma unroll
-        for (int c = 0; c < 16; ++c) T[c] = T[c] * 256 + __float2int_rn(v[c]);
-      }
+      for (int r = 0; r < kRegionsS; ++r) tmem_ld8(base + static_cast<uint32_t>(r * 32), v[r]);
+      tc_wait_ld();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[bf]);  // the MMA may reuse this set
-      if (Cq) {
-        double *dst = Cq + lane * 32 + c0;
+      long long T[kCols];
 #pragma unroll
-        for (int c = 0; c < 16; c += 2) {
-          double2 o;
-          o.x = (er == kNoExp || fc[c] == kNoExp) ? 0.0 : scaled_i64_to_double(T[c], er + fc[c] - 56);
-          o.y = (er == kNoExp || fc[c + 1] == kNoExp)
-                    ? 0.0
-                    : scaled_i64_to_double(T[c + 1], er + fc[c + 1] - 56);
-          *reinterpret_cast<double2 *>(dst + c) = o;
+      for (int c = 0; c < kCols; ++c) {
+        long long t = __float2int_rn(v[0][c]);
+#pragma unroll
+        for (int r = 1; r < kRegionsS; ++r) t = t * 256 + __float2int_rn(v[r][c]);
+        T[c] = t;
+      }
+      if (Cq) {
+        // convert this lane's row (its own exponents), stage the warp's
+        // 32 x kCols block, and store it as row pieces of kCols doubles
+        double *stg = staging + (warp - 2) * 32 * kStgPitch;
+        bool good = true;
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) {
+          bool ok;
+          const double x = scaled_i64_fast(T[c], er + fc[c] - 56, &ok);
+          const bool none = er == kNoExp || fc[c] == kNoExp;
+          good = good && (ok || none);
+          stg[lane * kStgPitch + c] = none ? 0.0 : x;
         }
+        if (!__all_sync(0xffffffffu, good)) {
+          // a result outside the normal range of doubles somewhere in the
+          // warp (rare): the exact general conversion for this lane's row
+#pragma unroll
+          for (int c = 0; c < kCols; ++c)
+            stg[lane * kStgPitch + c] = (er == kNoExp || fc[c] == kNoExp)
+                                            ? 0.0
+                                            : scaled_i64_to_double(T[c], er + fc[c] - 56);
+        }
+        __syncwarp();
+        constexpr int kRowsPer = 32 / kCols;  // rows stored by one instruction
+        const int col = lane % kCols, sub = lane / kCols;
+#pragma unroll
+        for (int k = 0; k < 32 / kRowsPer; ++k) {
+          const int row = kRowsPer * k + sub;
+          Cq[row * 32 + c0 + col] = stg[row * kStgPitch + col];
+        }
+        __syncwarp();  // the staging block is read before the next group writes it
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&qempty[qs]);
@@ -1935,7 +2050,8 @@ int launch_single32(const SingleWork &w, const SingleWork *works, int32_t nworks
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem)));
   const int64_t grid = std::min<int64_t>((ntotal + single32::kChunk - 1) / single32::kChunk, sms);
-  k_split_single32<<<static_cast<unsigned>(std::max<int64_t>(grid, 1)), kThreads, smem, s>>>(
+  k_split_single32<<<static_cast<unsigned>(std::max<int64_t>(grid, 1)), single32::kThreadsS,
+                     smem, s>>>(
       w, works, nworks, gunits, ntotal, counter, status, g_opt.wait_budget_ns);
   return launched("split_single32");
 }

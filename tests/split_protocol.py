@@ -38,7 +38,9 @@ import random
 from dataclasses import dataclass, field
 
 QUEUE = 4        # unit queue slots
-EPI_WARPS = 8    # epilogue warps
+EPI_WARPS = 8    # epilogue warps of the general kernel
+EPI_WARPS_ONE_PAIR = 16  # epilogue warps of the one-pair kernel (four per lane quarter)
+LANES = 32       # producer lanes (one cp.async arrival each per stage fill)
 REGIONS = 3      # TMEM regions per accumulator set
 
 
@@ -347,17 +349,18 @@ def one_pair_roles(st: State, groups, mistakes=frozenset()):
     S = cfg.stages
     bars = st.bars
     for i in range(S):
-        bars[f"full{i}"] = Barrier(f"full{i}", 1)
+        # the B copy's expect_tx arrival and one cp.async arrival per lane
+        bars[f"full{i}"] = Barrier(f"full{i}", 1 + LANES)
         bars[f"empty{i}"] = Barrier(f"empty{i}", 1)
     for i in range(QUEUE):
         bars[f"qfull{i}"] = Barrier(f"qfull{i}", 1)
-        bars[f"qempty{i}"] = Barrier(f"qempty{i}", 1 + EPI_WARPS)
+        bars[f"qempty{i}"] = Barrier(f"qempty{i}", 1 + EPI_WARPS_ONE_PAIR)
     for bf in range(cfg.nb):
         bars[f"acc_full{bf}"] = Barrier(f"acc_full{bf}", 1)
-        bars[f"acc_empty{bf}"] = Barrier(f"acc_empty{bf}", EPI_WARPS)
+        bars[f"acc_empty{bf}"] = Barrier(f"acc_empty{bf}", EPI_WARPS_ONE_PAIR)
     bars["drain"] = Barrier("drain", 1)
-    everyone = frozenset(["mma"] + [f"epi{w}" for w in range(EPI_WARPS)])
-    warps = frozenset(f"epi{w}" for w in range(EPI_WARPS))
+    everyone = frozenset(["mma"] + [f"epi{w}" for w in range(EPI_WARPS_ONE_PAIR)])
+    warps = frozenset(f"epi{w}" for w in range(EPI_WARPS_ONE_PAIR))
     slots = {}
     ngroups = len(groups)
     nb = cfg.nb
@@ -395,8 +398,12 @@ def one_pair_roles(st: State, groups, mistakes=frozenset()):
                 raise ProtocolError(f"stage {s} refilled for group {n} while MMAs of "
                                     f"group {st.stage_busy[s]} still read it")
             st.stage_busy[s] = n
-            bars[f"full{s}"].arrive(expect_tx=count + 1)  # A tiles of each unit, the B leaf
-            st.copies.extend([(bars[f"full{s}"], 1)] * (count + 1))
+            # lane 0: the B leaf's bulk copy (expect_tx); every lane: its
+            # 16-byte A copies, then an arrival that fires once they land
+            bars[f"full{s}"].arrive(expect_tx=1)
+            st.copies.append((bars[f"full{s}"], 1))
+            lanes = LANES - 1 if "producer_one_lane_short" in mistakes else LANES
+            st.copies.extend([(bars[f"full{s}"], None)] * lanes)
             yield None
         staged = n if n < ngroups else ngroups
         if "producer_no_drain" not in mistakes:
@@ -474,7 +481,7 @@ def one_pair_roles(st: State, groups, mistakes=frozenset()):
             yield None
 
     roles = {"producer": producer(), "mma": mma()}
-    for wid in range(EPI_WARPS):
+    for wid in range(EPI_WARPS_ONE_PAIR):
         roles[f"epi{wid}"] = epilogue(wid)
     return roles
 
@@ -539,7 +546,10 @@ def run(cfg: Config, units, seed: int, mistakes=frozenset(), timeout=None,
         kind, name = rng.choice(choices)
         if kind == "copy":
             bar, nbytes = st.copies.pop(rng.randrange(len(st.copies)))
-            bar.complete_tx(nbytes)
+            if nbytes is None:
+                bar.arrive()  # a cp.async arrival: this lane's copies landed
+            else:
+                bar.complete_tx(nbytes)
         elif kind == "tensor":
             op = st.inflight.pop(0)  # MMAs and commits complete in issue order
             if op[0] == "commit":
