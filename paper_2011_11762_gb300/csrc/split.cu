@@ -374,29 +374,28 @@ __device__ inline double scaled_i64_to_double(long long v, int e2) {
       sgn | (static_cast<unsigned long long>(biased) << 52) | (mant & ((1ULL << 52) - 1))));
 }
 
-// The same rounding without branches (selects only), so that a thread's
-// independent conversions interleave; *ok is false when the result would
-// leave the normal range of doubles, and the caller then uses
-// scaled_i64_to_double.  |v| < 2^63; the result is bit for bit the same.
+// The same rounding without branches, in few integer operations (the FP64
+// pipe, which a double conversion or multiply would use, is narrow): |v| is
+// normalised so that its leading one sits at bit 63; bits 63..11 are the
+// 53-bit significand, bits 10..0 decide round-to-nearest-even, and adding the
+// significand (leading one included) to (exponent - 1) << 52 lets a rounding
+// carry move into the exponent.  *ok is false when the result could leave the
+// normal range of doubles, and the caller then uses scaled_i64_to_double.
+// |v| < 2^63; where *ok holds the result is bit for bit the same.
 __device__ __forceinline__ double scaled_i64_fast(long long v, int e2, bool *ok) {
-  const unsigned long long sgn = static_cast<unsigned long long>(v) & (1ULL << 63);
-  const unsigned long long m = v < 0 ? 0ULL - static_cast<unsigned long long>(v)
-                                     : static_cast<unsigned long long>(v);
-  int top = 63 - __clzll(static_cast<long long>(m));  // -1 for m == 0
-  const int sh = top - 52;
-  const int shr = sh > 0 ? sh : 0, shl = sh < 0 ? -sh : 0;
-  unsigned long long mant = (m >> shr) << (shl < 63 ? shl : 63);
-  const unsigned long long rem = m & ((1ULL << shr) - 1ULL), half = (1ULL << shr) >> 1;
-  const bool up = shr > 0 && (rem > half || (rem == half && (mant & 1ULL)));
-  mant += up ? 1ULL : 0ULL;
-  const bool carry = (mant >> 53) != 0;
-  mant = carry ? mant >> 1 : mant;
-  top += carry ? 1 : 0;
-  const int biased = top + e2 + 1023;
-  *ok = m == 0 || (biased > 0 && biased < 2047);
-  const long long bits = static_cast<long long>(
-      sgn | (static_cast<unsigned long long>(biased & 0x7ff) << 52) | (mant & ((1ULL << 52) - 1)));
-  return m == 0 ? 0.0 : __longlong_as_double(bits);
+  const unsigned long long s = static_cast<unsigned long long>(v >> 63);  // 0 or all ones
+  const unsigned long long m = (static_cast<unsigned long long>(v) ^ s) - s;
+  const int lz = __clzll(static_cast<long long>(m));  // 64 for m == 0
+  const unsigned long long nrm = m << (lz & 63);
+  const unsigned long long sig = nrm >> 11;
+  const unsigned int low = static_cast<unsigned int>(nrm) & 0x7ffu;
+  const unsigned int up = (low + (static_cast<unsigned int>(sig) & 1u) + 0x3ffu) >> 11;
+  const int biased = 1023 + 63 - lz + e2;  // before a rounding carry
+  *ok = m == 0 || (biased > 0 && biased < 2046);
+  const unsigned long long bits =
+      (static_cast<unsigned long long>(static_cast<unsigned int>(biased - 1) & 0x7ffu) << 52) +
+      sig + up;
+  return m == 0 ? 0.0 : __longlong_as_double(static_cast<long long>(bits | (s << 63)));
 }
 
 // ------------------------------------------------------------ pre-kernels --
@@ -1551,7 +1550,6 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------ MMA issuer --
     if (lane == 0) {
-      constexpr uint32_t IDESC = make_idesc(128, 32);
       for (uint32_t n = 0;; ++n) {
         const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
         if (!wait_or_abort(&qfull[qs], qph, wait_ns, abort_flag)) {
@@ -1579,16 +1577,20 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
         tc_fence_after();
         const uint32_t sa = smem_addr(stage_base + st * kStage), sb = sa + kA;
         const uint32_t set = tmem + bf * kSetCols;
+        // A digit i meets B digits 1..7-i: the B slice tiles lie one after
+        // the other (32 rows each, the same 8-row group stride), so one MMA
+        // of N = 32 (7 - i) rows of B covers them, writing regions i - 1..5
+        // (columns 32 (i - 1) on); digit 1's MMA covers all six regions and
+        // starts them
+        const uint64_t bd = sw64_desc(sb);
 #pragma unroll
-        for (int x = 0; x < kNPairs; ++x) {
-          const int t = pair_t(x), i = pair_i(x), j = t - i;
-          const bool first = x == 0 || pair_t(x - 1) != t;  // first pair of its diagonal
+        for (int i = 1; i <= kASlices; ++i) {
+          const uint32_t idesc = make_idesc(128, 32 * (7 - i));
           const uint64_t ad = sw64_desc(sa + (i - 1) * 4 * kTile);
-          const uint64_t bd = sw64_desc(sb + (j - 1) * kTile);
-          const uint32_t dt = set + static_cast<uint32_t>((t - 2) * 32);
+          const uint32_t dt = set + static_cast<uint32_t>((i - 1) * 32);
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk)
-            tc_mma(dt, ad + 2 * kk, bd + 2 * kk, IDESC, (first && kk == 0) ? 0u : 1u);
+            tc_mma(dt, ad + 2 * kk, bd + 2 * kk, idesc, (i == 1 && kk == 0) ? 0u : 1u);
         }
         tc_commit(&empty[st]);  // the stage is free when these MMAs finish
         tc_commit(&acc_full[bf]);
@@ -1632,13 +1634,22 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[bf]);  // the MMA may reuse this set
+      // a region holds an integer of magnitude below 2^22: adding 1.5 * 2^23
+      // moves it, exactly, into [2^23, 2^24), where the float's bit pattern
+      // is 0x4B400000 plus the integer (no float-to-integer conversion); two
+      // regions combine in 32 bits (S_t 2^8 + S_t+1 < 2^31 in magnitude) and
+      // the three pairs in 64: T = P_0 2^32 + P_1 2^16 + P_2
       long long T[kCols];
 #pragma unroll
       for (int c = 0; c < kCols; ++c) {
-        long long t = __float2int_rn(v[0][c]);
+        uint32_t u[kRegionsS];
 #pragma unroll
-        for (int r = 1; r < kRegionsS; ++r) t = t * 256 + __float2int_rn(v[r][c]);
-        T[c] = t;
+        for (int r = 0; r < kRegionsS; ++r) u[r] = __float_as_uint(v[r][c] + 12582912.0f);
+        constexpr uint32_t kBias = 257u * 0x4B400000u;  // both offsets of a pair
+        const int p0 = static_cast<int>(u[0] * 256u + u[1] - kBias);
+        const int p1 = static_cast<int>(u[2] * 256u + u[3] - kBias);
+        const int p2 = static_cast<int>(u[4] * 256u + u[5] - kBias);
+        T[c] = static_cast<long long>(p0) * 0x100000000LL + static_cast<long long>(p1) * 0x10000LL + p2;
       }
       if (Cq) {
         // convert this lane's row (its own exponents), stage the warp's
