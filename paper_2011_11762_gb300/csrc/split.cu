@@ -374,28 +374,36 @@ __device__ inline double scaled_i64_to_double(long long v, int e2) {
       sgn | (static_cast<unsigned long long>(biased) << 52) | (mant & ((1ULL << 52) - 1))));
 }
 
-// The same rounding without branches, in few integer operations (the FP64
-// pipe, which a double conversion or multiply would use, is narrow): |v| is
-// normalised so that its leading one sits at bit 63; bits 63..11 are the
-// 53-bit significand, bits 10..0 decide round-to-nearest-even, and adding the
-// significand (leading one included) to (exponent - 1) << 52 lets a rounding
-// carry move into the exponent.  *ok is false when the result could leave the
-// normal range of doubles, and the caller then uses scaled_i64_to_double.
-// |v| < 2^63; where *ok holds the result is bit for bit the same.
+// The same rounding without branches, in few 32-bit integer operations (the
+// FP64 pipe, which a double conversion or multiply would use, is narrow).
+// |v| is normalised so that its leading one sits at bit 63 of the word pair
+// (hi, lo) -- from the high word when it is non-zero, else from the low one
+// -- so that hi and the top 21 bits of lo are the 53-bit significand and the
+// low 11 bits of lo decide round-to-nearest-even; adding the significand
+// (leading one included) to (exponent - 1) << 52 lets a rounding carry move
+// into the exponent.  *ok is false when the result could leave the normal
+// range of doubles, and the caller then uses scaled_i64_to_double.  |v| <
+// 2^63; v == 0 gives +0 with *ok true (e2 unused); where *ok holds the result
+// is bit for bit that of scaled_i64_to_double.
 __device__ __forceinline__ double scaled_i64_fast(long long v, int e2, bool *ok) {
   const unsigned long long s = static_cast<unsigned long long>(v >> 63);  // 0 or all ones
   const unsigned long long m = (static_cast<unsigned long long>(v) ^ s) - s;
-  const int lz = __clzll(static_cast<long long>(m));  // 64 for m == 0
-  const unsigned long long nrm = m << (lz & 63);
-  const unsigned long long sig = nrm >> 11;
-  const unsigned int low = static_cast<unsigned int>(nrm) & 0x7ffu;
-  const unsigned int up = (low + (static_cast<unsigned int>(sig) & 1u) + 0x3ffu) >> 11;
-  const int biased = 1023 + 63 - lz + e2;  // before a rounding carry
-  *ok = m == 0 || (biased > 0 && biased < 2046);
+  const uint32_t mh = static_cast<uint32_t>(m >> 32), ml = static_cast<uint32_t>(m);
+  const bool big = mh != 0;
+  const uint32_t wh = big ? mh : ml, wl = big ? ml : 0u;
+  const int lz = __clz(static_cast<int>(wh));  // 32 when v == 0
+  const uint32_t nh = __funnelshift_l(wl, wh, lz), nl = wl << (lz & 31);
+  const uint32_t sig_h = nh >> 11, sig_l = __funnelshift_r(nl, nh, 11);
+  const uint32_t up = ((nl & 0x7ffu) + (sig_l & 1u) + 0x3ffu) >> 11;
+  // exponent field before a rounding carry (unsigned: e2 may be a sentinel
+  // when v == 0)
+  const uint32_t biased = static_cast<uint32_t>(e2) + (big ? 1086u : 1054u) -
+                          static_cast<uint32_t>(lz);
+  *ok = wh == 0 || biased - 1u < 2045u;
+  const unsigned long long sig = (static_cast<unsigned long long>(sig_h) << 32) | sig_l;
   const unsigned long long bits =
-      (static_cast<unsigned long long>(static_cast<unsigned int>(biased - 1) & 0x7ffu) << 52) +
-      sig + up;
-  return m == 0 ? 0.0 : __longlong_as_double(static_cast<long long>(bits | (s << 63)));
+      (static_cast<unsigned long long>((biased - 1u) & 0x7ffu) << 52) + sig + up;
+  return wh == 0 ? 0.0 : __longlong_as_double(static_cast<long long>(bits | (s << 63)));
 }
 
 // ------------------------------------------------------------ pre-kernels --
@@ -1654,24 +1662,26 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
       if (Cq) {
         // convert this lane's row (its own exponents), stage the warp's
         // 32 x kCols block, and store it as row pieces of kCols doubles
+        // (a line without stored values -- exponent kNoExp -- has zero
+        // digits, so T = 0 there and converts to +0 whatever the exponent)
         double *stg = staging + (warp - 2) * 32 * kStgPitch;
+        const uint32_t eb = static_cast<uint32_t>(er) - 56u;
         bool good = true;
 #pragma unroll
         for (int c = 0; c < kCols; ++c) {
           bool ok;
-          const double x = scaled_i64_fast(T[c], er + fc[c] - 56, &ok);
-          const bool none = er == kNoExp || fc[c] == kNoExp;
-          good = good && (ok || none);
-          stg[lane * kStgPitch + c] = none ? 0.0 : x;
+          const double x =
+              scaled_i64_fast(T[c], static_cast<int>(eb + static_cast<uint32_t>(fc[c])), &ok);
+          good = good && ok;
+          stg[lane * kStgPitch + c] = x;
         }
         if (!__all_sync(0xffffffffu, good)) {
           // a result outside the normal range of doubles somewhere in the
           // warp (rare): the exact general conversion for this lane's row
 #pragma unroll
           for (int c = 0; c < kCols; ++c)
-            stg[lane * kStgPitch + c] = (er == kNoExp || fc[c] == kNoExp)
-                                            ? 0.0
-                                            : scaled_i64_to_double(T[c], er + fc[c] - 56);
+            stg[lane * kStgPitch + c] = scaled_i64_to_double(
+                T[c], static_cast<int>(eb + static_cast<uint32_t>(fc[c])));
         }
         __syncwarp();
         constexpr int kRowsPer = 32 / kCols;  // rows stored by one instruction
