@@ -44,6 +44,20 @@ __global__ void k_dup_and_zero(const uint64_t *__restrict__ skeys, const int32_t
   }
 }
 
+__global__ void k_leaf_counts(const uint64_t *__restrict__ key, const int32_t *__restrict__ keep,
+                              int64_t n, int64_t G, int32_t *__restrict__ rowcnt,
+                              int32_t *__restrict__ colcnt) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (keep && !keep[i]) continue;
+    const uint32_t r = morton_row(key[i]), c = morton_col(key[i]);
+    if (r < G && c < G) {
+      atomicAdd(&rowcnt[r], 1);
+      atomicAdd(&colcnt[c], 1);
+    }
+  }
+}
+
 __global__ void k_compact(const uint64_t *__restrict__ skeys, const int32_t *__restrict__ sidx,
                           const int32_t *__restrict__ keep, const int64_t *__restrict__ pos,
                           const double *__restrict__ vin, int64_t n, int bb,
@@ -293,10 +307,27 @@ int build_matrix(int64_t n, int32_t b, int64_t nblocks, const int32_t *d_brow,
     CHT_TRY(launched("dup_and_zero"));
   }
   CHT_TRY(scan_exclusive(keep.p, pos.p, nblocks, s));
+  // leaf counts per row and column, read in the same synchronisation
+  const int64_t G = pat->G;
+  const bool counts = G <= kMaxCountG;
+  DevArray<int32_t> cnts;
+  if (counts) {
+    CHT_TRY(cnts.alloc(2 * G, s));
+    CHT_CUDA_TRY(cudaMemsetAsync(cnts.p, 0, sizeof(int32_t) * 2 * G, s));
+    CHT_TRY(count_leaves(skeys.p, keep.p, nblocks, G, cnts.p, cnts.p + G, s));
+    pat->rowcnt.resize(G);
+    pat->colcnt.resize(G);
+  }
   int herr = 0;
   int64_t nkeep = 0;
   CHT_CUDA_TRY(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   CHT_CUDA_TRY(cudaMemcpyAsync(&nkeep, pos.p + nblocks, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  if (counts) {
+    CHT_CUDA_TRY(cudaMemcpyAsync(pat->rowcnt.data(), cnts.p, sizeof(int32_t) * G,
+                                 cudaMemcpyDeviceToHost, s));
+    CHT_CUDA_TRY(cudaMemcpyAsync(pat->colcnt.data(), cnts.p + G, sizeof(int32_t) * G,
+                                 cudaMemcpyDeviceToHost, s));
+  }
   CHT_CUDA_TRY(cudaStreamSynchronize(s));
   if (herr & 1) {
     set_error("leaf coordinate outside the %lld x %lld leaf grid", (long long)pat->G,
@@ -320,6 +351,13 @@ int build_matrix(int64_t n, int32_t b, int64_t nblocks, const int32_t *d_brow,
   m->pat = std::move(pat);
   *out = m.release();
   return CHT_OK;
+}
+
+int count_leaves(const uint64_t *key, const int32_t *keep, int64_t n, int64_t G,
+                 int32_t *rowcnt, int32_t *colcnt, cudaStream_t s) {
+  if (n <= 0) return CHT_OK;
+  k_leaf_counts<<<grid_for(n, 256), 256, 0, s>>>(key, keep, n, G, rowcnt, colcnt);
+  return launched("leaf_counts");
 }
 
 int same_leaves(const Pattern &x, const Pattern &y, int *d_flag, cudaStream_t s, bool *same) {

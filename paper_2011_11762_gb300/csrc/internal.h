@@ -127,6 +127,11 @@ struct Pattern {
   mutable bool have_rows = false;
   mutable cudaEvent_t rows_ready = nullptr;  // recorded after the index build
   mutable std::mutex rows_mutex;
+  // stored leaves per leaf row and per leaf column, on the host ([G] each;
+  // empty when not known, e.g. G > kMaxCountG): read in the synchronisation
+  // that sized the pattern, they let the symbolic phase size a product's
+  // pair list without one
+  std::vector<int32_t> rowcnt, colcnt;
   Pattern() = default;
   Pattern(const Pattern &) = delete;
   Pattern &operator=(const Pattern &) = delete;
@@ -134,6 +139,13 @@ struct Pattern {
 };
 uint64_t next_id();
 int bits_for(int64_t G);
+// Largest leaf grid side for which patterns keep host leaf counts.
+constexpr int64_t kMaxCountG = 1 << 16;
+// Adds the leaf counts per row and column of the n Morton keys key[i] with
+// keep[i] != 0 (keep null: all) into rowcnt and colcnt ([G] each, device);
+// keys outside the G x G grid are skipped.
+int count_leaves(const uint64_t *key, const int32_t *keep, int64_t n, int64_t G,
+                 int32_t *rowcnt, int32_t *colcnt, cudaStream_t s);
 // Fills brow/bcol from the sorted mkey.
 int build_pattern_index(Pattern &p, cudaStream_t s);
 // Makes p's row index available to work queued on s after this call: built
@@ -232,6 +244,9 @@ struct cht_plan {
   std::shared_ptr<cht::Pattern> C;   // product pattern
   int64_t npairs = 0;
   int64_t max_seg = 0;               // most pairs of any C leaf
+  // C leaves with exactly one pair, and their groups of up to four sharing
+  // a B leaf (read in the symbolic phase's synchronisation; -1: not known)
+  int64_t n_one = -1, n_groups = -1;
   cht::DevArray<int64_t> cseg;       // [nC + 1]
   cht::DevArray<int32_t> pa, pb, pc; // per pair (sorted by C leaf, then K)
   cht::DevArray<int32_t> order;      // schedule [nC]

@@ -2004,10 +2004,15 @@ int build_single_groups(const cht_plan *plan, const Pattern &pb_pat, cudaStream_
   }
   CHT_TRY(scan_exclusive(one.p, opos.p, nC, s));
   CHT_TRY(scan_exclusive(more.p, mpos.p, nC, s));
-  int64_t counts[2] = {0, 0};
-  CHT_CUDA_TRY(cudaMemcpyAsync(&counts[0], opos.p + nC, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CHT_CUDA_TRY(cudaMemcpyAsync(&counts[1], mpos.p + nC, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CHT_CUDA_TRY(cudaStreamSynchronize(s));
+  // the counts come from the symbolic phase's synchronisation when it
+  // counted them (32-leaf plans), else from one here
+  const bool known = plan->n_one >= 0 && plan->n_groups >= 0;
+  int64_t counts[2] = {plan->n_one, nC - plan->n_one};
+  if (!known) {
+    CHT_CUDA_TRY(cudaMemcpyAsync(&counts[0], opos.p + nC, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CHT_CUDA_TRY(cudaMemcpyAsync(&counts[1], mpos.p + nC, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CHT_CUDA_TRY(cudaStreamSynchronize(s));
+  }
   const int64_t nS = counts[0];
   g.nsingle = nS;
   g.nmore = counts[1];
@@ -2041,8 +2046,8 @@ int build_single_groups(const cht_plan *plan, const Pattern &pb_pat, cudaStream_
   k_group_starts<<<grid_for(nS, 256), 256, 0, s>>>(head.p, hx.p, start.p, nS, gs.p);
   CHT_TRY(launched("group_starts"));
   CHT_TRY(scan_exclusive(gs.p, gx.p, nS, s));
-  int64_t ng = 0;
-  CHT_TRY(read_i64(gx.p + nS, &ng, s));
+  int64_t ng = plan->n_groups;
+  if (!known) CHT_TRY(read_i64(gx.p + nS, &ng, s));
   g.ngroups = ng;
   CHT_TRY(g.gb.alloc(ng, s));
   CHT_TRY(g.ga.alloc(4 * ng, s));
@@ -2152,8 +2157,9 @@ int split_multiply(cht_plan *plan, cht_mat *A, cht_mat *B, int nslices, cudaStre
   *err_bound = static_cast<double>(plan->n) * (kSB + 3) * 0x1p-48 + 0x1p-50;
   const bool pieces = plan->max_seg > max_unit_pairs(b);
   const bool one_pair = b == 32 && !pieces && g_opt.split_single;
-  // the plan's one-pair groups first (their build synchronises, so it should
-  // not wait for the slicing pre-kernels)
+  // the plan's one-pair groups first (their build synchronises when the
+  // symbolic phase did not count them, and should then not wait for the
+  // slicing pre-kernels)
   const SingleGroups *groups = nullptr;
   if (one_pair) CHT_TRY(plan_groups(plan, *B->pat, s, &groups));
   Operands op;

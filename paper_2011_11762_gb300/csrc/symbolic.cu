@@ -33,7 +33,7 @@ __global__ void k_pair_fill(const int32_t *__restrict__ a_row, const int32_t *__
                             int64_t nA, const int64_t *__restrict__ off,
                             const int64_t *__restrict__ b_rowptr,
                             const int32_t *__restrict__ b_rowcol,
-                            const int32_t *__restrict__ b_rowleaf, int L,
+                            const int32_t *__restrict__ b_rowleaf, int L, int64_t P,
                             uint64_t *__restrict__ key, int32_t *__restrict__ pa,
                             int32_t *__restrict__ pb, int32_t *__restrict__ idx) {
   const int lane = threadIdx.x & 31;
@@ -46,6 +46,7 @@ __global__ void k_pair_fill(const int32_t *__restrict__ a_row, const int32_t *__
     const int64_t rs = b_rowptr[K];
     for (int64_t t = lane; t < cnt; t += 32) {
       const int64_t p = base + t;
+      if (p >= P) break;  // (only if the host count were short; checked later)
       const uint32_t J = static_cast<uint32_t>(b_rowcol[rs + t]);
       key[p] = (morton(I, J) << L) | K;
       pa[p] = static_cast<int32_t>(a);
@@ -103,15 +104,48 @@ __global__ void k_lpt_keys(const int64_t *__restrict__ seg, int64_t n, uint64_t 
   }
 }
 
-// Longest segment of the *d_n segments of seg (the count read on the device).
-__global__ void k_max_seg(const int64_t *__restrict__ seg, const int64_t *__restrict__ d_n,
-                          unsigned long long *__restrict__ out) {
+// Statistics of the *d_n C leaves (count read on the device): stats[0] = the
+// count, stats[1] = the longest segment, stats[2] = the C leaves of one pair;
+// with cntB, each such leaf counts on its B leaf; with rowcnt, every leaf
+// counts on its leaf row and column.
+__global__ void k_c_stats(const int64_t *__restrict__ seg, const uint64_t *__restrict__ ckey,
+                          const int64_t *__restrict__ d_n, const int32_t *__restrict__ pb,
+                          int32_t *__restrict__ cntB, int32_t *__restrict__ rowcnt,
+                          int32_t *__restrict__ colcnt, unsigned long long *__restrict__ stats) {
   const int64_t n = *d_n;
-  unsigned long long m = 0;
-  GRID_STRIDE(u, n) m = max(m, static_cast<unsigned long long>(seg[u + 1] - seg[u]));
+  if (blockIdx.x == 0 && threadIdx.x == 0) stats[0] = static_cast<unsigned long long>(n);
+  unsigned long long m = 0, ones = 0;
+  GRID_STRIDE(u, n) {
+    const int64_t p0 = seg[u], len = seg[u + 1] - p0;
+    m = max(m, static_cast<unsigned long long>(len));
+    if (len == 1) {
+      ++ones;
+      if (cntB) atomicAdd(&cntB[pb[p0]], 1);
+    }
+    if (rowcnt) {
+      atomicAdd(&rowcnt[morton_row(ckey[u])], 1);
+      atomicAdd(&colcnt[morton_col(ckey[u])], 1);
+    }
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+  for (int o = 16; o > 0; o >>= 1) {
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    ones += __shfl_xor_sync(0xffffffffu, ones, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (m) atomicMax(&stats[1], m);
+    if (ones) atomicAdd(&stats[2], ones);
+  }
+}
+
+// Groups of up to four one-pair C leaves per B leaf: sum of ceil(cnt / 4).
+__global__ void k_group_count(const int32_t *__restrict__ cntB, int64_t nB,
+                              unsigned long long *__restrict__ out) {
+  unsigned long long g = 0;
+  GRID_STRIDE(k, nB) g += static_cast<unsigned long long>((cntB[k] + 3) >> 2);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+  if ((threadIdx.x & 31) == 0 && g) atomicAdd(out, g);
 }
 
 __global__ void k_iota(int32_t *__restrict__ v, int64_t n) {
@@ -224,11 +258,25 @@ __global__ void k_compact3(const int32_t *__restrict__ keep, const int64_t *__re
 
 }  // namespace
 
+// Pairs of a product: sum over K of the A leaves in column K times the B
+// leaves in row K, from the patterns' host counts; -1 when a count is missing.
+static int64_t host_pair_count(const Pattern &A, const Pattern &B) {
+  if (A.colcnt.empty() || B.rowcnt.empty() || A.G != B.G ||
+      static_cast<int64_t>(A.colcnt.size()) != A.G || static_cast<int64_t>(B.rowcnt.size()) != B.G)
+    return -1;
+  int64_t P = 0;
+  for (int64_t K = 0; K < A.G; ++K)
+    P += static_cast<int64_t>(A.colcnt[K]) * static_cast<int64_t>(B.rowcnt[K]);
+  return P;
+}
+
 // Triples (I, K, J) of stored A(I,K), B(K,J), sorted by (Morton(I,J), K):
-// outputs key[P] (sorted), pa[P], pb[P].  Synchronises once to read P.
+// outputs key[P] (sorted), pa[P], pb[P].  P comes from the patterns' host
+// counts (no synchronisation; the device total is copied to *d_ptotal for a
+// later check) or, without them, from one synchronisation.
 static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
                         DevArray<uint64_t> &skey, DevArray<int32_t> &pa, DevArray<int32_t> &pb,
-                        int64_t *P_out, const double *normA = nullptr,
+                        int64_t *P_out, int64_t *d_ptotal, const double *normA = nullptr,
                         const double *normB = nullptr, double tau = 0.0,
                         bool upper_only = false) {
   const int L = A.L;
@@ -242,8 +290,13 @@ static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
     CHT_TRY(launched("pair_count"));
   }
   CHT_TRY(scan_exclusive(cnt.p, off.p, A.nnz, s));
-  int64_t P = 0;
-  CHT_TRY(read_i64(off.p + A.nnz, &P, s));
+  int64_t P = host_pair_count(A, B);
+  if (P < 0) {
+    CHT_TRY(read_i64(off.p + A.nnz, &P, s));
+  } else if (d_ptotal) {
+    CHT_CUDA_TRY(cudaMemcpyAsync(d_ptotal, off.p + A.nnz, sizeof(int64_t),
+                                 cudaMemcpyDeviceToDevice, s));
+  }
   if (P > 0x7fffffffLL) {
     set_error("%lld leaf pairs exceed the int32 pair index", (long long)P);
     return CHT_ERR_UNSUPPORTED;
@@ -261,7 +314,7 @@ static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
   if (P > 0) {
     k_pair_fill<<<grid_for(A.nnz * 32, 256), 256, 0, s>>>(A.brow.p, A.bcol.p, A.nnz, off.p,
                                                           B.rowptr.p, B.rowcol.p, B.rowleaf.p, L,
-                                                          key.p, pa0.p, pb0.p, idx.p);
+                                                          P, key.p, pa0.p, pb0.p, idx.p);
     CHT_TRY(launched("pair_fill"));
   }
   if (P > 0 && (normA || upper_only)) {
@@ -343,10 +396,17 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   plan->patA = A.id;
   plan->patB = B.id;
 
+  // statistics read in the phase's one synchronisation: [0] C leaves, [1]
+  // longest segment, [2] one-pair C leaves, [3] their groups (32-leaves),
+  // [4] the device's pair total (checked against the host's count)
+  DevArray<int64_t> stats;
+  CHT_TRY(stats.alloc(5, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(stats.p, 0, sizeof(int64_t) * 5, s));
   DevArray<uint64_t> skey;
   DevArray<int32_t> pa, pb;
   int64_t P = 0;
-  CHT_TRY(make_triples(A, B, s, skey, pa, pb, &P, normA, normB, tau, upper_only));
+  CHT_TRY(make_triples(A, B, s, skey, pa, pb, &P, stats.p + 4, normA, normB, tau, upper_only));
+  const int64_t P_made = host_pair_count(A, B);  // the count the pair list was sized with
   plan->npairs = P;
 
   DevArray<int32_t> head;
@@ -358,34 +418,68 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
     CHT_TRY(launched("heads"));
   }
   CHT_TRY(scan_exclusive(head.p, cpos.p, P, s));
-  // C leaves <= P: segments and keys are written at that capacity, and one
-  // synchronisation reads the C leaf count and the longest segment together
+  // C leaves <= P: segments and keys are written at that capacity
   const int64_t *d_nC = cpos.p + P;
   DevArray<uint64_t> ckey_cap;
-  DevArray<int64_t> cseg_cap, stats;
+  DevArray<int64_t> cseg_cap;
   CHT_TRY(ckey_cap.alloc(P, s));
   CHT_TRY(cseg_cap.alloc(P + 1, s));
   CHT_TRY(plan->pc.alloc(P, s));
-  CHT_TRY(stats.alloc(1, s));
-  CHT_CUDA_TRY(cudaMemsetAsync(stats.p, 0, sizeof(int64_t), s));
+  // per-B-leaf counts of one-pair C leaves (32-leaves: the split form's
+  // groups), and the C pattern's leaf counts per row and column
+  const bool groups = A.b == 32 && B.nnz > 0;
+  const int64_t G = A.G;
+  const bool counts = G <= kMaxCountG;
+  DevArray<int32_t> cntB, rc;
+  if (groups) {
+    CHT_TRY(cntB.alloc(B.nnz, s));
+    CHT_CUDA_TRY(cudaMemsetAsync(cntB.p, 0, sizeof(int32_t) * B.nnz, s));
+  }
+  if (counts) {
+    CHT_TRY(rc.alloc(2 * G, s));
+    CHT_CUDA_TRY(cudaMemsetAsync(rc.p, 0, sizeof(int32_t) * 2 * G, s));
+  }
+  auto *st = reinterpret_cast<unsigned long long *>(stats.p);
   if (P > 0) {
     k_segments<<<grid_for(P, 256), 256, 0, s>>>(skey.p, cpos.p, head.p, P, L, d_nC, ckey_cap.p,
                                                 cseg_cap.p, plan->pc.p);
     CHT_TRY(launched("segments"));
-    k_max_seg<<<grid_for(P, 256), 256, 0, s>>>(cseg_cap.p, d_nC,
-                                                reinterpret_cast<unsigned long long *>(stats.p));
-    CHT_TRY(launched("max_seg"));
+    k_c_stats<<<grid_for(P, 256), 256, 0, s>>>(cseg_cap.p, ckey_cap.p, d_nC, pb.p,
+                                                groups ? cntB.p : nullptr,
+                                                counts ? rc.p : nullptr,
+                                                counts ? rc.p + G : nullptr, st);
+    CHT_TRY(launched("c_stats"));
+    if (groups) {
+      k_group_count<<<grid_for(B.nnz, 256), 256, 0, s>>>(cntB.p, B.nnz, st + 3);
+      CHT_TRY(launched("group_count"));
+    }
   } else {
     CHT_CUDA_TRY(cudaMemsetAsync(cseg_cap.p, 0, sizeof(int64_t), s));
   }
-  int64_t host_stats[2] = {0, 0};
-  CHT_CUDA_TRY(cudaMemcpyAsync(&host_stats[0], d_nC, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  CHT_CUDA_TRY(cudaMemcpyAsync(&host_stats[1], stats.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  int64_t host_stats[5] = {0, 0, 0, 0, 0};
+  auto C = std::make_shared<Pattern>();
+  CHT_CUDA_TRY(cudaMemcpyAsync(host_stats, stats.p, sizeof(host_stats), cudaMemcpyDeviceToHost, s));
+  if (counts) {
+    C->rowcnt.resize(G);
+    C->colcnt.resize(G);
+    CHT_CUDA_TRY(cudaMemcpyAsync(C->rowcnt.data(), rc.p, sizeof(int32_t) * G,
+                                 cudaMemcpyDeviceToHost, s));
+    CHT_CUDA_TRY(cudaMemcpyAsync(C->colcnt.data(), rc.p + G, sizeof(int32_t) * G,
+                                 cudaMemcpyDeviceToHost, s));
+  }
   CHT_CUDA_TRY(cudaStreamSynchronize(s));
+  if (P_made >= 0 && host_stats[4] != P_made) {
+    set_error("pair count %lld from the leaf counts, %lld on the device", (long long)P_made,
+              (long long)host_stats[4]);
+    return CHT_ERR_INVALID;
+  }
   const int64_t nC = host_stats[0];
   plan->max_seg = host_stats[1];
+  if (groups) {
+    plan->n_one = host_stats[2];
+    plan->n_groups = host_stats[3];
+  }
 
-  auto C = std::make_shared<Pattern>();
   C->n = A.n;
   C->b = A.b;
   C->G = A.G;
@@ -474,7 +568,7 @@ int backward_lists_recompute(const Pattern &A, const Pattern &B, const Pattern &
   DevArray<uint64_t> skey;
   DevArray<int32_t> pa, pb;
   int64_t P = 0;
-  CHT_TRY(make_triples(A, B, s, skey, pa, pb, &P));
+  CHT_TRY(make_triples(A, B, s, skey, pa, pb, &P, nullptr));
   CHT_TRY(ensure_row_index(dC, s));
   DevArray<int32_t> pc, keep, ka, kb, kc;
   DevArray<int64_t> pos;
