@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 
 #include "internal.h"
@@ -99,13 +100,59 @@ static void keep_pool_memory() {
   done[dev] = true;
 }
 
+// Small blocks are cached per (stream, size class) and handed out again on
+// the same stream: stream order makes the reuse safe (a block freed after
+// work W on stream s is reused only by work queued on s after W), and the
+// symbolic phase's dozens of short-lived arrays then cost no allocator call.
+// Larger blocks, blocks beyond the cache's cap and any cached block after an
+// allocation failure go back to the stream-ordered pool.
+namespace {
+constexpr size_t kCacheMaxBlock = size_t(64) << 20;   // larger: not cached
+constexpr size_t kCacheMaxTotal = size_t(1) << 30;    // cached bytes per process
+std::mutex g_cache_mutex;
+std::map<std::pair<cudaStream_t, size_t>, std::vector<void *>> g_cache;
+size_t g_cached_bytes = 0;
+
+size_t size_class(size_t bytes) {
+  size_t c = 256;
+  while (c < bytes) c <<= 1;
+  return c;
+}
+
+// Returns every cached block to the pool (after an allocation failure).
+void flush_cache() {
+  std::lock_guard<std::mutex> lock(g_cache_mutex);
+  for (auto &kv : g_cache)
+    for (void *p : kv.second) cudaFreeAsync(p, kv.first.first);
+  g_cache.clear();
+  g_cached_bytes = 0;
+  cudaGetLastError();
+}
+}  // namespace
+
 void *dev_alloc(size_t bytes, cudaStream_t s) {
   if (g_alloc) return g_alloc(bytes, s, g_alloc_ctx);
+  const bool cached = bytes <= kCacheMaxBlock;
+  const size_t cls = cached ? size_class(bytes) : bytes;
+  if (cached) {
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    auto it = g_cache.find({s, cls});
+    if (it != g_cache.end() && !it->second.empty()) {
+      void *p = it->second.back();
+      it->second.pop_back();
+      g_cached_bytes -= cls;
+      return p;
+    }
+  }
   keep_pool_memory();
   void *p = nullptr;
-  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+  if (cudaMallocAsync(&p, cls, s) != cudaSuccess) {
     cudaGetLastError();
-    return nullptr;
+    flush_cache();
+    if (cudaMallocAsync(&p, cls, s) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
   }
   return p;
 }
@@ -115,6 +162,15 @@ void dev_free(void *p, size_t bytes, cudaStream_t s) {
   if (g_free) {
     g_free(p, bytes, s, g_alloc_ctx);
     return;
+  }
+  if (bytes <= kCacheMaxBlock) {
+    const size_t cls = size_class(bytes);
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
+    if (g_cached_bytes + cls <= kCacheMaxTotal) {
+      g_cache[{s, cls}].push_back(p);
+      g_cached_bytes += cls;
+      return;
+    }
   }
   cudaFreeAsync(p, s);
 }

@@ -169,9 +169,11 @@ inline unsigned grid_for(int64_t n, int threads) {
 // out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
 int scan_exclusive(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
 int scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
-// Stable LSD radix sort of (key, value) by the low `nbits` bits of key.
+// Stable LSD radix sort of (key, value) by bits lo_bit .. lo_bit + nbits - 1
+// of key.  Passes read whole bytes, so up to 7 bits above that range take
+// part in the order too: callers keep them zero.
 int radix_sort_pairs(const uint64_t *kin, const int32_t *vin, uint64_t *kout,
-                     int32_t *vout, int64_t n, int nbits, cudaStream_t s);
+                     int32_t *vout, int64_t n, int nbits, cudaStream_t s, int lo_bit = 0);
 // Copy of a device int64 to the host (synchronises s).
 int read_i64(const int64_t *d, int64_t *h, cudaStream_t s);
 

@@ -8,8 +8,11 @@
 // is the set of triples (I, K, J) with A(I, K) and B(K, J) stored.  Sorting the
 // triples by (Morton(I, J), K) groups them per C leaf in Morton order, with
 // ascending K inside each group.  All of this is exact integer work.
+#include <algorithm>
+
 #include "device.cuh"
 #include "internal.h"
+#include "scan.cuh"
 
 namespace cht {
 
@@ -19,14 +22,16 @@ namespace {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < (n); \
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
 
-// S1: pairs of A leaf (I, K) = stored leaves in row K of B.
-__global__ void k_pair_count(const int32_t *__restrict__ a_col, int64_t nA,
-                             const int64_t *__restrict__ b_rowptr, int32_t *__restrict__ cnt) {
-  GRID_STRIDE(a, nA) {
+// S1: pairs of A leaf (I, K) = stored leaves in row K of B (an element
+// loader of the scan that gives each A leaf's pair offset).
+struct PairCount {
+  const int32_t *a_col;
+  const int64_t *b_rowptr;
+  __device__ int64_t operator()(int64_t a) const {
     const int32_t K = a_col[a];
-    cnt[a] = static_cast<int32_t>(b_rowptr[K + 1] - b_rowptr[K]);
+    return b_rowptr[K + 1] - b_rowptr[K];
   }
-}
+};
 
 // S3: one warp per A leaf writes its pairs: key (Morton(I, J) << L) | K.
 __global__ void k_pair_fill(const int32_t *__restrict__ a_row, const int32_t *__restrict__ a_col,
@@ -68,38 +73,48 @@ __global__ void k_pair_gather(const int32_t *__restrict__ sidx, int64_t P,
 }
 
 // S4: a new C leaf starts where the Morton(I, J) part of the key changes.
-__global__ void k_heads(const uint64_t *__restrict__ skey, int64_t P, int L,
-                        int32_t *__restrict__ head) {
-  GRID_STRIDE(i, P) head[i] = (i == 0 || (skey[i] >> L) != (skey[i - 1] >> L)) ? 1 : 0;
+__device__ inline bool is_head(const uint64_t *skey, int64_t i, int L) {
+  return i == 0 || (skey[i] >> L) != (skey[i - 1] >> L);
 }
+struct HeadFlag {  // scan loader: C leaf index of every pair
+  const uint64_t *skey;
+  int L;
+  __device__ int64_t operator()(int64_t i) const { return is_head(skey, i, L) ? 1 : 0; }
+};
 
-// S4: C leaf of every pair, and each C leaf's Morton key and segment start;
-// *d_nC = cpos[P], the number of C leaves (read from the device, so the
-// host need not know it yet).
+// S4: C leaf of every pair, and each C leaf's Morton key, coordinates and
+// segment start; *d_nC = cpos[P], the number of C leaves (read from the
+// device, so the host need not know it yet).
 __global__ void k_segments(const uint64_t *__restrict__ skey, const int64_t *__restrict__ cpos,
-                           const int32_t *__restrict__ head, int64_t P, int L,
-                           const int64_t *__restrict__ d_nC, uint64_t *__restrict__ ckey,
-                           int64_t *__restrict__ cseg, int32_t *__restrict__ pc) {
+                           int64_t P, int L, const int64_t *__restrict__ d_nC,
+                           uint64_t *__restrict__ ckey, int32_t *__restrict__ crow,
+                           int32_t *__restrict__ ccol, int64_t *__restrict__ cseg,
+                           int32_t *__restrict__ pc) {
   GRID_STRIDE(i, P) {
-    const int64_t c = cpos[i] - (head[i] ? 0 : 1);
+    const bool head = is_head(skey, i, L);
+    const int64_t c = cpos[i] - (head ? 0 : 1);
     pc[i] = static_cast<int32_t>(c);
-    if (head[i]) {
+    if (head) {
+      const uint64_t m = skey[i] >> L;
       cseg[c] = i;
-      ckey[c] = skey[i] >> L;
+      ckey[c] = m;
+      crow[c] = static_cast<int32_t>(morton_row(m));
+      ccol[c] = static_cast<int32_t>(morton_col(m));
     }
     if (i == 0) cseg[*d_nC] = P;
   }
 }
 
-// S5: longest-first order key (stable sort keeps Morton order among ties);
-// 16 bits: segments of 65535 pairs or more all count as longest.
-constexpr int kLptBits = 16;
-__global__ void k_lpt_keys(const int64_t *__restrict__ seg, int64_t n, uint64_t *__restrict__ key,
-                           int32_t *__restrict__ idx) {
+// S5: longest-first order key (stable sort keeps Morton order among ties):
+// cap - min(len, cap), so that longer segments come first and segments of
+// cap pairs or more all count as longest.
+constexpr int64_t kLptCap = 0xffff;
+__global__ void k_lpt_keys(const int64_t *__restrict__ seg, int64_t n, int64_t cap,
+                           uint64_t *__restrict__ key, int32_t *__restrict__ idx) {
   GRID_STRIDE(u, n) {
     int64_t len = seg[u + 1] - seg[u];
-    if (len > 0xffffLL) len = 0xffffLL;
-    key[u] = 0xffffULL - static_cast<uint64_t>(len);
+    if (len > cap) len = cap;
+    key[u] = static_cast<uint64_t>(cap - len);
     idx[u] = static_cast<int32_t>(u);
   }
 }
@@ -281,15 +296,9 @@ static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
                         bool upper_only = false) {
   const int L = A.L;
   CHT_TRY(ensure_row_index(B, s));
-  DevArray<int32_t> cnt;
   DevArray<int64_t> off;
-  CHT_TRY(cnt.alloc(A.nnz, s));
   CHT_TRY(off.alloc(A.nnz + 1, s));
-  if (A.nnz > 0) {
-    k_pair_count<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.bcol.p, A.nnz, B.rowptr.p, cnt.p);
-    CHT_TRY(launched("pair_count"));
-  }
-  CHT_TRY(scan_exclusive(cnt.p, off.p, A.nnz, s));
+  CHT_TRY(scan_exclusive_fn(PairCount{A.bcol.p, B.rowptr.p}, A.nnz, off.p, s));
   int64_t P = host_pair_count(A, B);
   if (P < 0) {
     CHT_TRY(read_i64(off.p + A.nnz, &P, s));
@@ -350,7 +359,10 @@ static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
     P = Pk;
   }
   if (P > 0) {
-    CHT_TRY(radix_sort_pairs(key.p, idx.p, skey.p, sidx.p, P, 3 * L, s));
+    // the fill wrote the pairs in A's (Morton) leaf order, so for one (I, J)
+    // in ascending K: a stable sort on the Morton(I, J) bits alone keeps K
+    // ascending inside every C leaf
+    CHT_TRY(radix_sort_pairs(key.p, idx.p, skey.p, sidx.p, P, 2 * L, s, L));
     k_pair_gather<<<grid_for(P, 256), 256, 0, s>>>(sidx.p, P, pa0.p, pb0.p, pa.p, pb.p);
     CHT_TRY(launched("pair_gather"));
   }
@@ -358,9 +370,14 @@ static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
   return CHT_OK;
 }
 
-int schedule_units(const int64_t *seg, int64_t n, int32_t *order, cudaStream_t s) {
+// Longest-first order of n units with segments seg; max_len: the longest
+// segment when known (the sort then reads only the bits it needs), else 0.
+int schedule_units(const int64_t *seg, int64_t n, int32_t *order, cudaStream_t s,
+                   int64_t max_len = 0) {
   if (n <= 0) return CHT_OK;
-  if (g_opt.schedule == 1) {
+  const int64_t cap = max_len > 0 ? std::min(max_len, kLptCap) : kLptCap;
+  if (g_opt.schedule == 1 || (max_len == 1)) {
+    // Morton order, or every segment has one pair: the identity
     k_iota<<<grid_for(n, 256), 256, 0, s>>>(order, n);
     return launched("iota");
   }
@@ -369,9 +386,9 @@ int schedule_units(const int64_t *seg, int64_t n, int32_t *order, cudaStream_t s
   CHT_TRY(key.alloc(n, s));
   CHT_TRY(skey.alloc(n, s));
   CHT_TRY(idx.alloc(n, s));
-  k_lpt_keys<<<grid_for(n, 256), 256, 0, s>>>(seg, n, key.p, idx.p);
+  k_lpt_keys<<<grid_for(n, 256), 256, 0, s>>>(seg, n, cap, key.p, idx.p);
   CHT_TRY(launched("lpt_keys"));
-  return radix_sort_pairs(key.p, idx.p, skey.p, order, n, kLptBits, s);
+  return radix_sort_pairs(key.p, idx.p, skey.p, order, n, bits_for(cap + 1), s);
 }
 
 int leaf_norms(const double *vals, int64_t n, int b, double *out, cudaStream_t s) {
@@ -409,21 +426,17 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   const int64_t P_made = host_pair_count(A, B);  // the count the pair list was sized with
   plan->npairs = P;
 
-  DevArray<int32_t> head;
   DevArray<int64_t> cpos;
-  CHT_TRY(head.alloc(P, s));
   CHT_TRY(cpos.alloc(P + 1, s));
-  if (P > 0) {
-    k_heads<<<grid_for(P, 256), 256, 0, s>>>(skey.p, P, L, head.p);
-    CHT_TRY(launched("heads"));
-  }
-  CHT_TRY(scan_exclusive(head.p, cpos.p, P, s));
-  // C leaves <= P: segments and keys are written at that capacity
+  CHT_TRY(scan_exclusive_fn(HeadFlag{skey.p, L}, P, cpos.p, s));
+  // C leaves <= P: the C pattern's keys, coordinates and segments are
+  // written at that capacity (and kept at it)
+  auto C = std::make_shared<Pattern>();
   const int64_t *d_nC = cpos.p + P;
-  DevArray<uint64_t> ckey_cap;
-  DevArray<int64_t> cseg_cap;
-  CHT_TRY(ckey_cap.alloc(P, s));
-  CHT_TRY(cseg_cap.alloc(P + 1, s));
+  CHT_TRY(C->mkey.alloc(P, s));
+  CHT_TRY(C->brow.alloc(P, s));
+  CHT_TRY(C->bcol.alloc(P, s));
+  CHT_TRY(plan->cseg.alloc(P + 1, s));
   CHT_TRY(plan->pc.alloc(P, s));
   // per-B-leaf counts of one-pair C leaves (32-leaves: the split form's
   // groups), and the C pattern's leaf counts per row and column
@@ -441,10 +454,10 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   }
   auto *st = reinterpret_cast<unsigned long long *>(stats.p);
   if (P > 0) {
-    k_segments<<<grid_for(P, 256), 256, 0, s>>>(skey.p, cpos.p, head.p, P, L, d_nC, ckey_cap.p,
-                                                cseg_cap.p, plan->pc.p);
+    k_segments<<<grid_for(P, 256), 256, 0, s>>>(skey.p, cpos.p, P, L, d_nC, C->mkey.p,
+                                                C->brow.p, C->bcol.p, plan->cseg.p, plan->pc.p);
     CHT_TRY(launched("segments"));
-    k_c_stats<<<grid_for(P, 256), 256, 0, s>>>(cseg_cap.p, ckey_cap.p, d_nC, pb.p,
+    k_c_stats<<<grid_for(P, 256), 256, 0, s>>>(plan->cseg.p, C->mkey.p, d_nC, pb.p,
                                                 groups ? cntB.p : nullptr,
                                                 counts ? rc.p : nullptr,
                                                 counts ? rc.p + G : nullptr, st);
@@ -454,10 +467,9 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
       CHT_TRY(launched("group_count"));
     }
   } else {
-    CHT_CUDA_TRY(cudaMemsetAsync(cseg_cap.p, 0, sizeof(int64_t), s));
+    CHT_CUDA_TRY(cudaMemsetAsync(plan->cseg.p, 0, sizeof(int64_t), s));
   }
   int64_t host_stats[5] = {0, 0, 0, 0, 0};
-  auto C = std::make_shared<Pattern>();
   CHT_CUDA_TRY(cudaMemcpyAsync(host_stats, stats.p, sizeof(host_stats), cudaMemcpyDeviceToHost, s));
   if (counts) {
     C->rowcnt.resize(G);
@@ -486,16 +498,8 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   C->L = L;
   C->nnz = nC;
   C->id = next_id();
-  CHT_TRY(C->mkey.alloc(nC, s));
-  CHT_TRY(plan->cseg.alloc(nC + 1, s));
   CHT_TRY(plan->order.alloc(nC, s));
-  if (nC > 0)
-    CHT_CUDA_TRY(cudaMemcpyAsync(C->mkey.p, ckey_cap.p, sizeof(uint64_t) * nC,
-                                 cudaMemcpyDeviceToDevice, s));
-  CHT_CUDA_TRY(cudaMemcpyAsync(plan->cseg.p, cseg_cap.p, sizeof(int64_t) * (nC + 1),
-                               cudaMemcpyDeviceToDevice, s));
-  CHT_TRY(build_pattern_index(*C, s));
-  CHT_TRY(schedule_units(plan->cseg.p, nC, plan->order.p, s));
+  CHT_TRY(schedule_units(plan->cseg.p, nC, plan->order.p, s, plan->max_seg));
   plan->pa = std::move(pa);
   plan->pb = std::move(pb);
   plan->C = std::move(C);
