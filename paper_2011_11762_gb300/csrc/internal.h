@@ -249,6 +249,7 @@ struct cht_plan {
   // C leaves with exactly one pair, and their groups of up to four sharing
   // a B leaf (read in the symbolic phase's synchronisation; -1: not known)
   int64_t n_one = -1, n_groups = -1;
+  cht::DevArray<int32_t> one_pair_b; // [nB]: one-pair C leaves per B leaf (32-leaves)
   cht::DevArray<int64_t> cseg;       // [nC + 1]
   cht::DevArray<int32_t> pa, pb, pc; // per pair (sorted by C leaf, then K)
   cht::DevArray<int32_t> order;      // schedule [nC]

@@ -49,6 +49,7 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "scan.cuh"
 
 namespace cht {
 
@@ -1903,83 +1904,40 @@ __global__ void k_pack_units(int64_t n, int64_t prod, int64_t off, int64_t *__re
 }
 
 // ------------------------------------- grouping of the one-pair C leaves --
-// The C leaves with exactly one pair, sorted by that pair's B leaf in row-
-// major (K, J) order -- neighbouring groups then share the A leaves of one
-// inner index K through L2 -- and cut into groups of at most 4 per B leaf;
-// the C leaves with two or more pairs form the general kernel's unit list.
-__global__ void k_classify(const int64_t *__restrict__ cseg, int64_t nC,
-                           int32_t *__restrict__ one, int32_t *__restrict__ more) {
+// The C leaves with exactly one pair, grouped by that pair's B leaf (groups
+// in B's leaf order, i.e. Morton order of (K, J): neighbouring groups share
+// A leaves of nearby inner indices K through L2) and cut into groups of at
+// most 4 per B leaf; the C leaves with two or more pairs form the general
+// kernel's unit list.  The symbolic phase counted the one-pair leaves per B
+// leaf (cntB), so B leaf k's groups start at the prefix sum of ceil(cnt / 4)
+// and each one-pair C leaf takes a slot in its B leaf's run by an atomic
+// counter: the order inside a run (and in the list of the others) is not
+// fixed, which changes no result -- every C leaf is computed on its own.
+struct GroupsOf {  // scan loader: groups of B leaf k
+  const int32_t *cntB;
+  __device__ int64_t operator()(int64_t k) const { return (cntB[k] + 3) >> 2; }
+};
+
+__global__ void k_group_place(const int64_t *__restrict__ cseg, int64_t nC,
+                              const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
+                              const int64_t *__restrict__ gstart, int32_t *__restrict__ fill,
+                              unsigned long long *__restrict__ nmore, int32_t *__restrict__ gb,
+                              int32_t *__restrict__ ga, int32_t *__restrict__ gc,
+                              int64_t *__restrict__ more) {
   for (int64_t o = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; o < nC;
        o += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t np = cseg[o + 1] - cseg[o];
-    one[o] = np == 1 ? 1 : 0;
-    more[o] = np >= 2 ? 1 : 0;
-  }
-}
-
-__global__ void k_single_keys(const int64_t *__restrict__ cseg, const int32_t *__restrict__ pb,
-                              const int32_t *__restrict__ b_row, const int32_t *__restrict__ b_col,
-                              int L, const int32_t *__restrict__ one,
-                              const int64_t *__restrict__ opos, const int32_t *__restrict__ more,
-                              const int64_t *__restrict__ mpos, int64_t nC,
-                              uint64_t *__restrict__ key, int32_t *__restrict__ val,
-                              int64_t *__restrict__ munits) {
-  for (int64_t o = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; o < nC;
-       o += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    if (one[o]) {
-      const int32_t bl = pb[cseg[o]];
-      const int64_t i = opos[o];
-      key[i] = (static_cast<uint64_t>(b_row[bl]) << L) | static_cast<uint32_t>(b_col[bl]);
-      val[i] = static_cast<int32_t>(o);
-    } else if (more[o]) {
-      munits[mpos[o]] = o;
-    }
-  }
-}
-
-__global__ void k_key_heads(const uint64_t *__restrict__ key, int64_t n,
-                            int32_t *__restrict__ head) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    head[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
-}
-
-// run r starts at start[r]; hx = exclusive scan of the heads
-__global__ void k_run_starts(const int32_t *__restrict__ head, const int64_t *__restrict__ hx,
-                             int64_t n, int64_t *__restrict__ start) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    if (head[i]) start[hx[i]] = i;
-}
-
-// a group starts at every 4th element of a run
-__global__ void k_group_starts(const int32_t *__restrict__ head, const int64_t *__restrict__ hx,
-                               const int64_t *__restrict__ start, int64_t n,
-                               int32_t *__restrict__ gs) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t pos = i - start[hx[i] + head[i] - 1];
-    gs[i] = (pos & 3) == 0 ? 1 : 0;
-  }
-}
-
-__global__ void k_group_fill(const int32_t *__restrict__ val, const int32_t *__restrict__ head,
-                             const int64_t *__restrict__ hx, const int64_t *__restrict__ start,
-                             const int32_t *__restrict__ gs, const int64_t *__restrict__ gx,
-                             int64_t n, const int64_t *__restrict__ cseg,
-                             const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
-                             int32_t *__restrict__ gb, int32_t *__restrict__ ga,
-                             int32_t *__restrict__ gc) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t pos = i - start[hx[i] + head[i] - 1];
-    const int64_t g = gx[i] + gs[i] - 1;
-    const int q = static_cast<int>(pos & 3);
-    const int32_t o = val[i];
     const int64_t p = cseg[o];
-    ga[4 * g + q] = pa[p];
-    gc[4 * g + q] = o;
-    if (q == 0) gb[g] = pb[p];
+    if (cseg[o + 1] - p == 1) {
+      const int32_t k = pb[p];
+      const int slot = atomicAdd(&fill[k], 1);
+      const int64_t g = gstart[k] + (slot >> 2);
+      const int q = slot & 3;
+      ga[4 * g + q] = pa[p];
+      gc[4 * g + q] = static_cast<int32_t>(o);
+      if (q == 0) gb[g] = k;
+    } else {
+      more[atomicAdd(nmore, 1ULL)] = o;
+    }
   }
 }
 
@@ -1989,75 +1947,36 @@ struct SingleGroups {
   int64_t ngroups = 0, nmore = 0, nsingle = 0;
 };
 
-int build_single_groups(const cht_plan *plan, const Pattern &pb_pat, cudaStream_t s,
-                        SingleGroups &g) {
-  const int64_t nC = plan->C->nnz;
-  DevArray<int32_t> one, more;
-  DevArray<int64_t> opos, mpos;
-  CHT_TRY(one.alloc(nC, s));
-  CHT_TRY(more.alloc(nC, s));
-  CHT_TRY(opos.alloc(nC + 1, s));
-  CHT_TRY(mpos.alloc(nC + 1, s));
-  if (nC > 0) {
-    k_classify<<<grid_for(nC, 256), 256, 0, s>>>(plan->cseg.p, nC, one.p, more.p);
-    CHT_TRY(launched("classify"));
+int build_single_groups(const cht_plan *plan, cudaStream_t s, SingleGroups &g) {
+  const int64_t nC = plan->C->nnz, nB = plan->nB;
+  if (plan->n_one < 0 || plan->n_groups < 0 || plan->one_pair_b.p == nullptr) {
+    set_error("the plan carries no one-pair counts (a 32-leaf plan from the symbolic phase does)");
+    return CHT_ERR_INVALID;
   }
-  CHT_TRY(scan_exclusive(one.p, opos.p, nC, s));
-  CHT_TRY(scan_exclusive(more.p, mpos.p, nC, s));
-  // the counts come from the symbolic phase's synchronisation when it
-  // counted them (32-leaf plans), else from one here
-  const bool known = plan->n_one >= 0 && plan->n_groups >= 0;
-  int64_t counts[2] = {plan->n_one, nC - plan->n_one};
-  if (!known) {
-    CHT_CUDA_TRY(cudaMemcpyAsync(&counts[0], opos.p + nC, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CHT_CUDA_TRY(cudaMemcpyAsync(&counts[1], mpos.p + nC, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CHT_CUDA_TRY(cudaStreamSynchronize(s));
-  }
-  const int64_t nS = counts[0];
-  g.nsingle = nS;
-  g.nmore = counts[1];
-  DevArray<uint64_t> key, skey;
-  DevArray<int32_t> val, sval;
-  CHT_TRY(key.alloc(nS, s));
-  CHT_TRY(skey.alloc(nS, s));
-  CHT_TRY(val.alloc(nS, s));
-  CHT_TRY(sval.alloc(nS, s));
-  CHT_TRY(g.more.alloc(g.nmore, s));
-  if (nC > 0) {
-    k_single_keys<<<grid_for(nC, 256), 256, 0, s>>>(
-        plan->cseg.p, plan->pb.p, pb_pat.brow.p, pb_pat.bcol.p, pb_pat.L, one.p, opos.p, more.p,
-        mpos.p, nC, key.p, val.p, g.more.p);
-    CHT_TRY(launched("single_keys"));
-  }
-  if (nS == 0) return CHT_OK;
-  CHT_TRY(radix_sort_pairs(key.p, val.p, skey.p, sval.p, nS, 2 * pb_pat.L, s));
-  DevArray<int32_t> head, gs;
-  DevArray<int64_t> hx, start, gx;
-  CHT_TRY(head.alloc(nS, s));
-  CHT_TRY(gs.alloc(nS, s));
-  CHT_TRY(hx.alloc(nS + 1, s));
-  CHT_TRY(start.alloc(nS, s));
-  CHT_TRY(gx.alloc(nS + 1, s));
-  k_key_heads<<<grid_for(nS, 256), 256, 0, s>>>(skey.p, nS, head.p);
-  CHT_TRY(launched("key_heads"));
-  CHT_TRY(scan_exclusive(head.p, hx.p, nS, s));
-  k_run_starts<<<grid_for(nS, 256), 256, 0, s>>>(head.p, hx.p, nS, start.p);
-  CHT_TRY(launched("run_starts"));
-  k_group_starts<<<grid_for(nS, 256), 256, 0, s>>>(head.p, hx.p, start.p, nS, gs.p);
-  CHT_TRY(launched("group_starts"));
-  CHT_TRY(scan_exclusive(gs.p, gx.p, nS, s));
-  int64_t ng = plan->n_groups;
-  if (!known) CHT_TRY(read_i64(gx.p + nS, &ng, s));
-  g.ngroups = ng;
+  g.nsingle = plan->n_one;
+  g.nmore = nC - plan->n_one;
+  g.ngroups = plan->n_groups;
+  const int64_t ng = g.ngroups;
+  DevArray<int64_t> gstart;
+  DevArray<int32_t> fill;
+  DevArray<unsigned long long> nmore;
+  CHT_TRY(gstart.alloc(nB + 1, s));
+  CHT_TRY(fill.alloc(nB, s));
+  CHT_TRY(nmore.alloc(1, s));
   CHT_TRY(g.gb.alloc(ng, s));
   CHT_TRY(g.ga.alloc(4 * ng, s));
   CHT_TRY(g.gc.alloc(4 * ng, s));
+  CHT_TRY(g.more.alloc(g.nmore, s));
+  if (nC == 0) return CHT_OK;
+  CHT_TRY(scan_exclusive_fn(GroupsOf{plan->one_pair_b.p}, nB, gstart.p, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(fill.p, 0, sizeof(int32_t) * nB, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(nmore.p, 0, sizeof(unsigned long long), s));
   CHT_CUDA_TRY(cudaMemsetAsync(g.ga.p, 0, sizeof(int32_t) * 4 * ng, s));
   CHT_CUDA_TRY(cudaMemsetAsync(g.gc.p, 0xff, sizeof(int32_t) * 4 * ng, s));  // -1
-  k_group_fill<<<grid_for(nS, 256), 256, 0, s>>>(sval.p, head.p, hx.p, start.p, gs.p, gx.p, nS,
-                                                 plan->cseg.p, plan->pa.p, plan->pb.p, g.gb.p,
-                                                 g.ga.p, g.gc.p);
-  return launched("group_fill");
+  k_group_place<<<grid_for(nC, 256), 256, 0, s>>>(plan->cseg.p, nC, plan->pa.p, plan->pb.p,
+                                                  gstart.p, fill.p, nmore.p, g.gb.p, g.ga.p,
+                                                  g.gc.p, g.more.p);
+  return launched("group_place");
 }
 
 // One launch over `ntotal` groups: those of `w` (works NULL), or the groups
@@ -2113,10 +2032,10 @@ SingleWork make_single_work(const cht_plan *plan, const Operands &op, const Sing
 }
 
 // The plan's one-pair groups, built at its first use and kept in the plan.
-int plan_groups(cht_plan *plan, const Pattern &b_pat, cudaStream_t s, const SingleGroups **out) {
+int plan_groups(cht_plan *plan, cudaStream_t s, const SingleGroups **out) {
   if (!plan->split_groups) {
     auto g = std::make_shared<SingleGroups>();
-    CHT_TRY(build_single_groups(plan, b_pat, s, *g));
+    CHT_TRY(build_single_groups(plan, s, *g));
     plan->split_groups = g;
   }
   *out = static_cast<const SingleGroups *>(plan->split_groups.get());
@@ -2161,7 +2080,7 @@ int split_multiply(cht_plan *plan, cht_mat *A, cht_mat *B, int nslices, cudaStre
   // symbolic phase did not count them, and should then not wait for the
   // slicing pre-kernels)
   const SingleGroups *groups = nullptr;
-  if (one_pair) CHT_TRY(plan_groups(plan, *B->pat, s, &groups));
+  if (one_pair) CHT_TRY(plan_groups(plan, s, &groups));
   Operands op;
   CHT_TRY(alloc_operands(*A->pat, *B->pat, s, op));
   if (b == 64)
@@ -2235,7 +2154,7 @@ int split_batch_prepare(cht_batch *bt, cudaStream_t s) {
     } else if (plan->b == 32 && g_opt.split_single) {
       // as cht_multiply: one-pair C leaves to the one-pair kernel
       const SingleGroups *g = nullptr;
-      CHT_TRY(plan_groups(plan, *bt->Bs[i]->pat, s, &g));
+      CHT_TRY(plan_groups(plan, s, &g));
       works[i] = make_single_work(plan, sb->ops[i], *g, bt->views[i]->view_vals);
       sb->one_pair[i] = 1;
       sb->ngunits += g->ngroups;

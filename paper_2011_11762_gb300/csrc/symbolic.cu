@@ -490,6 +490,7 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   if (groups) {
     plan->n_one = host_stats[2];
     plan->n_groups = host_stats[3];
+    plan->one_pair_b = std::move(cntB);
   }
 
   C->n = A.n;
