@@ -139,6 +139,10 @@ struct Pattern {
 };
 uint64_t next_id();
 int bits_for(int64_t G);
+// Most pairs of a C leaf whose pairs the split form's one-pair kernel takes
+// as separate units (their exact integer results are summed afterwards; the
+// sum of this many stays far inside 64 bits).
+constexpr int kFewPairsMax = 4;
 // Largest leaf grid side for which patterns keep host leaf counts.
 constexpr int64_t kMaxCountG = 1 << 16;
 // Adds the leaf counts per row and column of the n Morton keys key[i] with
@@ -246,10 +250,13 @@ struct cht_plan {
   std::shared_ptr<cht::Pattern> C;   // product pattern
   int64_t npairs = 0;
   int64_t max_seg = 0;               // most pairs of any C leaf
-  // C leaves with exactly one pair, and their groups of up to four sharing
-  // a B leaf (read in the symbolic phase's synchronisation; -1: not known)
-  int64_t n_one = -1, n_groups = -1;
-  cht::DevArray<int32_t> one_pair_b; // [nB]: one-pair C leaves per B leaf (32-leaves)
+  // 32-leaf plans, for the split form's B-leaf groups (read in the symbolic
+  // phase's synchronisation; -1: not known): C leaves with one pair, C
+  // leaves with 2 .. kFewPairsMax pairs and those leaves' pairs (each pair a
+  // unit of its own, summed afterwards), the groups of up to four units
+  // sharing a B leaf, and the units per B leaf
+  int64_t n_one = -1, n_few = -1, n_virt = -1, n_groups = -1;
+  cht::DevArray<int32_t> one_pair_b; // [nB]
   cht::DevArray<int64_t> cseg;       // [nC + 1]
   cht::DevArray<int32_t> pa, pb, pc; // per pair (sorted by C leaf, then K)
   cht::DevArray<int32_t> order;      // schedule [nC]

@@ -1343,11 +1343,18 @@ struct SingleWork {
   const uint8_t *b_slices;  // [nB][6][tile]
   const int32_t *gb;        // per group: B leaf
   const int32_t *ga;        // per group: 4 A leaves
-  const int32_t *gc;        // per group: 4 C leaves (-1: none)
+  // per group: 4 units: C leaf c >= 0 (its one pair), -1 none, or -2 - v:
+  // pair v of a C leaf with 2 .. kFewPairsMax pairs, whose exact integer
+  // result goes to scratch slot v (summed per C leaf by k_few_sum)
+  const int32_t *gc;
   const int32_t *crow, *ccol;
+  const int32_t *bcol;      // B leaf columns (a group's C column)
   const int *row_exp, *col_exp;
   double *C;
-  int64_t ngroups;
+  int64_t *scratch;         // [nvirt][32][32]
+  // C leaves of 2 .. kFewPairsMax pairs: leaf, first scratch slot, pairs
+  const int32_t *few_c, *few_v, *few_m;
+  int64_t ngroups, nfew, nvirt;
   int64_t nA, nB, nC, G;  // lengths (read by the bounds-checked build)
 };
 
@@ -1357,7 +1364,8 @@ struct alignas(16) GSlot {
   int32_t crow[4];  // the leaves' rows
   int32_t ccol;     // the shared leaf column
   int32_t count;    // units in the group (0: no more groups)
-  int32_t pad[2];
+  int32_t raw;      // bit q: unit q writes its exact integers (a scratch slot)
+  int32_t pad;
 };
 
 constexpr size_t single32_smem() {
@@ -1445,6 +1453,7 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
       if (valid_l && !CHT_INDEX_OK(g < w.ngroups, status)) valid_l = false;
       const uint8_t *as_l = w.a_slices, *bs_l = w.b_slices;
       double *C_l = w.C;
+      int64_t *sc_l = w.scratch;
       const int *re_l = w.row_exp, *ce_l = w.col_exp;
       if (valid_l) {
         gb_l = w.gb[g];
@@ -1453,15 +1462,16 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
         for (int q = 0; q < 4; ++q) {
           ga_l[q] = w.ga[4 * g + q];
           gc_l[q] = w.gc[4 * g + q];
-          ok = ok && gc_l[q] < w.nC && (gc_l[q] < 0 || (ga_l[q] >= 0 && ga_l[q] < w.nA));
+          ok = ok && gc_l[q] < w.nC && -2 - static_cast<int64_t>(gc_l[q]) < w.nvirt &&
+               (gc_l[q] == -1 || (ga_l[q] >= 0 && ga_l[q] < w.nA));
         }
-        ok = ok && gc_l[0] >= 0;
+        ok = ok && gc_l[0] != -1;
         if (!CHT_INDEX_OK(ok, status)) valid_l = false;
       }
       if (valid_l) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) cr_l[q] = gc_l[q] >= 0 ? w.crow[gc_l[q]] : 0;
-        ccol_l = w.ccol[gc_l[0]];
+        ccol_l = w.bcol[gb_l];  // the B leaf's column is every unit's C column
         bool ok = ccol_l >= 0 && ccol_l < w.G;
 #pragma unroll
         for (int q = 0; q < 4; ++q) ok = ok && cr_l[q] >= 0 && cr_l[q] < w.G;
@@ -1498,22 +1508,32 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
             __shfl_sync(0xffffffffu, reinterpret_cast<long long>(bs_l), j));
         double *Cbase = reinterpret_cast<double *>(
             __shfl_sync(0xffffffffu, reinterpret_cast<long long>(C_l), j));
+        int64_t *scratch = reinterpret_cast<int64_t *>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<long long>(sc_l), j));
         const int *row_exp = reinterpret_cast<const int *>(
             __shfl_sync(0xffffffffu, reinterpret_cast<long long>(re_l), j));
         const int *col_exp = reinterpret_cast<const int *>(
             __shfl_sync(0xffffffffu, reinterpret_cast<long long>(ce_l), j));
         const int gbv = __shfl_sync(0xffffffffu, gb_l, j);
         const int ccv = __shfl_sync(0xffffffffu, ccol_l, j);
-        int count = 0;
+        int count = 0, raw = 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) count += gc[q] >= 0 ? 1 : 0;
+        for (int q = 0; q < 4; ++q) {
+          count += gc[q] != -1 ? 1 : 0;
+          raw |= gc[q] <= -2 ? 1 << q : 0;
+        }
         if (lane < 4) {
-          sl.C[lane] = gc[lane] >= 0 ? Cbase + static_cast<int64_t>(gc[lane]) * 1024 : nullptr;
+          const int c = gc[lane];
+          sl.C[lane] = c >= 0    ? Cbase + static_cast<int64_t>(c) * 1024
+                       : c <= -2 ? reinterpret_cast<double *>(
+                                       scratch + (-2 - static_cast<int64_t>(c)) * 1024)
+                                 : nullptr;
           sl.crow[lane] = cr[lane];
         }
         if (lane == 0) {
           sl.ccol = ccv;
           sl.count = count;
+          sl.raw = raw;
           sl.row_exp = row_exp;
           sl.col_exp = col_exp;
         }
@@ -1538,7 +1558,7 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
         // 16-byte chunks l, l + 32, .. of every tile (coalesced)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          if (gc[q] < 0) continue;
+          if (gc[q] == -1) continue;
           const uint8_t *src = a_slices + static_cast<int64_t>(ga[q]) * Cfg<32>::SA * kTile;
 #pragma unroll
           for (int i = 0; i < kASlices; ++i)
@@ -1621,8 +1641,10 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
       const GSlot &sl = queue[qs];
       if (sl.count == 0) break;
       double *Cq = sl.C[q];
+      const bool raw = (sl.raw >> q) & 1;  // exact integers to a scratch slot
       // line exponents (loaded while the MMAs run)
-      const int er = Cq ? sl.row_exp[static_cast<int64_t>(sl.crow[q]) * 32 + lane] : kNoExp;
+      const int er =
+          Cq && !raw ? sl.row_exp[static_cast<int64_t>(sl.crow[q]) * 32 + lane] : kNoExp;
       int fc[kCols];
 #pragma unroll
       for (int c = 0; c < kCols; ++c)
@@ -1668,13 +1690,20 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
         double *stg = staging + (warp - 2) * 32 * kStgPitch;
         const uint32_t eb = static_cast<uint32_t>(er) - 56u;
         bool good = true;
+        if (raw) {
+          // the integers themselves (their bit patterns pass through the
+          // staging block and the stores unchanged)
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) {
-          bool ok;
-          const double x =
-              scaled_i64_fast(T[c], static_cast<int>(eb + static_cast<uint32_t>(fc[c])), &ok);
-          good = good && ok;
-          stg[lane * kStgPitch + c] = x;
+          for (int c = 0; c < kCols; ++c) stg[lane * kStgPitch + c] = __longlong_as_double(T[c]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < kCols; ++c) {
+            bool ok;
+            const double x =
+                scaled_i64_fast(T[c], static_cast<int>(eb + static_cast<uint32_t>(fc[c])), &ok);
+            good = good && ok;
+            stg[lane * kStgPitch + c] = x;
+          }
         }
         if (!__all_sync(0xffffffffu, good)) {
           // a result outside the normal range of doubles somewhere in the
@@ -1904,15 +1933,21 @@ __global__ void k_pack_units(int64_t n, int64_t prod, int64_t off, int64_t *__re
 }
 
 // ------------------------------------- grouping of the one-pair C leaves --
-// The C leaves with exactly one pair, grouped by that pair's B leaf (groups
-// in B's leaf order, i.e. Morton order of (K, J): neighbouring groups share
-// A leaves of nearby inner indices K through L2) and cut into groups of at
-// most 4 per B leaf; the C leaves with two or more pairs form the general
-// kernel's unit list.  The symbolic phase counted the one-pair leaves per B
-// leaf (cntB), so B leaf k's groups start at the prefix sum of ceil(cnt / 4)
-// and each one-pair C leaf takes a slot in its B leaf's run by an atomic
-// counter: the order inside a run (and in the list of the others) is not
-// fixed, which changes no result -- every C leaf is computed on its own.
+// The units of the one-pair kernel are the pairs of the C leaves with at
+// most kFewPairsMax pairs: a one-pair C leaf is one unit writing its C leaf;
+// a C leaf of 2 .. kFewPairsMax pairs gives one unit per pair, each writing
+// its exact integer result (in units of 2^(e_r + f_c - 54), the same for
+// every pair of the leaf) to a scratch slot, and k_few_sum adds them and
+// converts once: the exact sum of the method's slice products (i + j <= 7)
+// over the leaf's pairs, rounded once.  Units are grouped by their B leaf (groups in B's leaf order, i.e.
+// Morton order of (K, J): neighbouring groups share A leaves of nearby inner
+// indices K through L2), at most 4 per group; the C leaves with more pairs
+// form the general kernel's unit list.  The symbolic phase counted the units
+// per B leaf (cntB), so B leaf k's groups start at the prefix sum of
+// ceil(cnt / 4), and each unit takes a slot in its B leaf's run by an atomic
+// counter: the order inside a run, of the scratch slots and of the general
+// kernel's list is not fixed, which changes no result -- every C leaf is
+// computed on its own and every sum is exact.
 struct GroupsOf {  // scan loader: groups of B leaf k
   const int32_t *cntB;
   __device__ int64_t operator()(int64_t k) const { return (cntB[k] + 3) >> 2; }
@@ -1921,62 +1956,135 @@ struct GroupsOf {  // scan loader: groups of B leaf k
 __global__ void k_group_place(const int64_t *__restrict__ cseg, int64_t nC,
                               const int32_t *__restrict__ pa, const int32_t *__restrict__ pb,
                               const int64_t *__restrict__ gstart, int32_t *__restrict__ fill,
-                              unsigned long long *__restrict__ nmore, int32_t *__restrict__ gb,
-                              int32_t *__restrict__ ga, int32_t *__restrict__ gc,
-                              int64_t *__restrict__ more) {
+                              unsigned long long *__restrict__ counters,
+                              int32_t *__restrict__ gb, int32_t *__restrict__ ga,
+                              int32_t *__restrict__ gc, int64_t *__restrict__ more,
+                              int32_t *__restrict__ few_c, int32_t *__restrict__ few_v,
+                              int32_t *__restrict__ few_m) {
   for (int64_t o = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; o < nC;
        o += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t p = cseg[o];
-    if (cseg[o + 1] - p == 1) {
-      const int32_t k = pb[p];
+    const int64_t len = cseg[o + 1] - p;
+    const int m = len > kFewPairsMax ? kFewPairsMax + 1 : static_cast<int>(len);
+    if (m > kFewPairsMax) {
+      more[atomicAdd(&counters[0], 1ULL)] = o;
+      continue;
+    }
+    int64_t v0 = 0;
+    if (m > 1) {
+      const int64_t f = static_cast<int64_t>(atomicAdd(&counters[1], 1ULL));
+      v0 = static_cast<int64_t>(atomicAdd(&counters[2], static_cast<unsigned long long>(m)));
+      few_c[f] = static_cast<int32_t>(o);
+      few_v[f] = static_cast<int32_t>(v0);
+      few_m[f] = m;
+    }
+    for (int j = 0; j < m; ++j) {
+      const int32_t k = pb[p + j];
       const int slot = atomicAdd(&fill[k], 1);
       const int64_t g = gstart[k] + (slot >> 2);
       const int q = slot & 3;
-      ga[4 * g + q] = pa[p];
-      gc[4 * g + q] = static_cast<int32_t>(o);
+      ga[4 * g + q] = pa[p + j];
+      gc[4 * g + q] = m == 1 ? static_cast<int32_t>(o) : static_cast<int32_t>(-2 - (v0 + j));
       if (q == 0) gb[g] = k;
-    } else {
-      more[atomicAdd(nmore, 1ULL)] = o;
+    }
+  }
+}
+
+// C leaves of 2 .. kFewPairsMax pairs: the sum of their units' exact
+// integers, converted once with the leaf's line exponents.  One CTA per leaf;
+// `fewunits` packs (product << 32) | leaf for a batch (works non-null).
+__global__ void __launch_bounds__(256)
+    k_few_sum(const SingleWork single, const SingleWork *__restrict__ works, int32_t nworks,
+              const int64_t *__restrict__ fewunits, int64_t ntotal, int *__restrict__ status) {
+  for (int64_t u = blockIdx.x; u < ntotal; u += gridDim.x) {
+    const SingleWork *wp = &single;
+    int64_t f = u;
+    if (works) {
+      const int64_t packed = fewunits[u];
+      if (!CHT_INDEX_OK((packed >> 32) >= 0 && (packed >> 32) < nworks, status)) continue;
+      wp = &works[packed >> 32];
+      f = packed & 0xffffffffLL;
+    }
+    const SingleWork &w = *wp;
+    if (!CHT_INDEX_OK(f < w.nfew, status)) continue;
+    const int32_t o = w.few_c[f], v0 = w.few_v[f], m = w.few_m[f];
+    if (!CHT_INDEX_OK(o >= 0 && o < w.nC && v0 >= 0 && m >= 2 && m <= kFewPairsMax &&
+                          static_cast<int64_t>(v0) + m <= w.nvirt,
+                      status))
+      continue;
+    const int64_t I = w.crow[o], J = w.ccol[o];
+    if (!CHT_INDEX_OK(I >= 0 && I < w.G && J >= 0 && J < w.G, status)) continue;
+    const int64_t *src = w.scratch + static_cast<int64_t>(v0) * 1024;
+    double *dst = w.C + static_cast<int64_t>(o) * 1024;
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+      long long t = 0;
+      for (int j = 0; j < m; ++j) t += src[j * 1024 + e];
+      // (an empty line of A or B has zero digits: t = 0 converts to +0)
+      const int e2 = static_cast<int>(static_cast<uint32_t>(w.row_exp[I * 32 + (e >> 5)]) +
+                                      static_cast<uint32_t>(w.col_exp[J * 32 + (e & 31)]) - 56u);
+      bool ok;
+      const double x = scaled_i64_fast(t, e2, &ok);
+      dst[e] = ok ? x : scaled_i64_to_double(t, e2);
     }
   }
 }
 
 struct SingleGroups {
-  DevArray<int32_t> gb, ga, gc;  // per group: B leaf; 4 A leaves; 4 C leaves (-1: none)
-  DevArray<int64_t> more;        // C leaves with two or more pairs
-  int64_t ngroups = 0, nmore = 0, nsingle = 0;
+  DevArray<int32_t> gb, ga, gc;  // per group: B leaf; 4 A leaves; 4 units (see SingleWork::gc)
+  DevArray<int64_t> more;        // C leaves with more than kFewPairsMax pairs
+  DevArray<int32_t> few_c, few_v, few_m;  // C leaves of 2 .. kFewPairsMax pairs
+  int64_t ngroups = 0, nmore = 0, nsingle = 0, nfew = 0, nvirt = 0;
 };
 
 int build_single_groups(const cht_plan *plan, cudaStream_t s, SingleGroups &g) {
   const int64_t nC = plan->C->nnz, nB = plan->nB;
-  if (plan->n_one < 0 || plan->n_groups < 0 || plan->one_pair_b.p == nullptr) {
-    set_error("the plan carries no one-pair counts (a 32-leaf plan from the symbolic phase does)");
+  if (plan->n_one < 0 || plan->n_few < 0 || plan->n_virt < 0 || plan->n_groups < 0 ||
+      plan->one_pair_b.p == nullptr) {
+    set_error("the plan carries no unit counts (a 32-leaf plan from the symbolic phase does)");
     return CHT_ERR_INVALID;
   }
   g.nsingle = plan->n_one;
-  g.nmore = nC - plan->n_one;
+  g.nfew = plan->n_few;
+  g.nvirt = plan->n_virt;
+  g.nmore = nC - plan->n_one - plan->n_few;
   g.ngroups = plan->n_groups;
   const int64_t ng = g.ngroups;
   DevArray<int64_t> gstart;
   DevArray<int32_t> fill;
-  DevArray<unsigned long long> nmore;
+  DevArray<unsigned long long> counters;
   CHT_TRY(gstart.alloc(nB + 1, s));
   CHT_TRY(fill.alloc(nB, s));
-  CHT_TRY(nmore.alloc(1, s));
+  CHT_TRY(counters.alloc(3, s));
   CHT_TRY(g.gb.alloc(ng, s));
   CHT_TRY(g.ga.alloc(4 * ng, s));
   CHT_TRY(g.gc.alloc(4 * ng, s));
   CHT_TRY(g.more.alloc(g.nmore, s));
+  CHT_TRY(g.few_c.alloc(g.nfew, s));
+  CHT_TRY(g.few_v.alloc(g.nfew, s));
+  CHT_TRY(g.few_m.alloc(g.nfew, s));
   if (nC == 0) return CHT_OK;
   CHT_TRY(scan_exclusive_fn(GroupsOf{plan->one_pair_b.p}, nB, gstart.p, s));
   CHT_CUDA_TRY(cudaMemsetAsync(fill.p, 0, sizeof(int32_t) * nB, s));
-  CHT_CUDA_TRY(cudaMemsetAsync(nmore.p, 0, sizeof(unsigned long long), s));
+  CHT_CUDA_TRY(cudaMemsetAsync(counters.p, 0, sizeof(unsigned long long) * 3, s));
   CHT_CUDA_TRY(cudaMemsetAsync(g.ga.p, 0, sizeof(int32_t) * 4 * ng, s));
   CHT_CUDA_TRY(cudaMemsetAsync(g.gc.p, 0xff, sizeof(int32_t) * 4 * ng, s));  // -1
-  k_group_place<<<grid_for(nC, 256), 256, 0, s>>>(plan->cseg.p, nC, plan->pa.p, plan->pb.p,
-                                                  gstart.p, fill.p, nmore.p, g.gb.p, g.ga.p,
-                                                  g.gc.p, g.more.p);
+  k_group_place<<<grid_for(nC, 256), 256, 0, s>>>(
+      plan->cseg.p, nC, plan->pa.p, plan->pb.p, gstart.p, fill.p, counters.p, g.gb.p, g.ga.p,
+      g.gc.p, g.more.p, g.few_c.p, g.few_v.p, g.few_m.p);
   return launched("group_place");
+}
+
+int launch_few_sum(const SingleWork &w, const SingleWork *works, int32_t nworks,
+                   const int64_t *fewunits, int64_t ntotal, cudaStream_t s) {
+  if (ntotal <= 0) return CHT_OK;
+  int *status = nullptr;
+  CHT_TRY(device_status_ptr(&status));
+  int sms = 0;
+  CHT_TRY(num_sms(&sms));
+  const int64_t grid = std::min<int64_t>(ntotal, 16LL * std::max(sms, 1));
+  k_few_sum<<<static_cast<unsigned>(grid), 256, 0, s>>>(w, works, nworks, fewunits, ntotal,
+                                                        status);
+  return launched("few_sum");
 }
 
 // One launch over `ntotal` groups: those of `w` (works NULL), or the groups
@@ -2011,7 +2119,7 @@ __global__ void k_pack_list(int64_t n, int64_t prod, const int64_t *__restrict__
 
 // The one-pair kernel's view of one product.
 SingleWork make_single_work(const cht_plan *plan, const Operands &op, const SingleGroups &g,
-                            double *Cvals) {
+                            const Pattern &bpat, double *Cvals, int64_t *scratch) {
   SingleWork sw{};
   sw.a_slices = op.a_sl.p;
   sw.b_slices = op.b_sl.p;
@@ -2022,8 +2130,15 @@ SingleWork make_single_work(const cht_plan *plan, const Operands &op, const Sing
   sw.ccol = plan->C->bcol.p;
   sw.row_exp = op.row_exp.p;
   sw.col_exp = op.col_exp.p;
+  sw.bcol = bpat.bcol.p;
   sw.C = Cvals;
+  sw.scratch = scratch;
+  sw.few_c = g.few_c.p;
+  sw.few_v = g.few_v.p;
+  sw.few_m = g.few_m.p;
   sw.ngroups = g.ngroups;
+  sw.nfew = g.nfew;
+  sw.nvirt = g.nvirt;
   sw.nA = plan->nA;
   sw.nB = plan->nB;
   sw.nC = plan->C->nnz;
@@ -2054,6 +2169,9 @@ struct SplitBatch {
   DevArray<SingleWork> works;      // the one-pair kernel's product table
   DevArray<int64_t> gunits;        // (product << 32) | group, every one-pair product
   int64_t ngunits = 0;
+  std::vector<DevArray<int64_t>> scratch;  // per product: few-pair units' integers
+  DevArray<int64_t> fewunits;      // (product << 32) | few-pair leaf
+  int64_t nfewunits = 0;
   DevArray<unsigned long long> counter;
   int maxb = 32;
 };
@@ -2102,10 +2220,14 @@ int split_multiply(cht_plan *plan, cht_mat *A, cht_mat *B, int nslices, cudaStre
     nunits = pu.nv;
   }
   if (one_pair) {
-    // one-pair C leaves grouped by B leaf; the others by the general kernel
+    // the pairs of C leaves with at most kFewPairsMax pairs grouped by B
+    // leaf (and the few-pair leaves' sums); the others by the general kernel
     const SingleGroups *g = groups;
-    const SingleWork sw = make_single_work(plan, op, *g, Cvals);
+    DevArray<int64_t> scratch;
+    CHT_TRY(scratch.alloc(static_cast<size_t>(g->nvirt) * 1024, s));
+    const SingleWork sw = make_single_work(plan, op, *g, *B->pat, Cvals, scratch.p);
     CHT_TRY(launch_single32(sw, nullptr, 0, nullptr, sw.ngroups, counter.p, s));
+    CHT_TRY(launch_few_sum(sw, nullptr, 0, nullptr, g->nfew, s));
     if (g->nmore > 0) CHT_TRY(launch_split<32>(d, nullptr, 0, g->more.p, g->nmore, counter.p, s));
     return CHT_OK;
   }
@@ -2134,6 +2256,7 @@ int split_batch_prepare(cht_batch *bt, cudaStream_t s) {
   sb->pieces.resize(bt->count);
   sb->has_pieces.assign(bt->count, 0);
   sb->one_pair.assign(bt->count, 0);
+  sb->scratch.resize(bt->count);
   bool own = false;
   for (int32_t i = 0; i < bt->count; ++i) {
     cht_plan *plan = bt->plans[i];
@@ -2155,9 +2278,12 @@ int split_batch_prepare(cht_batch *bt, cudaStream_t s) {
       // as cht_multiply: one-pair C leaves to the one-pair kernel
       const SingleGroups *g = nullptr;
       CHT_TRY(plan_groups(plan, s, &g));
-      works[i] = make_single_work(plan, sb->ops[i], *g, bt->views[i]->view_vals);
+      CHT_TRY(sb->scratch[i].alloc(static_cast<size_t>(g->nvirt) * 1024, s));
+      works[i] = make_single_work(plan, sb->ops[i], *g, *bt->Bs[i]->pat,
+                                  bt->views[i]->view_vals, sb->scratch[i].p);
       sb->one_pair[i] = 1;
       sb->ngunits += g->ngroups;
+      sb->nfewunits += g->nfew;
       own = true;
     }
   }
@@ -2171,13 +2297,14 @@ int split_batch_prepare(cht_batch *bt, cudaStream_t s) {
                : sb->one_pair[i] ? g->nmore
                                  : bt->plans[i]->C->nnz;
     }
-    if (total > 0x7fffffffLL || sb->ngunits > 0x7fffffffLL) {
+    if (total > 0x7fffffffLL || sb->ngunits > 0x7fffffffLL || sb->nfewunits > 0x7fffffffLL) {
       set_error("batch has too many work units");
       return CHT_ERR_UNSUPPORTED;
     }
     CHT_TRY(sb->units.alloc(total, s));
     CHT_TRY(sb->gunits.alloc(sb->ngunits, s));
-    int64_t off = 0, goff = 0;
+    CHT_TRY(sb->fewunits.alloc(sb->nfewunits, s));
+    int64_t off = 0, goff = 0, foff = 0;
     for (int32_t i = 0; i < bt->count; ++i) {
       const SingleGroups *g = static_cast<const SingleGroups *>(bt->plans[i]->split_groups.get());
       if (sb->one_pair[i]) {
@@ -2193,6 +2320,12 @@ int split_batch_prepare(cht_batch *bt, cudaStream_t s) {
           CHT_TRY(launched("pack_units"));
         }
         goff += g->ngroups;
+        if (g->nfew > 0) {
+          k_pack_units<<<grid_for(g->nfew, 256), 256, 0, s>>>(g->nfew, i, foff,
+                                                              sb->fewunits.p);
+          CHT_TRY(launched("pack_units"));
+        }
+        foff += g->nfew;
         continue;
       }
       const int64_t n = sb->has_pieces[i] ? sb->pieces[i].nv : bt->plans[i]->C->nnz;
@@ -2231,6 +2364,7 @@ int split_batch_run(cht_batch *bt, cudaStream_t s) {
   if (sb->ngunits > 0)
     CHT_TRY(launch_single32(SingleWork{}, sb->works.p, bt->count, sb->gunits.p, sb->ngunits,
                             sb->counter.p, s));
+  CHT_TRY(launch_few_sum(SingleWork{}, sb->works.p, bt->count, sb->fewunits.p, sb->nfewunits, s));
   if (sb->maxb == 64)
     CHT_TRY(launch_split<64>(none, sb->prods.p, bt->count, units, nunits, sb->counter.p, s));
   else

@@ -120,22 +120,29 @@ __global__ void k_lpt_keys(const int64_t *__restrict__ seg, int64_t n, int64_t c
 }
 
 // Statistics of the *d_n C leaves (count read on the device): stats[0] = the
-// count, stats[1] = the longest segment, stats[2] = the C leaves of one pair;
-// with cntB, each such leaf counts on its B leaf; with rowcnt, every leaf
-// counts on its leaf row and column.
+// count, stats[1] = the longest segment, stats[2] = the C leaves of one pair,
+// stats[5] = those of 2 .. kFewPairsMax pairs, stats[6] = their pairs; with
+// cntB, every pair of those leaves counts on its B leaf; with rowcnt, every
+// leaf counts on its leaf row and column.
 __global__ void k_c_stats(const int64_t *__restrict__ seg, const uint64_t *__restrict__ ckey,
                           const int64_t *__restrict__ d_n, const int32_t *__restrict__ pb,
                           int32_t *__restrict__ cntB, int32_t *__restrict__ rowcnt,
                           int32_t *__restrict__ colcnt, unsigned long long *__restrict__ stats) {
   const int64_t n = *d_n;
   if (blockIdx.x == 0 && threadIdx.x == 0) stats[0] = static_cast<unsigned long long>(n);
-  unsigned long long m = 0, ones = 0;
+  unsigned long long m = 0, ones = 0, few = 0, virt = 0;
   GRID_STRIDE(u, n) {
     const int64_t p0 = seg[u], len = seg[u + 1] - p0;
     m = max(m, static_cast<unsigned long long>(len));
-    if (len == 1) {
-      ++ones;
-      if (cntB) atomicAdd(&cntB[pb[p0]], 1);
+    if (len <= kFewPairsMax) {
+      if (len == 1) {
+        ++ones;
+      } else {
+        ++few;
+        virt += static_cast<unsigned long long>(len);
+      }
+      if (cntB)
+        for (int64_t j = 0; j < len; ++j) atomicAdd(&cntB[pb[p0 + j]], 1);
     }
     if (rowcnt) {
       atomicAdd(&rowcnt[morton_row(ckey[u])], 1);
@@ -146,14 +153,18 @@ __global__ void k_c_stats(const int64_t *__restrict__ seg, const uint64_t *__res
   for (int o = 16; o > 0; o >>= 1) {
     m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     ones += __shfl_xor_sync(0xffffffffu, ones, o);
+    few += __shfl_xor_sync(0xffffffffu, few, o);
+    virt += __shfl_xor_sync(0xffffffffu, virt, o);
   }
   if ((threadIdx.x & 31) == 0) {
     if (m) atomicMax(&stats[1], m);
     if (ones) atomicAdd(&stats[2], ones);
+    if (few) atomicAdd(&stats[5], few);
+    if (virt) atomicAdd(&stats[6], virt);
   }
 }
 
-// Groups of up to four one-pair C leaves per B leaf: sum of ceil(cnt / 4).
+// Groups of up to four units per B leaf: sum of ceil(cnt / 4).
 __global__ void k_group_count(const int32_t *__restrict__ cntB, int64_t nB,
                               unsigned long long *__restrict__ out) {
   unsigned long long g = 0;
@@ -414,11 +425,14 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   plan->patB = B.id;
 
   // statistics read in the phase's one synchronisation: [0] C leaves, [1]
-  // longest segment, [2] one-pair C leaves, [3] their groups (32-leaves),
-  // [4] the device's pair total (checked against the host's count)
+  // longest segment, [2] one-pair C leaves, [3] the groups of the split
+  // form's units (32-leaves), [4] the device's pair total (checked against
+  // the host's count), [5] C leaves of 2 .. kFewPairsMax pairs, [6] their
+  // pairs
+  constexpr int kStats = 7;
   DevArray<int64_t> stats;
-  CHT_TRY(stats.alloc(5, s));
-  CHT_CUDA_TRY(cudaMemsetAsync(stats.p, 0, sizeof(int64_t) * 5, s));
+  CHT_TRY(stats.alloc(kStats, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(stats.p, 0, sizeof(int64_t) * kStats, s));
   DevArray<uint64_t> skey;
   DevArray<int32_t> pa, pb;
   int64_t P = 0;
@@ -438,8 +452,9 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   CHT_TRY(C->bcol.alloc(P, s));
   CHT_TRY(plan->cseg.alloc(P + 1, s));
   CHT_TRY(plan->pc.alloc(P, s));
-  // per-B-leaf counts of one-pair C leaves (32-leaves: the split form's
-  // groups), and the C pattern's leaf counts per row and column
+  // per-B-leaf counts of the split form's units (32-leaves: the pairs of C
+  // leaves with at most kFewPairsMax pairs), and the C pattern's leaf
+  // counts per row and column
   const bool groups = A.b == 32 && B.nnz > 0;
   const int64_t G = A.G;
   const bool counts = G <= kMaxCountG;
@@ -469,7 +484,7 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   } else {
     CHT_CUDA_TRY(cudaMemsetAsync(plan->cseg.p, 0, sizeof(int64_t), s));
   }
-  int64_t host_stats[5] = {0, 0, 0, 0, 0};
+  int64_t host_stats[kStats] = {};
   CHT_CUDA_TRY(cudaMemcpyAsync(host_stats, stats.p, sizeof(host_stats), cudaMemcpyDeviceToHost, s));
   if (counts) {
     C->rowcnt.resize(G);
@@ -490,6 +505,8 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   if (groups) {
     plan->n_one = host_stats[2];
     plan->n_groups = host_stats[3];
+    plan->n_few = host_stats[5];
+    plan->n_virt = host_stats[6];
     plan->one_pair_b = std::move(cntB);
   }
 
