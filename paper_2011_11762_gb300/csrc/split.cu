@@ -652,11 +652,54 @@ __device__ inline int16_t exp16(int e) {
   return e == kNoExp ? kNoExp16 : static_cast<int16_t>(max(-32000, min(32000, e)));
 }
 
+// One MMA over all K-steps of a leaf pair: A slices u, u + 1 (M = 128) and
+// the nb B slices from j on (N = b nb), into TMEM column 64 (u + j - 2); the
+// first K-step overwrites when `start`.  (Column block c of the accumulator
+// holds diagonal c + 2 + part, so the B slices side by side land on their
+// diagonals' blocks.)
+template <int NB>
+__device__ __forceinline__ void mma64(uint32_t sa, uint32_t sb, uint32_t tmem, int u, int j,
+                                      bool start) {
+  constexpr uint32_t IDESC = make_idesc(128, 64 * NB);
+  const uint64_t ad = tile_desc<64>(sa + (u - 1) * Smem<64>::TILE);
+  const uint64_t bd = tile_desc<64>(sb + (j - 1) * Smem<64>::TILE);
+  const uint32_t dt = tmem + static_cast<uint32_t>(64 * (u + j - 2));
+#pragma unroll
+  for (int kk = 0; kk < Cfg<64>::KSTEPS; ++kk)
+    tc_mma(dt, ad + 2 * kk, bd + 2 * kk, IDESC, (start && kk == 0) ? 0u : 1u);
+}
+
 // The MMA blocks of one leaf pair from stage (sa: A slices, sb: B slices).
 // which = 0: all blocks; 1: the blocks of region 2 only; 2: regions 0, 1.
+// At b = 64 the slice products are issued as wide MMAs over B slices side
+// by side: (A1,2 x B5,6), (A1,2 x B1..4), (A3,4 x B1..4), (A5,6 x B1,2) for
+// all regions -- 4 MMAs per K-step instead of 6 blocks, the same 24 slice
+// products, each region first written with overwrite -- and, when only one
+// side may go (the look-ahead of region 2 before the exact regions are
+// released), (A1,2 x B5,6), (A3,4 x B3,4), (A5,6 x B1,2) for region 2 and
+// (A1,2 x B1..4), (A3,4 x B1,2) for regions 0, 1.
 template <int B>
 __device__ __forceinline__ void issue_blocks(uint32_t sa, uint32_t sb, uint32_t tmem,
                                              bool (&fresh)[kRegions], int which) {
+  if constexpr (B == 64) {
+    if (which == 0) {
+      mma64<2>(sa, sb, tmem, 1, 5, fresh[2]);
+      mma64<4>(sa, sb, tmem, 1, 1, fresh[0]);
+      mma64<4>(sa, sb, tmem, 3, 1, false);
+      mma64<2>(sa, sb, tmem, 5, 1, false);
+      fresh[0] = fresh[1] = fresh[2] = false;
+    } else if (which == 1) {
+      mma64<2>(sa, sb, tmem, 1, 5, fresh[2]);
+      mma64<2>(sa, sb, tmem, 3, 3, false);
+      mma64<2>(sa, sb, tmem, 5, 1, false);
+      fresh[2] = false;
+    } else {
+      mma64<4>(sa, sb, tmem, 1, 1, fresh[0]);
+      mma64<2>(sa, sb, tmem, 3, 1, false);
+      fresh[0] = fresh[1] = false;
+    }
+    return;
+  }
   using CF = Cfg<B>;
   using SM = Smem<B>;
   constexpr int N = CF::N;
