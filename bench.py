@@ -450,7 +450,7 @@ def section_split(args, world, cht, torch):
         t_tensor = alg_flops / (peak_bf16 * 1e12)
         t_hbm = alg_bytes / (hbm * 1e9)
         prof = read_profile_traffic("split_gemm_3d_locality" if b_ == 64
-                                    else "split_gemm_random_b32")
+                                    else "split_single32_random_b32")
         traffic = (float(prof["dram_bytes_per_pair"]) * plan.npairs
                    if prof and "dram_bytes_per_pair" in prof else None)
         if t_tensor >= t_hbm:
