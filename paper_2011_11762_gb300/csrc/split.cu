@@ -1345,14 +1345,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 // device counter; per group one bulk copy of the B leaf's 6 slice tiles, and
 // the 24 A tiles -- which land in [slice][unit] order, so no single bulk copy
 // can fetch a unit's six -- as 16-byte cp.async copies spread over the 32
-// lanes), warp 1 MMA issuer (one thread), warps 2..17 epilogue (four warps per
-// lane quarter, 8 columns each: the epilogue's integer assembly and
-// conversion set the pace, and four warps per scheduler hide their
-// latencies).  Two accumulator sets of 192 columns: the MMAs of group n + 1
-// run while the epilogue reads group n; the epilogue reads the six regions in
-// one round trip, releases its set, then assembles, converts and stores
-// (through a per-warp staging block, as whole row pieces).  Every wait is
-// bounded.
+// lanes), warp 1 MMA issuer (one thread), warps 2..17 epilogue in two teams
+// of 8 that take alternate groups (the epilogue's integer assembly and
+// conversion set the pace: while one team waits for its group's slot,
+// exponents or accumulators, the other computes), each team two warps per
+// lane quarter, 16 columns each.  Two accumulator sets of 192 columns, one
+// per team: the MMAs of group n + 1 run while the other team reads group n;
+// a warp reads the six regions (8 columns at a time), releases its set, then
+// assembles, converts and stores (through a per-warp staging block, as whole
+// row pieces).  After the last group the producer publishes one end slot per
+// team.  Every wait is bounded.
 namespace single32 {
 constexpr int kStages = 3;
 constexpr int kTile = Smem<32>::TILE;                 // 2 KB
@@ -1362,23 +1364,21 @@ constexpr int kB = kSB * kTile;                       // 12 KB
 constexpr int kStage = kA + kB;
 constexpr int kRegionsS = 6;                          // diagonals 2..7
 constexpr int kSetCols = 256;                         // accumulator set pitch (192 used)
-// 16 epilogue warps (four per TMEM lane quarter, 8 columns each): 18 warps
+// 16 epilogue warps in two teams of 8 taking alternate groups (team t the
+// groups n with n % 2 == t, in accumulator set t), so that one team's waits
+// hide behind the other's arithmetic; in a team two warps per TMEM lane
+// quarter, 16 columns each, handled 8 at a time: 18 warps in all
 constexpr int kEpi = 16;
+constexpr int kTeams = 2;
+constexpr int kTeamWarps = kEpi / kTeams;
 constexpr int kThreadsS = (2 + kEpi) * 32;
-constexpr int kCols = 32 / (kEpi / 4);                // columns per epilogue warp
-// per epilogue warp: its 32 x 8 block of C values, rows padded to 9 doubles
+constexpr int kCols = 32 / (kTeamWarps / 4);           // columns per epilogue warp
+constexpr int kPiece = 8;                              // columns converted and stored together
+// per epilogue warp: a 32 x 8 block of C values, rows padded to 9 doubles
 // (few bank conflicts), for stores of whole 64-byte row pieces
-constexpr int kStgPitch = kCols + 1;
+constexpr int kStgPitch = kPiece + 1;
 constexpr int kStgBytes = 32 * kStgPitch * 8;
 constexpr int kChunk = 8;                             // groups per counter step
-constexpr int kNPairs = 21;
-// the pairs (i, j), i + j <= 7, diagonal by diagonal (t = 2, 3, ..., 7)
-__device__ constexpr int pair_t(int x) {
-  return x < 1 ? 2 : x < 3 ? 3 : x < 6 ? 4 : x < 10 ? 5 : x < 15 ? 6 : 7;
-}
-__device__ constexpr int pair_i(int x) {
-  return x - (x < 1 ? 0 : x < 3 ? 1 : x < 6 ? 3 : x < 10 ? 6 : x < 15 ? 10 : 15) + 1;
-}
 }  // namespace single32
 
 struct SingleWork {
@@ -1447,11 +1447,11 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
     }
     for (int i = 0; i < kQueue; ++i) {
       mbar_init(&qfull[i], 1);
-      mbar_init(&qempty[i], 1 + kEpi);
+      mbar_init(&qempty[i], 1 + kTeamWarps);
     }
     for (int bf = 0; bf < 2; ++bf) {
       mbar_init(&acc_full[bf], 1);
-      mbar_init(&acc_empty[bf], kEpi);
+      mbar_init(&acc_empty[bf], kTeamWarps);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -1531,9 +1531,22 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
         GSlot &sl = queue[qs];
         const int valid = __shfl_sync(0xffffffffu, valid_l ? 1 : 0, j);
         if (!valid) {
+          // one end slot per epilogue team (each team reads every other slot)
           if (lane == 0) {
             sl.count = 0;
             mbar_arrive(&qfull[qs]);
+          }
+          for (uint32_t t = 1; t < static_cast<uint32_t>(kTeams); ++t) {
+            const uint32_t qe = (n + t) % kQueue, qeph = ((n + t) / kQueue) & 1u;
+            const bool ok_e = wait_or_abort(&qempty[qe], qeph ^ 1u, wait_ns, abort_flag);
+            if (!__shfl_sync(0xffffffffu, ok_e ? 1 : 0, 0)) {
+              if (lane == 0) fail();
+              break;
+            }
+            if (lane == 0) {
+              queue[qe].count = 0;
+              mbar_arrive(&qfull[qe]);
+            }
           }
           done = true;
           break;
@@ -1672,10 +1685,13 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
     }
   } else {
     // -------------------------------------------------------- epilogue --
+    const int e = warp - 2;                     // epilogue warp 0..15
+    const int team = e / kTeamWarps;            // takes the groups n = team, team + 2, ..
     const int q = warp & 3;                     // lane quarter = unit of the group
-    const int c0 = ((warp - 2) >> 2) * kCols;   // this warp's kCols columns
+    const int c0 = ((e % kTeamWarps) >> 2) * kCols;  // this warp's kCols columns
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * q) << 16);
-    for (uint32_t n = 0;; ++n) {
+    double *stg = staging + e * 32 * kStgPitch;
+    for (uint32_t n = static_cast<uint32_t>(team);; n += kTeams) {
       const uint32_t qs = n % kQueue, qph = (n / kQueue) & 1u;
       if (!warp_wait_or_abort(&qfull[qs], qph, wait_ns, abort_flag)) {
         fail();
@@ -1692,79 +1708,88 @@ __global__ void __launch_bounds__(single32::kThreadsS, 1)
 #pragma unroll
       for (int c = 0; c < kCols; ++c)
         fc[c] = sl.col_exp[static_cast<int64_t>(sl.ccol) * 32 + c0 + c];
-      const uint32_t bf = n & 1u, use = n >> 1;
+      const uint32_t bf = n & 1u, use = n >> 1;  // (bf == team)
       if (!warp_wait_or_abort(&acc_full[bf], use & 1u, wait_ns, abort_flag)) {
         fail();
         break;
       }
       tc_fence_after();
-      // the six diagonals, most significant first: T <- 2^8 T + S_t (all six
-      // regions in one TMEM round trip)
-      const uint32_t base = lane_base + bf * kSetCols + c0;
-      float v[kRegionsS][kCols];
+      // the six diagonals of 8 columns at a time (all six regions in one TMEM
+      // round trip).  A region holds an integer of magnitude below 2^22:
+      // adding 1.5 * 2^23 moves it, exactly, into [2^23, 2^24), where the
+      // float's bit pattern is 0x4B400000 plus the integer (no
+      // float-to-integer conversion); two regions combine in 32 bits
+      // (S_t 2^8 + S_t+1 < 2^31 in magnitude) and the three pairs in 64:
+      // T = P_0 2^32 + P_1 2^16 + P_2
+      long long T[kCols];
 #pragma unroll
-      for (int r = 0; r < kRegionsS; ++r) tmem_ld8(base + static_cast<uint32_t>(r * 32), v[r]);
-      tc_wait_ld();
+      for (int h = 0; h < kCols / kPiece; ++h) {
+        const uint32_t base = lane_base + bf * kSetCols + c0 + h * kPiece;
+        float v[kRegionsS][kPiece];
+#pragma unroll
+        for (int r = 0; r < kRegionsS; ++r) tmem_ld8(base + static_cast<uint32_t>(r * 32), v[r]);
+        tc_wait_ld();
+#pragma unroll
+        for (int c = 0; c < kPiece; ++c) {
+          uint32_t u[kRegionsS];
+#pragma unroll
+          for (int r = 0; r < kRegionsS; ++r) u[r] = __float_as_uint(v[r][c] + 12582912.0f);
+          constexpr uint32_t kBias = 257u * 0x4B400000u;  // both offsets of a pair
+          const int p0 = static_cast<int>(u[0] * 256u + u[1] - kBias);
+          const int p1 = static_cast<int>(u[2] * 256u + u[3] - kBias);
+          const int p2 = static_cast<int>(u[4] * 256u + u[5] - kBias);
+          T[h * kPiece + c] = static_cast<long long>(p0) * 0x100000000LL +
+                              static_cast<long long>(p1) * 0x10000LL + p2;
+        }
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[bf]);  // the MMA may reuse this set
-      // a region holds an integer of magnitude below 2^22: adding 1.5 * 2^23
-      // moves it, exactly, into [2^23, 2^24), where the float's bit pattern
-      // is 0x4B400000 plus the integer (no float-to-integer conversion); two
-      // regions combine in 32 bits (S_t 2^8 + S_t+1 < 2^31 in magnitude) and
-      // the three pairs in 64: T = P_0 2^32 + P_1 2^16 + P_2
-      long long T[kCols];
-#pragma unroll
-      for (int c = 0; c < kCols; ++c) {
-        uint32_t u[kRegionsS];
-#pragma unroll
-        for (int r = 0; r < kRegionsS; ++r) u[r] = __float_as_uint(v[r][c] + 12582912.0f);
-        constexpr uint32_t kBias = 257u * 0x4B400000u;  // both offsets of a pair
-        const int p0 = static_cast<int>(u[0] * 256u + u[1] - kBias);
-        const int p1 = static_cast<int>(u[2] * 256u + u[3] - kBias);
-        const int p2 = static_cast<int>(u[4] * 256u + u[5] - kBias);
-        T[c] = static_cast<long long>(p0) * 0x100000000LL + static_cast<long long>(p1) * 0x10000LL + p2;
-      }
       if (Cq) {
         // convert this lane's row (its own exponents), stage the warp's
-        // 32 x kCols block, and store it as row pieces of kCols doubles
+        // 32 x 8 block, and store it as row pieces of 8 doubles; twice
         // (a line without stored values -- exponent kNoExp -- has zero
         // digits, so T = 0 there and converts to +0 whatever the exponent)
-        double *stg = staging + (warp - 2) * 32 * kStgPitch;
         const uint32_t eb = static_cast<uint32_t>(er) - 56u;
-        bool good = true;
-        if (raw) {
-          // the integers themselves (their bit patterns pass through the
-          // staging block and the stores unchanged)
 #pragma unroll
-          for (int c = 0; c < kCols; ++c) stg[lane * kStgPitch + c] = __longlong_as_double(T[c]);
-        } else {
+        for (int h = 0; h < kCols / kPiece; ++h) {
+          bool good = true;
+          if (raw) {
+            // the integers themselves (their bit patterns pass through the
+            // staging block and the stores unchanged)
 #pragma unroll
-          for (int c = 0; c < kCols; ++c) {
-            bool ok;
-            const double x =
-                scaled_i64_fast(T[c], static_cast<int>(eb + static_cast<uint32_t>(fc[c])), &ok);
-            good = good && ok;
-            stg[lane * kStgPitch + c] = x;
+            for (int c = 0; c < kPiece; ++c)
+              stg[lane * kStgPitch + c] = __longlong_as_double(T[h * kPiece + c]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < kPiece; ++c) {
+              bool ok;
+              const double x = scaled_i64_fast(
+                  T[h * kPiece + c],
+                  static_cast<int>(eb + static_cast<uint32_t>(fc[h * kPiece + c])), &ok);
+              good = good && ok;
+              stg[lane * kStgPitch + c] = x;
+            }
           }
-        }
-        if (!__all_sync(0xffffffffu, good)) {
-          // a result outside the normal range of doubles somewhere in the
-          // warp (rare): the exact general conversion for this lane's row
+          if (!__all_sync(0xffffffffu, good)) {
+            // a result outside the normal range of doubles somewhere in the
+            // warp (rare): the exact general conversion for this lane's row
 #pragma unroll
-          for (int c = 0; c < kCols; ++c)
-            stg[lane * kStgPitch + c] = scaled_i64_to_double(
-                T[c], static_cast<int>(eb + static_cast<uint32_t>(fc[c])));
-        }
-        __syncwarp();
-        constexpr int kRowsPer = 32 / kCols;  // rows stored by one instruction
-        const int col = lane % kCols, sub = lane / kCols;
+            for (int c = 0; c < kPiece; ++c)
+              stg[lane * kStgPitch + c] = scaled_i64_to_double(
+                  T[h * kPiece + c],
+                  static_cast<int>(eb + static_cast<uint32_t>(fc[h * kPiece + c])));
+          }
+          __syncwarp();
+          constexpr int kRowsPer = 32 / kPiece;  // rows stored by one instruction
+          const int col = lane % kPiece, sub = lane / kPiece;
 #pragma unroll
-        for (int k = 0; k < 32 / kRowsPer; ++k) {
-          const int row = kRowsPer * k + sub;
-          Cq[row * 32 + c0 + col] = stg[row * kStgPitch + col];
+          for (int k = 0; k < 32 / kRowsPer; ++k) {
+            const int row = kRowsPer * k + sub;
+            Cq[row * 32 + c0 + h * kPiece + col] = stg[row * kStgPitch + col];
+          }
+          __syncwarp();  // the staging block is read before it is written again
         }
-        __syncwarp();  // the staging block is read before the next group writes it
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&qempty[qs]);

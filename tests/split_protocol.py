@@ -84,6 +84,7 @@ class Config:
     stages: int    # operand stages
     windows: dict  # pairs per exact window, by leaf size
     kind: str = "general"  # "one_pair": the kernel of one-pair C leaves
+    teams: int = 1  # one-pair kernel: epilogue teams taking alternate groups
 
 
 # the kernel taking 64-leaves (and 32-leaf units of mixed batches), and the
@@ -93,7 +94,7 @@ KERNEL_32 = Config(nb=2, nxb=2, stages=4, windows={32: 32})
 # k_split_single32: groups of up to 4 one-pair C leaves sharing a B leaf; two
 # accumulator sets of 6 regions (group n uses set n % 2), each read whole and
 # released by every epilogue warp before it stores; no exchange buffer
-ONE_PAIR = Config(nb=2, nxb=0, stages=3, windows={}, kind="one_pair")
+ONE_PAIR = Config(nb=2, nxb=0, stages=3, windows={}, kind="one_pair", teams=2)
 ONE_PAIR_REGIONS = 6
 
 
@@ -339,14 +340,20 @@ def kernel_roles(st: State, units, mistakes=frozenset()):
 def one_pair_roles(st: State, groups, mistakes=frozenset()):
     """Generators for the roles of k_split_single32 (same conventions as
     kernel_roles).  ``groups`` lists the units of each group this CTA takes
-    (1..4); the protocol does not depend on them.  Per group: the producer
-    stages the slot and one operand stage; the MMA thread waits for the
-    epilogue's release of the group before last (the previous user of the
-    same accumulator set), then for the stage, and restarts that set's six
-    regions; every epilogue warp reads all six regions of the group's set,
-    releases them, then stores (reading the slot) and frees the slot."""
+    (1..4); the protocol does not depend on them.  The 16 epilogue warps form
+    ``cfg.teams`` teams (of 8 with two teams); team t takes the groups n with
+    n % teams == t, and accumulator set n % 2 (with two teams: its own set).
+    Per group: the producer stages the slot and one operand stage; the MMA
+    thread waits for the release of the group before last (the previous user
+    of the same accumulator set), then for the stage, and restarts that set's
+    six regions; every warp of the group's team reads all six regions,
+    releases the set, then stores (reading the slot) and frees the slot.
+    After the last group the producer publishes one end slot per team, so
+    that every team meets one."""
     cfg = st.cfg
     S = cfg.stages
+    T = cfg.teams
+    W = EPI_WARPS_ONE_PAIR // T  # warps per team
     bars = st.bars
     for i in range(S):
         # the B copy's expect_tx arrival and one cp.async arrival per lane
@@ -354,16 +361,17 @@ def one_pair_roles(st: State, groups, mistakes=frozenset()):
         bars[f"empty{i}"] = Barrier(f"empty{i}", 1)
     for i in range(QUEUE):
         bars[f"qfull{i}"] = Barrier(f"qfull{i}", 1)
-        bars[f"qempty{i}"] = Barrier(f"qempty{i}", 1 + EPI_WARPS_ONE_PAIR)
+        bars[f"qempty{i}"] = Barrier(f"qempty{i}", 1 + W)
     for bf in range(cfg.nb):
         bars[f"acc_full{bf}"] = Barrier(f"acc_full{bf}", 1)
-        bars[f"acc_empty{bf}"] = Barrier(f"acc_empty{bf}", EPI_WARPS_ONE_PAIR)
+        bars[f"acc_empty{bf}"] = Barrier(f"acc_empty{bf}", W)
     bars["drain"] = Barrier("drain", 1)
-    everyone = frozenset(["mma"] + [f"epi{w}" for w in range(EPI_WARPS_ONE_PAIR)])
-    warps = frozenset(f"epi{w}" for w in range(EPI_WARPS_ONE_PAIR))
+    team_of = {f"epi{w}": w // W for w in range(EPI_WARPS_ONE_PAIR)}
+    team_warps = [frozenset(f"epi{w}" for w in range(t * W, (t + 1) * W)) for t in range(T)]
     slots = {}
     ngroups = len(groups)
     nb = cfg.nb
+    ends = 1 if "producer_single_end_slot" in mistakes else T
 
     def wait(name, phase, abortable=True):
         return ("wait", bars[name], phase, abortable)
@@ -374,7 +382,8 @@ def one_pair_roles(st: State, groups, mistakes=frozenset()):
 
     def producer():
         n = 0
-        for n in range(ngroups + 1):
+        staged = 0
+        for n in range(ngroups + ends):
             qs = n % QUEUE
             if not (yield wait(f"qempty{qs}", n // QUEUE - 1)):
                 fail()
@@ -384,10 +393,13 @@ def one_pair_roles(st: State, groups, mistakes=frozenset()):
                                     f"{sorted(st.slot_readers[qs])} still use it")
             count = groups[n] if n < ngroups else 0
             slots[qs] = (count, n)
-            st.slot_readers[qs] = set(everyone)
+            readers = set(team_warps[n % T])
+            if n <= ngroups:
+                readers.add("mma")  # the MMA thread stops at the first end slot
+            st.slot_readers[qs] = readers
             bars[f"qfull{qs}"].arrive()
             if count == 0:
-                break
+                continue
             yield None
             s = n % S
             if "producer_skips_empty_wait" not in mistakes:
@@ -404,8 +416,8 @@ def one_pair_roles(st: State, groups, mistakes=frozenset()):
             st.copies.append((bars[f"full{s}"], 1))
             lanes = LANES - 1 if "producer_one_lane_short" in mistakes else LANES
             st.copies.extend([(bars[f"full{s}"], None)] * lanes)
+            staged = n + 1
             yield None
-        staged = n if n < ngroups else ngroups
         if "producer_no_drain" not in mistakes:
             for j in range(max(0, staged - S), staged):
                 yield wait(f"full{j % S}", j // S, abortable=False)
@@ -436,7 +448,7 @@ def one_pair_roles(st: State, groups, mistakes=frozenset()):
                 if old and old[1]:
                     raise ProtocolError(f"region {r} restarted for group {n} while "
                                         f"{sorted(old[1])} have not read group {old[0]}")
-                st.readers[key] = (n, set(warps))
+                st.readers[key] = (n, set(team_warps[n % T]))
                 st.inflight.append(("mma", key))
             st.inflight.append(("commit", bars[f"empty{s}"], n))
             st.inflight.append(("commit", bars[f"acc_full{bf}"], None))
@@ -447,7 +459,9 @@ def one_pair_roles(st: State, groups, mistakes=frozenset()):
 
     def epilogue(wid):
         me = f"epi{wid}"
-        for n in range(ngroups + 1):
+        t = team_of[me]
+        n = t
+        while True:
             qs = n % QUEUE
             if not (yield wait(f"qfull{qs}", n // QUEUE)):
                 fail()
@@ -479,6 +493,7 @@ def one_pair_roles(st: State, groups, mistakes=frozenset()):
             if "epi_skips_slot_release" not in mistakes or wid != 3:
                 bars[f"qempty{qs}"].arrive()
             yield None
+            n += T
 
     roles = {"producer": producer(), "mma": mma()}
     for wid in range(EPI_WARPS_ONE_PAIR):

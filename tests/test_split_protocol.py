@@ -120,7 +120,8 @@ def test_one_pair_protocol_holds_under_random_schedules():
 
 @pytest.mark.parametrize("mistake", ["mma_skips_unit_wait", "epi_releases_before_last_region",
                                      "producer_skips_empty_wait", "epi_skips_slot_release",
-                                     "epi_single_accumulator_set", "producer_one_lane_short"])
+                                     "epi_single_accumulator_set", "producer_one_lane_short",
+                                     "producer_single_end_slot"])
 def test_one_pair_planted_mistakes_are_caught(mistake):
     groups = [4, 1, 3, 4, 2, 4, 4, 1, 4]
     caught = 0
