@@ -522,7 +522,6 @@ __global__ void __launch_bounds__(256) k_split_b(const double *__restrict__ vals
                                                  const int32_t *__restrict__ bcol,
                                                  int64_t nleaves, const int *__restrict__ col_exp,
                                                  uint8_t *__restrict__ out) {
-  constexpr int CH = B / 8;
   constexpr int TILE = Smem<B>::TILE;
   constexpr int OUT = SplitBSmem<B>::OUT;
   extern __shared__ __align__(16) uint8_t smem_b[];
@@ -539,28 +538,38 @@ __global__ void __launch_bounds__(256) k_split_b(const double *__restrict__ vals
     // reads of the previous leaf's image ended before every thread got here
     __syncthreads();
     const int64_t col0 = static_cast<int64_t>(bcol[leaf]) * B;
-    for (int q = threadIdx.x; q < B * CH; q += blockDim.x) {
-      const int n = q % B, c = q / B;
+    // work items of KV K values of one column: 8 (a 16-byte chunk) at
+    // b = 64, 4 (half a chunk) at b = 32, so that all 256 threads have one
+    constexpr int KV = B == 32 ? 4 : 8;
+    for (int q = threadIdx.x; q < B * (B / KV); q += blockDim.x) {
+      const int n = q % B, c = q / B;  // column, item (K values c*KV ..)
       const int f = col_exp[col0 + n];
-      int g[kSB][8];
+      int g[kSB][KV];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < KV; ++k) {
         bool neg;
-        const unsigned long long mag = fixed_mag(tile[c * 8 + k][n], f, kSB * kW, &neg);
+        const unsigned long long mag = fixed_mag(tile[c * KV + k][n], f, kSB * kW, &neg);
         int gk[kSB];
         balanced_digits<kSB>(mag, neg, gk);
 #pragma unroll
         for (int j = 0; j < kSB; ++j) g[j][k] = gk[j];
       }
-      uint8_t *base = img + tile_offset<B>(n, c);
+      uint8_t *base = img + tile_offset<B>(n, c * KV / 8) + (c * KV % 8) * 2;
 #pragma unroll
       for (int j = 0; j < kSB; ++j) {
-        uint4 v;
-        v.x = pack_bf16x2(g[j][0], g[j][1]);
-        v.y = pack_bf16x2(g[j][2], g[j][3]);
-        v.z = pack_bf16x2(g[j][4], g[j][5]);
-        v.w = pack_bf16x2(g[j][6], g[j][7]);
-        *reinterpret_cast<uint4 *>(base + j * TILE) = v;
+        if constexpr (KV == 8) {
+          uint4 v;
+          v.x = pack_bf16x2(g[j][0], g[j][1]);
+          v.y = pack_bf16x2(g[j][2], g[j][3]);
+          v.z = pack_bf16x2(g[j][4], g[j][5]);
+          v.w = pack_bf16x2(g[j][6], g[j][7]);
+          *reinterpret_cast<uint4 *>(base + j * TILE) = v;
+        } else {
+          uint2 v;
+          v.x = pack_bf16x2(g[j][0], g[j][1]);
+          v.y = pack_bf16x2(g[j][2], g[j][3]);
+          *reinterpret_cast<uint2 *>(base + j * TILE) = v;
+        }
       }
     }
     // the image is complete, and the staged leaf is no longer read
