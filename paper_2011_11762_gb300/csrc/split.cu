@@ -2093,15 +2093,43 @@ __global__ void __launch_bounds__(256)
     if (!CHT_INDEX_OK(I >= 0 && I < w.G && J >= 0 && J < w.G, status)) continue;
     const int64_t *src = w.scratch + static_cast<int64_t>(v0) * 1024;
     double *dst = w.C + static_cast<int64_t>(o) * 1024;
-    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
-      long long t = 0;
-      for (int j = 0; j < m; ++j) t += src[j * 1024 + e];
-      // (an empty line of A or B has zero digits: t = 0 converts to +0)
-      const int e2 = static_cast<int>(static_cast<uint32_t>(w.row_exp[I * 32 + (e >> 5)]) +
-                                      static_cast<uint32_t>(w.col_exp[J * 32 + (e & 31)]) - 56u);
-      bool ok;
-      const double x = scaled_i64_fast(t, e2, &ok);
-      dst[e] = ok ? x : scaled_i64_to_double(t, e2);
+    // each thread: 4 consecutive elements of one row, every slot's values
+    // loaded at once (16-byte loads), then summed, converted and stored
+    for (int e0 = threadIdx.x * 4; e0 < 1024; e0 += blockDim.x * 4) {
+      longlong2 part[kFewPairsMax][2];
+#pragma unroll
+      for (int j = 0; j < kFewPairsMax; ++j) {
+        if (j < m) {
+          const longlong2 *p = reinterpret_cast<const longlong2 *>(src + j * 1024 + e0);
+          part[j][0] = p[0];
+          part[j][1] = p[1];
+        } else {
+          part[j][0] = make_longlong2(0, 0);
+          part[j][1] = make_longlong2(0, 0);
+        }
+      }
+      const int er = w.row_exp[I * 32 + (e0 >> 5)];
+      const int4 fc = *reinterpret_cast<const int4 *>(w.col_exp + J * 32 + (e0 & 31));
+      long long t[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int j = 0; j < kFewPairsMax; ++j) {
+        t[0] += part[j][0].x;
+        t[1] += part[j][0].y;
+        t[2] += part[j][1].x;
+        t[3] += part[j][1].y;
+      }
+      const int f[4] = {fc.x, fc.y, fc.z, fc.w};
+      double x[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        // (an empty line of A or B has zero digits: t = 0 converts to +0)
+        const int e2 = static_cast<int>(static_cast<uint32_t>(er) + static_cast<uint32_t>(f[k]) - 56u);
+        bool ok;
+        x[k] = scaled_i64_fast(t[k], e2, &ok);
+        if (!ok) x[k] = scaled_i64_to_double(t[k], e2);
+      }
+      reinterpret_cast<double2 *>(dst + e0)[0] = make_double2(x[0], x[1]);
+      reinterpret_cast<double2 *>(dst + e0)[1] = make_double2(x[2], x[3]);
     }
   }
 }
