@@ -188,6 +188,20 @@ int device_status_ptr(int **ptr) {
   return CHT_OK;
 }
 
+int side_stream(SideStream **out) {
+  static thread_local SideStream side[kMaxDevices];
+  int dev = 0;
+  CHT_TRY(current_device(&dev));
+  SideStream &ss = side[dev];
+  if (!ss.s) {
+    CHT_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+    CHT_CUDA_TRY(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
+    CHT_CUDA_TRY(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming));
+  }
+  *out = &ss;
+  return CHT_OK;
+}
+
 int num_sms(int *sms) {
   int dev = 0;
   CHT_TRY(current_device(&dev));

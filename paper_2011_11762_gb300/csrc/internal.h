@@ -61,6 +61,16 @@ enum : int { DEV_STATUS_TIMEOUT = 1, DEV_STATUS_BAD_INDEX = 2 };
 #endif
 int device_status_ptr(int **ptr);
 int num_sms(int *sms);
+// A second stream of the calling host thread on the current device, with
+// two events, for work that can run beside the caller's stream s: record
+// `fork` on s and make the side stream wait for it, queue the side work,
+// record `join` on the side stream and make s wait for it.  Created at the
+// thread's first use on a device and kept.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+int side_stream(SideStream **out);
 
 // ------------------------------------------------------------- allocation --
 void *dev_alloc(size_t bytes, cudaStream_t s);

@@ -1828,9 +1828,13 @@ int alloc_operands(const Pattern &pa, const Pattern &pb, cudaStream_t s, Operand
   return CHT_OK;
 }
 
-// Exponents and slices of A and B (the pre-kernels of one product).
+// Exponents and slices of A and B (the pre-kernels of one product).  With
+// `side`, B's two kernels run on the side stream, beside A's (the two
+// chains share nothing; both are short and latency-bound on small products),
+// and s waits for them at the end.
 template <int B>
-int split_operands(const cht_mat *A, const cht_mat *Bm, cudaStream_t s, Operands &op) {
+int split_operands(const cht_mat *A, const cht_mat *Bm, cudaStream_t s, Operands &op,
+                   bool side = false) {
   using CF = Cfg<B>;
   const Pattern &pa = *A->pat, &pb = *Bm->pat;
   // kNoExp fill (every byte 0x80)
@@ -1838,13 +1842,21 @@ int split_operands(const cht_mat *A, const cht_mat *Bm, cudaStream_t s, Operands
   CHT_CUDA_TRY(cudaMemsetAsync(op.col_exp.p, 0x80, sizeof(int) * pa.n, s));
   const double *av = const_cast<cht_mat *>(A)->values();
   const double *bv = const_cast<cht_mat *>(Bm)->values();
+  SideStream *ss = nullptr;
+  cudaStream_t sb = s;
+  if (side && pa.nnz > 0 && pb.nnz > 0) {
+    CHT_TRY(side_stream(&ss));
+    CHT_CUDA_TRY(cudaEventRecord(ss->fork, s));
+    CHT_CUDA_TRY(cudaStreamWaitEvent(ss->s, ss->fork, 0));
+    sb = ss->s;
+  }
   if (pa.nnz > 0) {
     k_row_exp<B><<<grid_for(pa.nnz * B * (B / 16), 256), 256, 0, s>>>(av, pa.brow.p, pa.nnz,
                                                                       op.row_exp.p);
     CHT_TRY(launched("row_exp"));
   }
   if (pb.nnz > 0) {
-    k_col_exp<B><<<grid_for(pb.nnz * B, 256), 256, 0, s>>>(bv, pb.bcol.p, pb.nnz, op.col_exp.p);
+    k_col_exp<B><<<grid_for(pb.nnz * B, 256), 256, 0, sb>>>(bv, pb.bcol.p, pb.nnz, op.col_exp.p);
     CHT_TRY(launched("col_exp"));
   }
   if (pa.nnz > 0) {
@@ -1859,9 +1871,13 @@ int split_operands(const cht_mat *A, const cht_mat *Bm, cudaStream_t s, Operands
     constexpr int smem = SplitBSmem<B>::TOTAL;
     CHT_CUDA_TRY(cudaFuncSetAttribute(k_split_b<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       smem));
-    k_split_b<B><<<static_cast<unsigned>(nblk), 256, smem, s>>>(bv, pb.bcol.p, pb.nnz,
-                                                                op.col_exp.p, op.b_sl.p);
+    k_split_b<B><<<static_cast<unsigned>(nblk), 256, smem, sb>>>(bv, pb.bcol.p, pb.nnz,
+                                                                 op.col_exp.p, op.b_sl.p);
     CHT_TRY(launched("split_b"));
+  }
+  if (ss) {
+    CHT_CUDA_TRY(cudaEventRecord(ss->join, ss->s));
+    CHT_CUDA_TRY(cudaStreamWaitEvent(s, ss->join, 0));
   }
   return CHT_OK;
 }
@@ -2307,9 +2323,9 @@ int split_multiply(cht_plan *plan, cht_mat *A, cht_mat *B, int nslices, cudaStre
   Operands op;
   CHT_TRY(alloc_operands(*A->pat, *B->pat, s, op));
   if (b == 64)
-    CHT_TRY(split_operands<64>(A, B, s, op));
+    CHT_TRY(split_operands<64>(A, B, s, op, true));
   else
-    CHT_TRY(split_operands<32>(A, B, s, op));
+    CHT_TRY(split_operands<32>(A, B, s, op, true));
   SplitProd d = make_prod(plan, op, Cvals);
   DevArray<unsigned long long> counter;
   CHT_TRY(counter.alloc(1, s));
