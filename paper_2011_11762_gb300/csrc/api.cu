@@ -105,7 +105,11 @@ static void keep_pool_memory() {
 // work W on stream s is reused only by work queued on s after W), and the
 // symbolic phase's dozens of short-lived arrays then cost no allocator call.
 // Larger blocks, blocks beyond the cache's cap and any cached block after an
-// allocation failure go back to the stream-ordered pool.
+// allocation failure go back to the stream-ordered pool.  The cache keys on
+// the stream handle: a caller that destroys a stream while the library's
+// work on it is still running, and then gets the same handle for a new
+// stream, should synchronise the old one first (as for any stream-ordered
+// free).
 namespace {
 constexpr size_t kCacheMaxBlock = size_t(64) << 20;   // larger: not cached
 constexpr size_t kCacheMaxTotal = size_t(1) << 30;    // cached bytes per process
