@@ -338,3 +338,30 @@ def test_split_one_pair_leaves(lib, scaled):
         assert np.all(np.abs(got - ref) <= sp.error_bound(ad, bd, S, W)
                       + 2 * np.spacing(np.abs(ref)))
     lib.sync_status()
+
+
+def test_split_pair_count_boundary(lib):
+    """C leaves of 1 .. 5 leaf pairs (banded +-2 times banded +-2 on an 8 x 8
+    leaf grid of 32-leaves): those of at most FEW pairs go to the one-pair
+    kernel (the several-pair ones as one unit per pair, their exact integers
+    summed and rounded once), those of FEW + 1 to the general kernel; each
+    against the exact emulation of its own slice pairs."""
+    n, b = 256, 32
+    a, bm = w.banded(n, b, 2, 7071), w.banded(n, b, 2, 7072)
+    A, B = gu.upload(lib, a), gu.upload(lib, bm)
+    plan = lib.cht_symbolic_multiply(A, B)
+    seg = np.diff(plan.arrays()["cseg"].numpy())
+    assert set(seg.tolist()) == {1, 2, 3, 4, 5}
+    C, _ = lib.cht_multiply(plan, A, B, mode=lib.CHT_SPLIT_BF16, sync=True)
+    ad, bd = a.to_dense(), bm.to_dense()
+    emu, e, f, one = _emulate(lib, plan, ad, bd, b, n)
+    assert one is not None and one.any() and not one.all()
+    got = _dense_on(C, n)
+    scale = np.ldexp(1.0, (e[:, None] + f[None, :]).astype(np.int64))
+    tol = scale * float(n) ** 2 * 2.0 ** -54 + 2 * np.spacing(np.abs(emu))
+    tol = np.where(one, 2 * np.spacing(np.abs(emu)), tol)
+    mask = _dense_on(lib.cht_multiply(plan, A, B, sync=True)[0], n) != 0
+    assert np.all(np.abs(got - emu)[mask] <= tol[mask])
+    assert np.all(np.abs(got - ad @ bd) <= sp.error_bound(ad, bd, S, W)
+                  + 2 * np.spacing(np.abs(ad @ bd)))
+    lib.sync_status()
