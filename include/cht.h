@@ -138,8 +138,12 @@ int cht_mat_free(cht_mat_t M);
  * A and B must have equal n and b (else CHT_ERR_SHAPE).
  * *nnzb_C and *npairs (either may be NULL) get the number of C leaves and of
  * pairs; the useful work of the numeric phase is 2 * b^3 * npairs flops.
- * Synchronises `stream` three times (to size the pair list and C's pattern,
- * and to record the longest pair segment).
+ * Synchronises `stream` once, to read C's leaf count, the longest pair
+ * segment and C's leaf counts per row and column: the pair list is sized
+ * from the leaf counts per row and column that every pattern keeps on the
+ * host (read when the pattern was made).  Grids of more than 65536 leaves
+ * per side keep no such counts and cost one more synchronisation, as do
+ * the filters of the _spamm, _symsquare and _upper variants.
  * ---------------------------------------------------------------------- */
 int cht_symbolic_multiply(cht_mat_t A, cht_mat_t B, void *stream,
                           cht_plan_t *out, int64_t *nnzb_C, int64_t *npairs);
@@ -256,12 +260,16 @@ int cht_plan_free(cht_plan_t P);
  * Each C leaf is summed in ascending K by one CTA: results are bitwise
  * reproducible run to run.  No atomics touch C.
  * CHT_SPLIT_BF16: nslices = 0 or 6 (6 digits of 8 bits per operand, 48
- * bits); inputs must be finite; b = 32 or 64.  At b = 32 the C leaves with
- * exactly one leaf pair are computed by a kernel that stacks four of them
- * sharing a B leaf in one MMA (slice pairs i + j <= 7); the other C leaves
- * by the general kernel (8 A digits, 4 stacked A slices).  The first such
- * multiply on a plan groups its one-pair leaves and keeps the groups in the
- * plan (synchronises `stream` twice).  One work unit sums at most
+ * bits); inputs must be finite; b = 32 or 64.  At b = 32 the pairs of the
+ * C leaves with at most 4 leaf pairs are computed by a kernel that stacks
+ * four of them sharing a B leaf in one MMA (slice pairs i + j <= 7; a C
+ * leaf of several pairs has its pairs' exact integer results summed and
+ * rounded once, with one int64 scratch leaf per such pair); the other C
+ * leaves by the general kernel (8 A digits, 4 stacked A slices).  The first
+ * such multiply on a plan groups those pairs (from counts the symbolic phase
+ * took, without a synchronisation) and keeps the groups in the plan.  The
+ * B operand's pre-kernels run on a second stream of the calling thread,
+ * joined to `stream` before the numeric kernels.  One work unit sums at most
  * 1016 (b = 64) or 4000 (b = 32) leaf pairs exactly; a C leaf with more is
  * cut into equal pieces whose sums are added in FP64 in piece order (still
  * reproducible; scratch of one leaf per piece).  The bound returned is
@@ -390,10 +398,10 @@ typedef enum {
                                  with 4 x 4 register tiles at b = 64, 128
                                  threads at b = 32); 2 = DFMA with 128-thread
                                  CTAs (4 x 8 tiles) at b = 64 as well      */
-  CHT_OPT_SPLIT_SINGLE = 4    /* split form, 32-leaves: 1 (default) = C
-                                 leaves with one leaf pair go to the kernel
-                                 that groups them by B leaf (see
-                                 cht_multiply); 0 = every C leaf to the
+  CHT_OPT_SPLIT_SINGLE = 4    /* split form, 32-leaves: 1 (default) = the
+                                 pairs of C leaves with at most 4 leaf pairs
+                                 go to the kernel that groups them by B leaf
+                                 (see cht_multiply); 0 = every C leaf to the
                                  general kernel                            */
 } cht_option;
 int cht_set_option(int option, int64_t value);
