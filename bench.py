@@ -62,6 +62,8 @@ def parse_args():
                     help="extra sections (comma list; '' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunks", type=int, default=8,
+                    help="Morton ranges of C computed and copied to the host in turn (e2e)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
     return ap.parse_args()
@@ -326,7 +328,7 @@ def fp64_e2e(args, world, cht, torch, a, b):
         if state["out"] is None or tuple(state["out"].shape) != shape:
             state["out"] = torch.empty(shape, dtype=torch.float64, pin_memory=True)
         # C straight to pinned host memory, chunk by chunk while it computes
-        cht.cht_multiply_to_host(p, A, B, state["out"], nchunks=8)
+        cht.cht_multiply_to_host(p, A, B, state["out"], nchunks=args.e2e_chunks)
         state["flops"] = p.useful_flops
         state["d2h"] = state["out"].numel() * 8
         stream.synchronize()  # this step's C is in host memory
