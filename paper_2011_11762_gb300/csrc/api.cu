@@ -206,6 +206,25 @@ int side_stream(SideStream **out) {
   return CHT_OK;
 }
 
+int pinned_scratch(size_t bytes, void **out) {
+  struct Buf {
+    void *p = nullptr;
+    size_t n = 0;
+  };
+  static thread_local Buf buf;
+  if (buf.n < bytes) {
+    if (buf.p) cudaFreeHost(buf.p);
+    buf.p = nullptr;
+    buf.n = 0;
+    size_t n = 4096;
+    while (n < bytes) n <<= 1;
+    CHT_CUDA_TRY(cudaHostAlloc(&buf.p, n, cudaHostAllocPortable));
+    buf.n = n;
+  }
+  *out = buf.p;
+  return CHT_OK;
+}
+
 int num_sms(int *sms) {
   int dev = 0;
   CHT_TRY(current_device(&dev));

@@ -71,6 +71,10 @@ struct SideStream {
   cudaEvent_t fork = nullptr, join = nullptr;
 };
 int side_stream(SideStream **out);
+// Pinned host memory of at least `bytes` for the calling host thread (kept
+// and reused: the next call may return the same memory), for device-to-host
+// reads that are followed by a synchronisation.
+int pinned_scratch(size_t bytes, void **out);
 
 // ------------------------------------------------------------- allocation --
 void *dev_alloc(size_t bytes, cudaStream_t s);
@@ -266,7 +270,8 @@ struct cht_plan {
   // unit of its own, summed afterwards), the groups of up to four units
   // sharing a B leaf, and the units per B leaf
   int64_t n_one = -1, n_few = -1, n_virt = -1, n_groups = -1;
-  cht::DevArray<int32_t> one_pair_b; // [nB]
+  cht::DevArray<int64_t> sym_block;  // the symbolic phase's counters (kept for:)
+  const int32_t *one_pair_b = nullptr;  // [nB], inside sym_block
   cht::DevArray<int64_t> cseg;       // [nC + 1]
   cht::DevArray<int32_t> pa, pb, pc; // per pair (sorted by C leaf, then K)
   cht::DevArray<int32_t> order;      // schedule [nC]

@@ -2160,7 +2160,7 @@ struct SingleGroups {
 int build_single_groups(const cht_plan *plan, cudaStream_t s, SingleGroups &g) {
   const int64_t nC = plan->C->nnz, nB = plan->nB;
   if (plan->n_one < 0 || plan->n_few < 0 || plan->n_virt < 0 || plan->n_groups < 0 ||
-      plan->one_pair_b.p == nullptr) {
+      plan->one_pair_b == nullptr) {
     set_error("the plan carries no unit counts (a 32-leaf plan from the symbolic phase does)");
     return CHT_ERR_INVALID;
   }
@@ -2184,7 +2184,7 @@ int build_single_groups(const cht_plan *plan, cudaStream_t s, SingleGroups &g) {
   CHT_TRY(g.few_v.alloc(g.nfew, s));
   CHT_TRY(g.few_m.alloc(g.nfew, s));
   if (nC == 0) return CHT_OK;
-  CHT_TRY(scan_exclusive_fn(GroupsOf{plan->one_pair_b.p}, nB, gstart.p, s));
+  CHT_TRY(scan_exclusive_fn(GroupsOf{plan->one_pair_b}, nB, gstart.p, s));
   CHT_CUDA_TRY(cudaMemsetAsync(fill.p, 0, sizeof(int32_t) * nB, s));
   CHT_CUDA_TRY(cudaMemsetAsync(counters.p, 0, sizeof(unsigned long long) * 3, s));
   CHT_CUDA_TRY(cudaMemsetAsync(g.ga.p, 0, sizeof(int32_t) * 4 * ng, s));

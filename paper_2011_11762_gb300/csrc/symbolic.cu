@@ -9,6 +9,7 @@
 // triples by (Morton(I, J), K) groups them per C leaf in Morton order, with
 // ascending K inside each group.  All of this is exact integer work.
 #include <algorithm>
+#include <cstring>
 
 #include "device.cuh"
 #include "internal.h"
@@ -429,10 +430,20 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   // form's units (32-leaves), [4] the device's pair total (checked against
   // the host's count), [5] C leaves of 2 .. kFewPairsMax pairs, [6] their
   // pairs
+  // One zeroed device block holds them, then C's leaf counts per row and
+  // column (2 G int32, when kept), then the units per B leaf (32-leaves): one
+  // memset, and one copy to pinned host memory at the synchronisation.
   constexpr int kStats = 7;
+  const bool groups = A.b == 32 && B.nnz > 0;
+  const int64_t G = A.G;
+  const bool counts = G <= kMaxCountG;
+  const int64_t n_rc = counts ? 2 * G : 0, n_b = groups ? B.nnz : 0;
+  const int64_t words = kStats + (n_rc + n_b + 1) / 2;  // int64 words
   DevArray<int64_t> stats;
-  CHT_TRY(stats.alloc(kStats, s));
-  CHT_CUDA_TRY(cudaMemsetAsync(stats.p, 0, sizeof(int64_t) * kStats, s));
+  CHT_TRY(stats.alloc(words, s));
+  CHT_CUDA_TRY(cudaMemsetAsync(stats.p, 0, sizeof(int64_t) * words, s));
+  int32_t *rc = counts ? reinterpret_cast<int32_t *>(stats.p + kStats) : nullptr;
+  int32_t *cntB = groups ? reinterpret_cast<int32_t *>(stats.p + kStats) + n_rc : nullptr;
   DevArray<uint64_t> skey;
   DevArray<int32_t> pa, pb;
   int64_t P = 0;
@@ -452,49 +463,38 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   CHT_TRY(C->bcol.alloc(P, s));
   CHT_TRY(plan->cseg.alloc(P + 1, s));
   CHT_TRY(plan->pc.alloc(P, s));
-  // per-B-leaf counts of the split form's units (32-leaves: the pairs of C
-  // leaves with at most kFewPairsMax pairs), and the C pattern's leaf
-  // counts per row and column
-  const bool groups = A.b == 32 && B.nnz > 0;
-  const int64_t G = A.G;
-  const bool counts = G <= kMaxCountG;
-  DevArray<int32_t> cntB, rc;
-  if (groups) {
-    CHT_TRY(cntB.alloc(B.nnz, s));
-    CHT_CUDA_TRY(cudaMemsetAsync(cntB.p, 0, sizeof(int32_t) * B.nnz, s));
-  }
-  if (counts) {
-    CHT_TRY(rc.alloc(2 * G, s));
-    CHT_CUDA_TRY(cudaMemsetAsync(rc.p, 0, sizeof(int32_t) * 2 * G, s));
-  }
+  // (per-B-leaf counts of the split form's units -- 32-leaves: the pairs of
+  // C leaves with at most kFewPairsMax pairs -- and the C pattern's leaf
+  // counts per row and column live in the statistics block)
   auto *st = reinterpret_cast<unsigned long long *>(stats.p);
   if (P > 0) {
     k_segments<<<grid_for(P, 256), 256, 0, s>>>(skey.p, cpos.p, P, L, d_nC, C->mkey.p,
                                                 C->brow.p, C->bcol.p, plan->cseg.p, plan->pc.p);
     CHT_TRY(launched("segments"));
     k_c_stats<<<grid_for(P, 256), 256, 0, s>>>(plan->cseg.p, C->mkey.p, d_nC, pb.p,
-                                                groups ? cntB.p : nullptr,
-                                                counts ? rc.p : nullptr,
-                                                counts ? rc.p + G : nullptr, st);
+                                                cntB, rc, counts ? rc + G : nullptr, st);
     CHT_TRY(launched("c_stats"));
     if (groups) {
-      k_group_count<<<grid_for(B.nnz, 256), 256, 0, s>>>(cntB.p, B.nnz, st + 3);
+      k_group_count<<<grid_for(B.nnz, 256), 256, 0, s>>>(cntB, B.nnz, st + 3);
       CHT_TRY(launched("group_count"));
     }
   } else {
     CHT_CUDA_TRY(cudaMemsetAsync(plan->cseg.p, 0, sizeof(int64_t), s));
   }
-  int64_t host_stats[kStats] = {};
-  CHT_CUDA_TRY(cudaMemcpyAsync(host_stats, stats.p, sizeof(host_stats), cudaMemcpyDeviceToHost, s));
-  if (counts) {
-    C->rowcnt.resize(G);
-    C->colcnt.resize(G);
-    CHT_CUDA_TRY(cudaMemcpyAsync(C->rowcnt.data(), rc.p, sizeof(int32_t) * G,
-                                 cudaMemcpyDeviceToHost, s));
-    CHT_CUDA_TRY(cudaMemcpyAsync(C->colcnt.data(), rc.p + G, sizeof(int32_t) * G,
-                                 cudaMemcpyDeviceToHost, s));
-  }
+  // the statistics and C's counts (not the units per B leaf, which stay on
+  // the device) in one copy
+  const size_t read_bytes = sizeof(int64_t) * kStats + sizeof(int32_t) * n_rc;
+  void *host = nullptr;
+  CHT_TRY(pinned_scratch(read_bytes, &host));
+  CHT_CUDA_TRY(cudaMemcpyAsync(host, stats.p, read_bytes, cudaMemcpyDeviceToHost, s));
   CHT_CUDA_TRY(cudaStreamSynchronize(s));
+  int64_t host_stats[kStats];
+  std::memcpy(host_stats, host, sizeof(host_stats));
+  if (counts) {
+    const int32_t *hc = reinterpret_cast<const int32_t *>(static_cast<const int64_t *>(host) + kStats);
+    C->rowcnt.assign(hc, hc + G);
+    C->colcnt.assign(hc + G, hc + 2 * G);
+  }
   if (P_made >= 0 && host_stats[4] != P_made) {
     set_error("pair count %lld from the leaf counts, %lld on the device", (long long)P_made,
               (long long)host_stats[4]);
@@ -507,7 +507,9 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
     plan->n_groups = host_stats[3];
     plan->n_few = host_stats[5];
     plan->n_virt = host_stats[6];
-    plan->one_pair_b = std::move(cntB);
+    // the units per B leaf stay where they are: the plan keeps the block
+    plan->one_pair_b = cntB;
+    plan->sym_block = std::move(stats);
   }
 
   C->n = A.n;
