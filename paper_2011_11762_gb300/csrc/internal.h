@@ -190,8 +190,13 @@ int scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
 // Stable LSD radix sort of (key, value) by bits lo_bit .. lo_bit + nbits - 1
 // of key.  Passes read whole bytes, so up to 7 bits above that range take
 // part in the order too: callers keep them zero.
+// `zeroed`: sort_state_words(n, nbits, lo_bit) words of zeroed device memory
+// for the sort's histograms and state (used up by the call), or null to
+// allocate and clear them here.
 int radix_sort_pairs(const uint64_t *kin, const int32_t *vin, uint64_t *kout,
-                     int32_t *vout, int64_t n, int nbits, cudaStream_t s, int lo_bit = 0);
+                     int32_t *vout, int64_t n, int nbits, cudaStream_t s, int lo_bit = 0,
+                     unsigned long long *zeroed = nullptr);
+int64_t sort_state_words(int64_t n, int nbits, int lo_bit = 0);
 // Copy of a device int64 to the host (synchronises s).
 int read_i64(const int64_t *d, int64_t *h, cudaStream_t s);
 

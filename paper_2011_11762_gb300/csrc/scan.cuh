@@ -173,9 +173,17 @@ __global__ void __launch_bounds__(kThreads)
 
 }  // namespace scan_detail
 
+// Words of zeroed state a scan of n elements uses.
+inline int64_t scan_state_words(int64_t n) {
+  return (n + scan_detail::kTile - 1) / scan_detail::kTile + 1;
+}
+
 // out[0..n] = exclusive prefix sums of load(0 .. n), out[n] = the total.
+// `zeroed`: scan_state_words(n) words of zeroed device memory for its state
+// (used up by the call), or null to allocate and clear them here.
 template <class Load>
-int scan_exclusive_fn(Load load, int64_t n, int64_t *out, cudaStream_t s) {
+int scan_exclusive_fn(Load load, int64_t n, int64_t *out, cudaStream_t s,
+                      unsigned long long *zeroed = nullptr) {
   using namespace scan_detail;
   if (n <= 0) {
     CHT_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
@@ -183,9 +191,13 @@ int scan_exclusive_fn(Load load, int64_t n, int64_t *out, cudaStream_t s) {
   }
   const int64_t ntiles = (n + kTile - 1) / kTile;
   DevArray<unsigned long long> state;
-  CHT_TRY(state.alloc(ntiles + 1, s));
-  CHT_CUDA_TRY(cudaMemsetAsync(state.p, 0, sizeof(unsigned long long) * (ntiles + 1), s));
-  k_scan<Load><<<static_cast<unsigned>(ntiles), kThreads, 0, s>>>(load, n, out, state.p);
+  unsigned long long *st = zeroed;
+  if (!st) {
+    CHT_TRY(state.alloc(ntiles + 1, s));
+    CHT_CUDA_TRY(cudaMemsetAsync(state.p, 0, sizeof(unsigned long long) * (ntiles + 1), s));
+    st = state.p;
+  }
+  k_scan<Load><<<static_cast<unsigned>(ntiles), kThreads, 0, s>>>(load, n, out, st);
   return launched("scan");
 }
 

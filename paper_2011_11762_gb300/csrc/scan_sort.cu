@@ -159,8 +159,15 @@ int scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s) {
   return scan_exclusive_fn(ArrayLoad<int64_t>{in}, n, out, s);
 }
 
+int64_t sort_state_words(int64_t n, int nbits, int lo_bit) {
+  const int npass = std::min((64 - lo_bit + 7) / 8, std::max(1, (nbits + 7) / 8));
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  return npass * kRadix + npass * (1 + ntiles * kRadix);
+}
+
 int radix_sort_pairs(const uint64_t *kin, const int32_t *vin, uint64_t *kout, int32_t *vout,
-                     int64_t n, int nbits, cudaStream_t s, int lo_bit) {
+                     int64_t n, int nbits, cudaStream_t s, int lo_bit,
+                     unsigned long long *zeroed) {
   if (n <= 0) return CHT_OK;
   if (lo_bit < 0 || lo_bit + nbits > 64) {
     set_error("radix sort on bits %d .. %d of 64-bit keys", lo_bit, lo_bit + nbits - 1);
@@ -175,10 +182,14 @@ int radix_sort_pairs(const uint64_t *kin, const int32_t *vin, uint64_t *kout, in
   const int64_t per_pass = 1 + ntiles * kRadix;  // counter + published words
   // one zeroed buffer: the histograms of every pass, then each pass's state
   DevArray<unsigned long long> buf;
-  CHT_TRY(buf.alloc(npass * kRadix + npass * per_pass, s));
-  CHT_CUDA_TRY(cudaMemsetAsync(
-      buf.p, 0, sizeof(unsigned long long) * (npass * kRadix + npass * per_pass), s));
-  unsigned long long *hist = buf.p, *state = buf.p + npass * kRadix;
+  unsigned long long *zb = zeroed;
+  if (!zb) {
+    CHT_TRY(buf.alloc(npass * kRadix + npass * per_pass, s));
+    CHT_CUDA_TRY(cudaMemsetAsync(
+        buf.p, 0, sizeof(unsigned long long) * (npass * kRadix + npass * per_pass), s));
+    zb = buf.p;
+  }
+  unsigned long long *hist = zb, *state = zb + npass * kRadix;
   int sms = 0;
   CHT_TRY(num_sms(&sms));
   const int64_t hgrid = std::min<int64_t>(ntiles, 4LL * std::max(sms, 1));

@@ -305,12 +305,13 @@ static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
                         DevArray<uint64_t> &skey, DevArray<int32_t> &pa, DevArray<int32_t> &pb,
                         int64_t *P_out, int64_t *d_ptotal, const double *normA = nullptr,
                         const double *normB = nullptr, double tau = 0.0,
-                        bool upper_only = false) {
+                        bool upper_only = false, unsigned long long *z_scan = nullptr,
+                        unsigned long long *z_sort = nullptr) {
   const int L = A.L;
   CHT_TRY(ensure_row_index(B, s));
   DevArray<int64_t> off;
   CHT_TRY(off.alloc(A.nnz + 1, s));
-  CHT_TRY(scan_exclusive_fn(PairCount{A.bcol.p, B.rowptr.p}, A.nnz, off.p, s));
+  CHT_TRY(scan_exclusive_fn(PairCount{A.bcol.p, B.rowptr.p}, A.nnz, off.p, s, z_scan));
   int64_t P = host_pair_count(A, B);
   if (P < 0) {
     CHT_TRY(read_i64(off.p + A.nnz, &P, s));
@@ -374,7 +375,8 @@ static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
     // the fill wrote the pairs in A's (Morton) leaf order, so for one (I, J)
     // in ascending K: a stable sort on the Morton(I, J) bits alone keeps K
     // ascending inside every C leaf
-    CHT_TRY(radix_sort_pairs(key.p, idx.p, skey.p, sidx.p, P, 2 * L, s, L));
+    CHT_TRY(radix_sort_pairs(key.p, idx.p, skey.p, sidx.p, P, 2 * L, s, L,
+                             (normA || upper_only) ? nullptr : z_sort));
     k_pair_gather<<<grid_for(P, 256), 256, 0, s>>>(sidx.p, P, pa0.p, pb0.p, pa.p, pb.p);
     CHT_TRY(launched("pair_gather"));
   }
@@ -385,7 +387,7 @@ static int make_triples(const Pattern &A, const Pattern &B, cudaStream_t s,
 // Longest-first order of n units with segments seg; max_len: the longest
 // segment when known (the sort then reads only the bits it needs), else 0.
 int schedule_units(const int64_t *seg, int64_t n, int32_t *order, cudaStream_t s,
-                   int64_t max_len = 0) {
+                   int64_t max_len = 0, unsigned long long *zeroed = nullptr) {
   if (n <= 0) return CHT_OK;
   const int64_t cap = max_len > 0 ? std::min(max_len, kLptCap) : kLptCap;
   if (g_opt.schedule == 1 || (max_len == 1)) {
@@ -400,7 +402,7 @@ int schedule_units(const int64_t *seg, int64_t n, int32_t *order, cudaStream_t s
   CHT_TRY(idx.alloc(n, s));
   k_lpt_keys<<<grid_for(n, 256), 256, 0, s>>>(seg, n, cap, key.p, idx.p);
   CHT_TRY(launched("lpt_keys"));
-  return radix_sort_pairs(key.p, idx.p, skey.p, order, n, bits_for(cap + 1), s);
+  return radix_sort_pairs(key.p, idx.p, skey.p, order, n, bits_for(cap + 1), s, 0, zeroed);
 }
 
 int leaf_norms(const double *vals, int64_t n, int b, double *out, cudaStream_t s) {
@@ -437,23 +439,39 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   const bool groups = A.b == 32 && B.nnz > 0;
   const int64_t G = A.G;
   const bool counts = G <= kMaxCountG;
+  // When the pair count is known now (host leaf counts, no pair filter) the
+  // same block also holds the zeroed state of the phase's two scans and two
+  // sorts, so that one memset serves the whole phase.
   const int64_t n_rc = counts ? 2 * G : 0, n_b = groups ? B.nnz : 0;
-  const int64_t words = kStats + (n_rc + n_b + 1) / 2;  // int64 words
+  const int64_t P_known = host_pair_count(A, B);
+  const bool pre = P_known >= 0 && !normA && !upper_only;
+  const int64_t w_scan1 = pre ? scan_state_words(A.nnz) : 0;
+  const int64_t w_sort = pre ? sort_state_words(P_known, 2 * L, L) : 0;
+  const int64_t w_scan2 = pre ? scan_state_words(P_known) : 0;
+  const int64_t w_lpt = pre ? sort_state_words(P_known, 16) : 0;
+  const int64_t w_counts = (n_rc + n_b + 1) / 2;  // int64 words
+  const int64_t words = kStats + w_counts + w_scan1 + w_sort + w_scan2 + w_lpt;
   DevArray<int64_t> stats;
   CHT_TRY(stats.alloc(words, s));
   CHT_CUDA_TRY(cudaMemsetAsync(stats.p, 0, sizeof(int64_t) * words, s));
   int32_t *rc = counts ? reinterpret_cast<int32_t *>(stats.p + kStats) : nullptr;
   int32_t *cntB = groups ? reinterpret_cast<int32_t *>(stats.p + kStats) + n_rc : nullptr;
+  auto *zw = reinterpret_cast<unsigned long long *>(stats.p + kStats + w_counts);
+  unsigned long long *z_scan1 = pre ? zw : nullptr;
+  unsigned long long *z_sort = pre ? zw + w_scan1 : nullptr;
+  unsigned long long *z_scan2 = pre ? zw + w_scan1 + w_sort : nullptr;
+  unsigned long long *z_lpt = pre ? zw + w_scan1 + w_sort + w_scan2 : nullptr;
   DevArray<uint64_t> skey;
   DevArray<int32_t> pa, pb;
   int64_t P = 0;
-  CHT_TRY(make_triples(A, B, s, skey, pa, pb, &P, stats.p + 4, normA, normB, tau, upper_only));
+  CHT_TRY(make_triples(A, B, s, skey, pa, pb, &P, stats.p + 4, normA, normB, tau, upper_only,
+                       z_scan1, z_sort));
   const int64_t P_made = host_pair_count(A, B);  // the count the pair list was sized with
   plan->npairs = P;
 
   DevArray<int64_t> cpos;
   CHT_TRY(cpos.alloc(P + 1, s));
-  CHT_TRY(scan_exclusive_fn(HeadFlag{skey.p, L}, P, cpos.p, s));
+  CHT_TRY(scan_exclusive_fn(HeadFlag{skey.p, L}, P, cpos.p, s, pre && P == P_known ? z_scan2 : nullptr));
   // C leaves <= P: the C pattern's keys, coordinates and segments are
   // written at that capacity (and kept at it)
   auto C = std::make_shared<Pattern>();
@@ -519,7 +537,8 @@ int symbolic(const Pattern &A, const Pattern &B, cudaStream_t s, cht_plan **out,
   C->nnz = nC;
   C->id = next_id();
   CHT_TRY(plan->order.alloc(nC, s));
-  CHT_TRY(schedule_units(plan->cseg.p, nC, plan->order.p, s, plan->max_seg));
+  CHT_TRY(schedule_units(plan->cseg.p, nC, plan->order.p, s, plan->max_seg,
+                         pre && nC <= P_known ? z_lpt : nullptr));
   plan->pa = std::move(pa);
   plan->pb = std::move(pb);
   plan->C = std::move(C);
